@@ -1,0 +1,193 @@
+"""FP64 CPU oracle for the LArTPC signal-simulation hot path (arXiv 2304.01841, §2).
+
+TEST INFRASTRUCTURE ONLY: imported by the test-suite, by the package smoke check and by
+the benchmark's CPU-baseline / reference arm.  The GPU library never imports it.  The
+rasterize / scatter steps are plain C loops in FP64 (oracle/wct_oracle.c, built with gcc
+into oracle/_build/); the convolution is scipy's FP64 FFT (oracle/convolve.py) plus a
+literal quadruple loop for small grids.
+
+Parity status of each function (what pins it; see tests/test_oracle_*.py):
+  windows / weights    pinned: mpmath Gaussian bin integrals, brute-force window sets,
+                       hand-computed drift / diffusion values, moments of the patch.
+  rasterize (no fluct) pinned: patch sums to q, outer-product structure, shift invariance.
+  rasterize (fluct)    pinned statistically: per-bin mean / variance of the multinomial,
+                       large-q limit.  The exact Philox stream is pinned only by statistics
+                       and by bit-equality with the independent CUDA implementation (no
+                       published known-answer vectors are available here).
+  scatter              pinned: charge conservation, hand-built folding cases.
+  convolve             pinned: delta response = identity, delta grid = placed response,
+                       direct quadruple loop, no circular wrap, linearity.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from typing import Optional, Tuple
+
+import numpy as np
+
+from .convolve import convolve_fft, convolve_direct_np  # noqa: F401
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "wct_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libwctoracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# Largest window the library accepts (ticks x impact bins); depos beyond are invalid.
+MAX_NT = 128
+MAX_NP = 512
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc (FP64, no floating-point contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+                               "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB)
+            P = ctypes.c_void_p
+            i64, i32, u64, dbl = ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_double
+            L.or_philox_batch.argtypes = [i64, P, P, P]
+            L.or_philox_batch.restype = None
+            L.or_bin_normal.argtypes = [u64, ctypes.c_uint32, i64, i64, i32, i32, u64]
+            L.or_bin_normal.restype = dbl
+            L.or_axis_weights.argtypes = [dbl, dbl, dbl, P, P, P, i64]
+            L.or_axis_weights.restype = None
+            L.or_windows.argtypes = [i64, P, P, P, P, P, P, P, i64, i64, P, P, P]
+            L.or_windows.restype = i64
+            L.or_rasterize.argtypes = [i64, P, P, P, P, P, P, P, P, i32, u64, i32, u64, P]
+            L.or_rasterize.restype = ctypes.c_int
+            L.or_scatter.argtypes = [i64, P, P, i32, i64, i64, P]
+            L.or_scatter.restype = None
+            L.or_convolve_direct.argtypes = [P, i64, i64, P, i64, i64, P]
+            L.or_convolve_direct.restype = None
+            _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _plane_vec(plane) -> np.ndarray:
+    return np.array([plane.pitch_mm, plane.origin_mm, plane.wire_angle_rad, plane.tick_us,
+                     plane.t_window0_us, float(plane.n_impact_per_pitch)], dtype=np.float64)
+
+
+def _diff_vec(diff) -> np.ndarray:
+    return np.array([diff.DL_cm2_s, diff.DT_cm2_s, diff.v_drift_mm_us, diff.nsigma], dtype=np.float64)
+
+
+# ------------------------------------------------------------------------------------------
+# Philox / normals
+# ------------------------------------------------------------------------------------------
+
+def philox4x32_10(ctr: np.ndarray, key: Tuple[int, int]) -> np.ndarray:
+    """Philox4x32-10 of each 4-word counter row under one key (uint32 [n,4] -> [n,4])."""
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    k = np.array(key, dtype=np.uint32)
+    out = np.empty_like(ctr)
+    lib().or_philox_batch(ctr.shape[0], _p(ctr), _p(k), _p(out))
+    return out
+
+
+def bin_normal(seed: int, depo_index: int, tick: int, impact: int, n_imp: int, plane: int,
+               event_id: int) -> float:
+    """The fluctuation pool's normal deviate for one absolute (tick, impact) bin."""
+    return lib().or_bin_normal(seed, depo_index, tick, impact, n_imp, plane, event_id)
+
+
+def axis_weights(mu: float, s: float, nsigma: float = 3.0, cap: int = 4096):
+    """(lo, weights) of one axis: erf-difference bin integrals over the +-nsigma window."""
+    lo = ctypes.c_int64()
+    n = ctypes.c_int64()
+    w = np.zeros(cap, dtype=np.float64)
+    lib().or_axis_weights(mu, s, nsigma, ctypes.byref(lo), ctypes.byref(n), _p(w), cap)
+    if n.value > cap:
+        raise ValueError("window larger than cap")
+    return int(lo.value), w[: n.value].copy()
+
+
+# ------------------------------------------------------------------------------------------
+# Rasterize / scatter / convolve
+# ------------------------------------------------------------------------------------------
+
+class Patches:
+    """Oracle patches of one plane: desc [n,5] = (offset, lo_t, lo_p, n_t, n_p), values FP64."""
+
+    def __init__(self, desc, values, mus, n_invalid):
+        self.desc = desc
+        self.values = values
+        self.mus = mus
+        self.n_invalid = n_invalid
+
+    def patch(self, i: int) -> np.ndarray:
+        off, _, _, nt, npp = (int(v) for v in self.desc[i])
+        return self.values[off: off + nt * npp].reshape(nt, npp)
+
+
+def windows(depos, plane, diff, max_nt: int = MAX_NT, max_np: int = MAX_NP):
+    n = depos.n
+    desc = np.zeros((n, 5), dtype=np.int64)
+    mus = np.zeros((n, 4), dtype=np.float64)
+    total = ctypes.c_int64()
+    pv, dv = _plane_vec(plane), _diff_vec(diff)
+    bad = lib().or_windows(n, _p(depos.t0), _p(depos.x), _p(depos.y), _p(depos.z), _p(depos.q),
+                           _p(pv), _p(dv), max_nt, max_np, _p(desc), _p(mus), ctypes.byref(total))
+    return desc, mus, int(total.value), int(bad)
+
+
+def rasterize(depos, plane, diff, plane_index: int = 0, fluctuate: Optional[bool] = None,
+              max_nt: int = MAX_NT, max_np: int = MAX_NP) -> Patches:
+    """All patches of one plane in FP64 (the reading of §2's rasterization step)."""
+    desc, mus, total, bad = windows(depos, plane, diff, max_nt, max_np)
+    vals = np.zeros(max(total, 1), dtype=np.float64)
+    fl = diff.fluctuate if fluctuate is None else fluctuate
+    pv, dv = _plane_vec(plane), _diff_vec(diff)
+    rc = lib().or_rasterize(depos.n, _p(depos.t0), _p(depos.x), _p(depos.y), _p(depos.z),
+                            _p(depos.q), _p(pv), _p(dv), _p(desc), int(bool(fl)),
+                            int(diff.seed) & 0xFFFFFFFFFFFFFFFF, plane_index,
+                            int(depos.event_id), _p(vals))
+    if rc != 0:
+        raise RuntimeError(f"oracle rasterize failed ({rc})")
+    return Patches(desc, vals[:total], mus, bad)
+
+
+def scatter(patches: Patches, plane) -> np.ndarray:
+    """Scatter-add of the patches onto the plane's wire x tick grid (FP64)."""
+    grid = np.zeros((plane.n_wires, plane.n_ticks), dtype=np.float64)
+    vals = patches.values if patches.values.size else np.zeros(1)
+    lib().or_scatter(patches.desc.shape[0], _p(patches.desc), _p(vals), plane.n_impact_per_pitch,
+                     plane.n_wires, plane.n_ticks, _p(grid))
+    return grid
+
+
+def convolve_direct(grid: np.ndarray, resp: np.ndarray) -> np.ndarray:
+    """Literal quadruple-loop linear convolution in C (small grids only)."""
+    g = np.ascontiguousarray(grid, dtype=np.float64)
+    r = np.ascontiguousarray(resp, dtype=np.float64)
+    out = np.zeros_like(g)
+    lib().or_convolve_direct(_p(g), g.shape[0], g.shape[1], _p(r), r.shape[0], r.shape[1], _p(out))
+    return out
+
+
+def simulate_plane(depos, plane, diff, resp, plane_index: int = 0):
+    """Whole hot path for one plane: (patches, grid, waveform), all FP64."""
+    pt = rasterize(depos, plane, diff, plane_index)
+    grid = scatter(pt, plane)
+    wf = convolve_fft(grid, resp)
+    return pt, grid, wf
