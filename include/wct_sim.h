@@ -1,0 +1,212 @@
+/*
+ * wct_sim.h — C ABI of the GB300 (sm_103a) LArTPC signal-simulation hot path.
+ *
+ * The library implements the three steps of the Wire-Cell signal simulation described in
+ * arXiv 2304.01841, §2 ("LArTPC Signal Simulation in the Wire-Cell Toolkit"):
+ *   1. Rasterization: each drifted ionisation-electron group (a "depo") is binned into a
+ *      patch of O(20x20) time-tick x pitch-impact bins (§2, item 1);
+ *   2. Scatter-add: the patches are summed onto the plane's wire x tick grid (§2, item 2);
+ *   3. Convolution: the grid is convolved with the 2D detector response by FFT (§2, item 3).
+ * All three run in hand-written CUDA kernels; the caller owns the depo arrays, grids and
+ * waveforms (device memory), the library owns the response spectra and its scratch.
+ *
+ * Conventions shared by every entry point:
+ *  - Units: mm, microseconds, electrons.  Output waveforms are in (response units) x e-.
+ *  - Device pointers are CUDA global-memory addresses on the current device; host pointers
+ *    appear only where stated.  `stream` is a cudaStream_t (NULL = legacy default stream);
+ *    every call is asynchronous on it unless stated otherwise.
+ *  - Grids and waveforms are row-major float32 [n_wires][n_ticks] (ticks contiguous).
+ *  - Argument errors are detected on the host and returned before anything is launched.
+ *    Errors found by kernels (invalid depos, exceeded limits, timed-out waits) are recorded
+ *    in a device status word and returned by wct_sim_sync() (or the next synchronising
+ *    call).  The library never aborts, traps or exits; wct_sim_last_error() describes the
+ *    most recent failure.
+ *  - A handle is not thread-safe: use one handle per host thread or lock around it.
+ */
+#ifndef WCT_SIM_H
+#define WCT_SIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wct_sim wct_sim_t;   /* opaque, library-owned */
+
+typedef enum {
+    WCT_OK = 0,
+    WCT_EINVAL = 1,     /* bad argument, or (device) invalid depo / depo window over the limits */
+    WCT_ENOMEM = 2,     /* device allocation failed or would exceed the HBM budget */
+    WCT_ECUDA = 3,      /* a CUDA runtime call failed */
+    WCT_ETIMEOUT = 4,   /* a bounded device-side wait ran out */
+    WCT_EBUSY = 5,      /* the handle is in use (e.g. during graph capture) */
+    WCT_EDEVICE = 6     /* other device-side error */
+} wct_status_t;
+
+/* Largest depo window accepted (ticks x impact bins); a depo whose +-nsigma window is
+ * larger is invalid (skipped and reported as WCT_EINVAL by wct_sim_sync). */
+#define WCT_MAX_WINDOW_TICKS 128
+#define WCT_MAX_WINDOW_IMPACTS 512
+/* Largest response extent in wires (odd) handled by the wire stage. */
+#define WCT_MAX_RESPONSE_WIRES 21
+
+/*
+ * One wire plane (§2: the "larger grid that spans the longitudinal time and transverse
+ * space").  Wire w covers pitch coordinate [pitch_origin + w*pitch, +pitch); impact bin j
+ * covers [pitch_origin + j*pitch/n_impact_per_pitch, ...) and folds onto wire
+ * floor(j / n_impact_per_pitch).  Tick k covers [t_window0 + k*tick, +tick).  The pitch
+ * coordinate of a point is p = z*cos(wire_angle) + y*sin(wire_angle).
+ */
+typedef struct {
+    int32_t n_wires;
+    int32_t n_impact_per_pitch;
+    int32_t n_ticks;
+    double pitch_mm;
+    double pitch_origin_mm;
+    double wire_angle_rad;
+    double tick_us;
+    double t_window0_us;
+} wct_plane_t;
+
+/*
+ * Detector response of one plane (§2: "detector response with dimensions O(100x100)").
+ * host_data: HOST pointer, row-major float32 [n_wires_resp][n_ticks_resp]; row
+ * n_wires_resp/2 is the wire the charge arrives on, tick 0 is the arrival tick.
+ * n_wires_resp must be odd and <= WCT_MAX_RESPONSE_WIRES.  Copied at create.
+ */
+typedef struct {
+    int32_t n_wires_resp;
+    int32_t n_ticks_resp;
+    const float *host_data;
+} wct_response_t;
+
+/*
+ * Drift / diffusion / fluctuation (the standard LArTPC picture behind §2's "individual
+ * ionization electron groups"): drift time t_d = x / v_drift; longitudinal and transverse
+ * widths sqrt(2 D t_d); patches span +-nsigma.  fluctuate != 0 draws a binomial-like
+ * normal fluctuation per patch bin from a Philox4x32-10 stream keyed by `seed` (§4.1 names
+ * Random123's Philox family as the CPU RNG) and renormalises each patch to its charge.
+ */
+typedef struct {
+    double DL_cm2_s;
+    double DT_cm2_s;
+    double v_drift_mm_us;
+    double nsigma;
+    int32_t fluctuate;
+    uint64_t seed;
+} wct_diffusion_t;
+
+/*
+ * Library options.  hbm_budget_bytes: upper bound on the library's own device memory
+ * (0 = unlimited); a call whose scratch would exceed it returns WCT_ENOMEM.
+ * schedule_id: kernel-schedule choice (-1 = the library's default / tuned choice).
+ * deterministic: reserved (0).
+ */
+typedef struct {
+    size_t hbm_budget_bytes;
+    int32_t schedule_id;
+    int32_t deterministic;
+} wct_opts_t;
+
+/*
+ * One event's depos, structure of arrays in DEVICE memory (float32, n entries each):
+ * t0 (us), x (drift distance, mm, >= 0), y, z (mm), q (electrons, >= 0).  The depo's
+ * index in these arrays and event_id (low 24 bits) key its fluctuation counters.
+ */
+typedef struct {
+    const float *t0_us;
+    const float *x_mm;
+    const float *y_mm;
+    const float *z_mm;
+    const float *q_e;
+    int64_t n;
+    uint64_t event_id;
+} wct_depos_t;
+
+/* Create a simulator for n_planes planes (1..8), each with its own response.  Builds the
+ * FFT plans, uploads the responses and computes their spectra on the device (synchronous).
+ * opts may be NULL (defaults).  On success *out receives the handle. */
+wct_status_t wct_sim_create(const wct_plane_t *planes, int n_planes, const wct_response_t *responses,
+                            const wct_diffusion_t *diffusion, const wct_opts_t *opts, wct_sim_t **out);
+
+/* Free the handle and all library-owned device memory (synchronises the device). */
+wct_status_t wct_sim_destroy(wct_sim_t *sim);
+
+/*
+ * Rasterization alone (§2 step 1), writing every depo's full patch.
+ * patch_desc: DEVICE int64 [n][5] = {offset, lo_tick, lo_impact, n_ticks, n_impacts}; the
+ *   offsets are the exclusive prefix sum of the patch sizes (the paper's scan, §4.3).
+ *   Invalid depos get an empty window.
+ * total_bins: HOST int64, receives the patch-buffer size (this call synchronises `stream`
+ *   to read it back).
+ * patches: DEVICE float32 [capacity], row-major [tick][impact] per patch, or NULL to only
+ *   compute patch_desc / total_bins.  If total_bins > patches_capacity nothing is written
+ *   to patches and WCT_EINVAL is returned.
+ */
+wct_status_t wct_sim_rasterize(wct_sim_t *sim, int plane, const wct_depos_t *depos, float *patches,
+                               int64_t patches_capacity, int64_t *patch_desc, int64_t *total_bins,
+                               void *stream);
+
+/*
+ * Scatter-add onto the plane grid (§2 step 2).  grid: DEVICE float32 [n_wires][n_ticks],
+ * fully overwritten (no need to clear it).  With patches == NULL the patches are computed
+ * on the fly from `depos` (fused rasterize + scatter; patch_desc unused); otherwise
+ * `patches` / `patch_desc` from wct_sim_rasterize are summed.  Patch bins outside the grid
+ * are dropped.
+ */
+wct_status_t wct_sim_scatter(wct_sim_t *sim, int plane, const wct_depos_t *depos, const float *patches,
+                             const int64_t *patch_desc, float *grid, void *stream);
+
+/*
+ * Convolution with the plane's response (§2 step 3):
+ *   waveform[w][t] = sum_r sum_tau grid[w - (r - n_wires_resp/2)][t - tau] * resp[r][tau]
+ * (linear, grid zero outside its extent, output cropped to the grid).  grid and waveform
+ * are DEVICE float32 [n_wires][n_ticks] and may be the same buffer.
+ */
+wct_status_t wct_sim_convolve(wct_sim_t *sim, int plane, const float *grid, float *waveform, void *stream);
+
+/* The whole DepoTransform (§2, all three steps) for every plane of one event.
+ * waveforms: HOST array of n_planes DEVICE pointers, each float32 [n_wires][n_ticks]. */
+wct_status_t wct_sim_run_event(wct_sim_t *sim, const wct_depos_t *depos, float *const *waveforms,
+                               void *stream);
+
+/* Several events in one pass: events[e] for e < n_events; waveforms: HOST array of
+ * n_events * n_planes DEVICE pointers, event-major. */
+wct_status_t wct_sim_run_batch(wct_sim_t *sim, const wct_depos_t *events, int n_events,
+                               float *const *waveforms, void *stream);
+
+/* Synchronise `stream` and return (then clear) the device status word: WCT_OK, or the
+ * first device-side error since the last sync (WCT_EINVAL for invalid depos). */
+wct_status_t wct_sim_sync(wct_sim_t *sim, void *stream);
+
+/* Per-plane sizes: info[0..7] = {n_wires, n_ticks, fft_length, spectrum_bins,
+ * spectrum_row_stride, tile_wires, tile_ticks, n_tiles}.  Host call, no device work. */
+wct_status_t wct_sim_plane_info(const wct_sim_t *sim, int plane, int64_t *info);
+
+/* Stage timing with CUDA events recorded on the caller's stream inside run_event.
+ * wct_sim_set_timing(sim, 1) starts (and resets) the record; every following run_event adds
+ * one event set per plane.  wct_sim_stage_times waits for the recorded events and writes the
+ * mean per run_event call (summed over planes), in microseconds:
+ *   us[0] prep + binning, us[1] rasterize + scatter, us[2] forward row FFT,
+ *   us[3] wire stage, us[4] inverse row FFT; us[5] (if n > 5) = number of calls timed. */
+wct_status_t wct_sim_set_timing(wct_sim_t *sim, int enable);
+wct_status_t wct_sim_stage_times(wct_sim_t *sim, float *us, int n);
+
+/* Counters of this handle: out[0] = kernels launched so far, out[1] = bytes of device
+ * memory the library holds.  Host call, no device work. */
+wct_status_t wct_sim_counters(const wct_sim_t *sim, int64_t *out, int n);
+
+/* Human-readable description of the last error on this handle ("" if none). */
+const char *wct_sim_last_error(const wct_sim_t *sim);
+
+/* The Philox4x32-10 generator the fluctuation uses (Salmon et al., SC'11; §4.1 of the
+ * paper), exposed for testing: out[i] = Philox4x32-10(ctr[i], key) for i < n, where ctr
+ * and out are DEVICE uint32 [n][4] and key = (seed low word, seed high word). */
+wct_status_t wct_philox4x32_10(const uint32_t *ctr, uint64_t seed, int64_t n, uint32_t *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WCT_SIM_H */

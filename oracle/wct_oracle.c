@@ -128,7 +128,8 @@ double or_bin_normal(uint64_t seed, uint32_t depo_index, int64_t tick, int64_t i
  * A width below 1e-6 bin is a point charge: the single bin floor(mu) (an edge belongs to
  * the bin above it).
  * A depo is invalid (skipped, counted) if a coordinate or charge is not finite, x < 0,
- * q < 0, or its window exceeds max_nt ticks or max_np impact bins.
+ * q < 0, its window exceeds max_nt ticks or max_np impact bins, or the window starts more
+ * than 2^30 bins from the origin.
  * ------------------------------------------------------------------------------------- */
 typedef struct {
     double mu_t, s_t, mu_p, s_p;
@@ -176,9 +177,16 @@ static int depo_window(float t0f, float xf, float yf, float zf, float qf,
     double dp = pitch / n_imp;
     w->mu_p = (p - origin) / dp;
     w->s_p = sigT / dp;
+    const double big = 1099511627776.0;   /* 2^40 bins: keeps floor() within int64 */
+    if (!(fabs(w->mu_t) < big && fabs(w->mu_p) < big && w->s_t < big && w->s_p < big))
+        return -1;
     axis_window(w->mu_t, w->s_t, nsigma, &w->lo_t, &w->n_t);
     axis_window(w->mu_p, w->s_p, nsigma, &w->lo_p, &w->n_p);
     if (w->n_t > max_nt || w->n_p > max_np)
+        return -1;
+    /* windows more than 2^30 bins from the origin are outside any representable grid */
+    const int64_t lim = (int64_t)1 << 30;
+    if (w->lo_t < -lim || w->lo_t > lim || w->lo_p < -lim || w->lo_p > lim)
         return -1;
     return 0;
 }

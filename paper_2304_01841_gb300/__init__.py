@@ -1,0 +1,204 @@
+"""GB300-native LArTPC signal-simulation hot path (rasterize + scatter-add + FFT convolve).
+
+The arithmetic runs in the CUDA library built from csrc/ (C ABI in include/wct_sim.h); this
+package only marshals arguments to it.  PyTorch provides device memory and streams.
+
+    sim = Simulator(planes, responses, diffusion)
+    dep = DeviceDepos.from_host(depos)            # SoA float32 on the GPU
+    waveforms = sim.run_event(dep)                # one [n_wires, n_ticks] float32 per plane
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+from . import _abi
+from ._abi import WctError, load  # noqa: F401
+
+__all__ = ["Simulator", "DeviceDepos", "WctError", "load", "philox4x32_10"]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream=None) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _ptr(t) -> int:
+    return int(t.data_ptr()) if t is not None else 0
+
+
+@dataclass
+class DeviceDepos:
+    """One event's depos as device float32 arrays (t0 us, x/y/z mm, q electrons)."""
+    t0: "object"
+    x: "object"
+    y: "object"
+    z: "object"
+    q: "object"
+    event_id: int = 0
+
+    @property
+    def n(self) -> int:
+        return int(self.t0.numel())
+
+    @classmethod
+    def from_host(cls, d, device="cuda", non_blocking: bool = False) -> "DeviceDepos":
+        torch = _torch()
+        f = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32)).to(device, non_blocking=non_blocking)
+        return cls(f(d.t0), f(d.x), f(d.y), f(d.z), f(d.q), int(getattr(d, "event_id", 0)))
+
+    def c_struct(self) -> _abi.wct_depos_t:
+        for a in (self.t0, self.x, self.y, self.z, self.q):
+            if not (a.is_cuda and a.dtype == _torch().float32 and a.is_contiguous() and a.numel() == self.n):
+                raise ValueError("depo arrays must be contiguous float32 CUDA tensors of equal length")
+        return _abi.wct_depos_t(_ptr(self.t0), _ptr(self.x), _ptr(self.y), _ptr(self.z), _ptr(self.q),
+                                self.n, int(self.event_id))
+
+
+class Simulator:
+    """Owns one wct_sim handle (planes, responses, diffusion) on the current CUDA device."""
+
+    def __init__(self, planes: Sequence, responses: Sequence[np.ndarray], diffusion,
+                 hbm_budget_bytes: int = 0, schedule_id: int = -1):
+        self._lib = load()
+        self.planes = list(planes)
+        n = len(self.planes)
+        P = (_abi.wct_plane_t * n)()
+        for i, p in enumerate(self.planes):
+            P[i] = _abi.wct_plane_t(p.n_wires, p.n_impact_per_pitch, p.n_ticks, p.pitch_mm, p.origin_mm,
+                                    p.wire_angle_rad, p.tick_us, p.t_window0_us)
+        self._resp_keep = [np.ascontiguousarray(r, dtype=np.float32) for r in responses]
+        R = (_abi.wct_response_t * n)()
+        for i, r in enumerate(self._resp_keep):
+            R[i] = _abi.wct_response_t(r.shape[0], r.shape[1], r.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+        D = _abi.wct_diffusion_t(diffusion.DL_cm2_s, diffusion.DT_cm2_s, diffusion.v_drift_mm_us, diffusion.nsigma,
+                                 int(bool(diffusion.fluctuate)), int(diffusion.seed) & 0xFFFFFFFFFFFFFFFF)
+        O = _abi.wct_opts_t(int(hbm_budget_bytes), int(schedule_id), 0)
+        h = ctypes.c_void_p()
+        rc = self._lib.wct_sim_create(P, n, R, ctypes.byref(D), ctypes.byref(O), ctypes.byref(h))
+        if rc != 0:
+            raise WctError(rc, "wct_sim_create failed")
+        self._h = h
+        self.diffusion = diffusion
+
+    # -- helpers --------------------------------------------------------------------------
+    def _check(self, rc: int):
+        if rc != 0:
+            raise WctError(rc, self._lib.wct_sim_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.wct_sim_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def plane_info(self, plane: int) -> dict:
+        info = (ctypes.c_int64 * 8)()
+        self._check(self._lib.wct_sim_plane_info(self._h, plane, info))
+        keys = ("n_wires", "n_ticks", "fft_length", "spectrum_bins", "spectrum_row_stride", "tile_wires",
+                "tile_ticks", "n_tiles")
+        return dict(zip(keys, (int(v) for v in info)))
+
+    def _grid(self, plane: int, out=None):
+        torch = _torch()
+        p = self.planes[plane]
+        if out is None:
+            return torch.empty((p.n_wires, p.n_ticks), dtype=torch.float32, device="cuda")
+        if out.shape != (p.n_wires, p.n_ticks) or out.dtype != torch.float32 or not out.is_contiguous():
+            raise ValueError("grid / waveform must be contiguous float32 [n_wires, n_ticks]")
+        return out
+
+    # -- the ABI, one call each -----------------------------------------------------------
+    def rasterize(self, plane: int, depos: DeviceDepos, with_patches: bool = True, stream=None):
+        """wct_sim_rasterize: returns (patch_desc [n,5] int64, patches float32 or None)."""
+        torch = _torch()
+        desc = torch.empty((max(depos.n, 1), 5), dtype=torch.int64, device="cuda")
+        total = ctypes.c_int64()
+        ds = depos.c_struct()
+        sh = _stream_handle(stream)
+        self._check(self._lib.wct_sim_rasterize(self._h, plane, ctypes.byref(ds), None, 0, _ptr(desc),
+                                                ctypes.byref(total), sh))
+        if not with_patches:
+            return desc[: depos.n], None
+        patches = torch.empty(max(total.value, 1), dtype=torch.float32, device="cuda")
+        self._check(self._lib.wct_sim_rasterize(self._h, plane, ctypes.byref(ds), _ptr(patches), patches.numel(),
+                                                _ptr(desc), ctypes.byref(total), sh))
+        return desc[: depos.n], patches[: total.value]
+
+    def scatter(self, plane: int, depos: DeviceDepos, patches=None, patch_desc=None, out=None, stream=None):
+        """wct_sim_scatter: fused (patches None) or from given patches; returns the grid."""
+        grid = self._grid(plane, out)
+        ds = depos.c_struct()
+        self._check(self._lib.wct_sim_scatter(self._h, plane, ctypes.byref(ds), _ptr(patches), _ptr(patch_desc),
+                                              _ptr(grid), _stream_handle(stream)))
+        return grid
+
+    def convolve(self, plane: int, grid, out=None, stream=None):
+        """wct_sim_convolve: returns the waveform (may be `grid` itself if out is grid)."""
+        wf = self._grid(plane, out)
+        self._check(self._lib.wct_sim_convolve(self._h, plane, _ptr(grid), _ptr(wf), _stream_handle(stream)))
+        return wf
+
+    def run_event(self, depos: DeviceDepos, outs: Optional[List] = None, stream=None) -> List:
+        """wct_sim_run_event: all planes of one event; returns one waveform per plane."""
+        wfs = [self._grid(p, None if outs is None else outs[p]) for p in range(len(self.planes))]
+        arr = (ctypes.c_void_p * len(wfs))(*[_ptr(w) for w in wfs])
+        ds = depos.c_struct()
+        self._check(self._lib.wct_sim_run_event(self._h, ctypes.byref(ds), arr, _stream_handle(stream)))
+        return wfs
+
+    def run_batch(self, events: Sequence[DeviceDepos], outs: Optional[List[List]] = None, stream=None):
+        """wct_sim_run_batch: several events; returns [event][plane] waveforms."""
+        npl = len(self.planes)
+        wfs = [[self._grid(p, None if outs is None else outs[e][p]) for p in range(npl)] for e in range(len(events))]
+        arr = (ctypes.c_void_p * (len(events) * npl))(*[_ptr(w) for ev in wfs for w in ev])
+        evs = (_abi.wct_depos_t * max(len(events), 1))(*[e.c_struct() for e in events])
+        self._check(self._lib.wct_sim_run_batch(self._h, evs, len(events), arr, _stream_handle(stream)))
+        return wfs
+
+    def sync(self, stream=None):
+        """wct_sim_sync: wait for the stream and raise on a device-side error."""
+        self._check(self._lib.wct_sim_sync(self._h, _stream_handle(stream)))
+
+    def set_timing(self, enable: bool = True):
+        self._check(self._lib.wct_sim_set_timing(self._h, int(bool(enable))))
+
+    STAGES = ("prep_binning", "raster_scatter", "row_r2c", "wire_stage", "row_c2r")
+
+    def stage_times(self) -> dict:
+        """Mean microseconds per run_event of each stage since set_timing(True)."""
+        us = (ctypes.c_float * 6)()
+        self._check(self._lib.wct_sim_stage_times(self._h, us, 6))
+        out = dict(zip(self.STAGES, (float(v) for v in us[:5])))
+        out["events"] = int(us[5])
+        return out
+
+    def counters(self) -> dict:
+        c = (ctypes.c_int64 * 2)()
+        self._check(self._lib.wct_sim_counters(self._h, c, 2))
+        return {"kernel_launches": int(c[0]), "device_bytes": int(c[1])}
+
+
+def philox4x32_10(ctr, seed: int, stream=None):
+    """wct_philox4x32_10 on a [n,4] uint32-as-int32 CUDA tensor; returns [n,4] (int32 view)."""
+    torch = _torch()
+    out = torch.empty_like(ctr)
+    L = load()
+    rc = L.wct_philox4x32_10(_ptr(ctr), int(seed) & 0xFFFFFFFFFFFFFFFF, ctr.shape[0], _ptr(out), _stream_handle(stream))
+    if rc != 0:
+        raise WctError(rc, "wct_philox4x32_10 failed")
+    return out

@@ -1,0 +1,363 @@
+// Convolution with the detector response (paper §2, step 3: "the main computation here is
+// FFT").  The paper calls vendor FFT libraries (cuFFT / rocFFT / FFTW, §4.1); here the
+// transforms are hand-written:
+//
+//   k_row_r2c   one CTA per wire row: real FFT along ticks of the zero-padded row (length
+//               P = 2M, P >= n_ticks + n_resp_ticks - 1, 7-smooth), computed as a complex
+//               FFT of length M of the even/odd-packed row in shared memory (mixed-radix
+//               Stockham, radices 2,3,4,5,7,8, each stage staged through registers) plus the
+//               usual split into the M + 1 half-spectrum bins.
+//   k_wire_stage one thread per spectrum bin f and a run of wires: the convolution across
+//               wires is a 21-tap complex stencil per time frequency,
+//                   T[w, f] = sum_k S[w + 10 - k, f] * Rt[k, f],
+//               where Rt[k, f] is the time-spectrum of response row k (scaled by 1/M).  It is
+//               linear (zero outside the plane), so no FFT along wires and no 2D response
+//               spectrum is needed.
+//   k_row_c2r   one CTA per wire row: inverse of k_row_r2c, cropped to n_ticks.
+#include "wct_internal.cuh"
+#include "wct_device.cuh"
+
+namespace wct {
+
+namespace {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
+// multiply by +i (INV) or -i (forward): the sign of the transform's exponent times i
+template <bool INV>
+__device__ __forceinline__ float2 mul_si(float2 a) {
+    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// ---- small DFTs in registers: y_m = sum_n x_n exp(s 2 pi i n m / R), s = -1 forward ------
+template <int R, bool INV>
+struct Dft;
+
+template <bool INV>
+struct Dft<2, INV> {
+    __device__ __forceinline__ static void run(float2 *v) {
+        const float2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    }
+};
+
+template <bool INV>
+struct Dft<4, INV> {
+    __device__ __forceinline__ static void run(float2 *v) {
+        const float2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+        const float2 s13 = cadd(v[1], v[3]), d13 = mul_si<INV>(csub(v[1], v[3]));
+        v[0] = cadd(s02, s13);
+        v[2] = csub(s02, s13);
+        v[1] = cadd(d02, d13);
+        v[3] = csub(d02, d13);
+    }
+};
+
+template <bool INV>
+struct Dft<8, INV> {
+    __device__ __forceinline__ static void run(float2 *v) {
+        float2 e[4] = {v[0], v[2], v[4], v[6]};
+        float2 o[4] = {v[1], v[3], v[5], v[7]};
+        Dft<4, INV>::run(e);
+        Dft<4, INV>::run(o);
+        const float h = 0.7071067811865476f;
+        const float sg = INV ? 1.f : -1.f;
+        // twiddles exp(s 2 pi i k / 8), k = 1, 2, 3
+        o[1] = cmul(o[1], make_float2(h, sg * h));
+        o[2] = mul_si<INV>(o[2]);
+        o[3] = cmul(o[3], make_float2(-h, sg * h));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[k] = cadd(e[k], o[k]);
+            v[k + 4] = csub(e[k], o[k]);
+        }
+    }
+};
+
+// Odd R: pair x_n with x_{R-n}; y_m = x_0 + sum_n t_n cos(2 pi n m / R) + s i sum_n u_n sin(...)
+template <int R>
+struct OddTab;
+template <>
+struct OddTab<3> {
+    __device__ __forceinline__ static float c(int k) { return -0.5f; }
+    __device__ __forceinline__ static float s(int k) { return 0.8660254037844387f; }
+};
+template <>
+struct OddTab<5> {
+    __device__ __forceinline__ static float c(int k) { return k == 1 ? 0.30901699437494745f : -0.8090169943749473f; }
+    __device__ __forceinline__ static float s(int k) { return k == 1 ? 0.9510565162951535f : 0.5877852522924732f; }
+};
+template <>
+struct OddTab<7> {
+    __device__ __forceinline__ static float c(int k) {
+        return k == 1 ? 0.6234898018587336f : (k == 2 ? -0.22252093395631434f : -0.900968867902419f);
+    }
+    __device__ __forceinline__ static float s(int k) {
+        return k == 1 ? 0.7818314824680298f : (k == 2 ? 0.9749279121818236f : 0.43388373911755823f);
+    }
+};
+
+template <int R, bool INV>
+struct DftOdd {
+    __device__ __forceinline__ static void run(float2 *v) {
+        constexpr int H = (R - 1) / 2;
+        float2 t[H], u[H];
+#pragma unroll
+        for (int n = 1; n <= H; ++n) {
+            t[n - 1] = cadd(v[n], v[R - n]);
+            u[n - 1] = csub(v[n], v[R - n]);
+        }
+        float2 y0 = v[0];
+#pragma unroll
+        for (int n = 0; n < H; ++n) y0 = cadd(y0, t[n]);
+        float2 out[R];
+        out[0] = y0;
+#pragma unroll
+        for (int m = 1; m <= H; ++m) {
+            float2 a = v[0], b = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int n = 1; n <= H; ++n) {
+                const int k = (n * m) % R;                  // 1..R-1
+                const int kk = k <= H ? k : R - k;         // cos symmetric, sin antisymmetric
+                const float cs = OddTab<R>::c(kk);
+                const float sn = k <= H ? OddTab<R>::s(kk) : -OddTab<R>::s(kk);
+                a.x = fmaf(t[n - 1].x, cs, a.x);
+                a.y = fmaf(t[n - 1].y, cs, a.y);
+                b.x = fmaf(u[n - 1].x, sn, b.x);
+                b.y = fmaf(u[n - 1].y, sn, b.y);
+            }
+            const float2 ib = mul_si<INV>(b);
+            out[m] = cadd(a, ib);
+            out[R - m] = csub(a, ib);
+        }
+#pragma unroll
+        for (int m = 0; m < R; ++m) v[m] = out[m];
+    }
+};
+template <bool INV>
+struct Dft<3, INV> : DftOdd<3, INV> {};
+template <bool INV>
+struct Dft<5, INV> : DftOdd<5, INV> {};
+template <bool INV>
+struct Dft<7, INV> : DftOdd<7, INV> {};
+
+// One Stockham stage of radix R, out of place (in -> out).  With Ns = product of the radices
+// of the earlier stages, butterfly j (j < M/R) reads in[j + r M/R], applies the twiddles
+// exp(s 2 pi i r (j mod Ns) / (Ns R)), does a size-R DFT and writes out[(j div Ns) Ns R +
+// (j mod Ns) + r Ns].  One butterfly at a time per thread keeps register use at ~2R.
+template <int R, bool INV>
+__device__ __forceinline__ void fft_stage(const float2 *__restrict__ in, float2 *__restrict__ out, int M, int Ns,
+                                          const float2 *__restrict__ tw) {
+    const int nb = M / R;
+    const int stride = M / (Ns * R);
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+        const int k = j % Ns;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = in[j + r * nb];
+        if (Ns > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                float2 w = __ldg(&tw[r * k * stride]);
+                if (INV) w.y = -w.y;
+                v[r] = cmul(v[r], w);
+            }
+        }
+        Dft<R, INV>::run(v);
+        const int base = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) out[base + r * Ns] = v[r];
+    }
+    __syncthreads();
+}
+
+// Complex FFT of length M in shared memory, ping-ponging between a and b; returns the
+// buffer holding the result.
+template <bool INV>
+__device__ float2 *cta_fft(float2 *a, float2 *b, const FFTPlan &p) {
+    int Ns = 1;
+    for (int s = 0; s < p.n_stages; ++s) {
+        const int R = p.radix[s];
+        switch (R) {
+            case 2: fft_stage<2, INV>(a, b, p.M, Ns, p.tw); break;
+            case 3: fft_stage<3, INV>(a, b, p.M, Ns, p.tw); break;
+            case 4: fft_stage<4, INV>(a, b, p.M, Ns, p.tw); break;
+            case 5: fft_stage<5, INV>(a, b, p.M, Ns, p.tw); break;
+            case 7: fft_stage<7, INV>(a, b, p.M, Ns, p.tw); break;
+            default: fft_stage<8, INV>(a, b, p.M, Ns, p.tw); break;
+        }
+        float2 *t = a;
+        a = b;
+        b = t;
+        Ns *= R;
+    }
+    return a;
+}
+
+// ---- forward: real row -> half spectrum -------------------------------------------------
+__global__ void __launch_bounds__(512)
+k_row_r2c(FFTPlan p, const float *__restrict__ in, int64_t in_stride, int n_cols, float2 *__restrict__ spec) {
+    extern __shared__ float2 smem2[];
+    float2 *buf = smem2;
+    const int M = p.M;
+    const int row = blockIdx.x;
+    const float *src = in + (int64_t)row * in_stride;
+    const bool vec = ((in_stride & 1) == 0) && ((reinterpret_cast<uintptr_t>(in) & 7) == 0);
+    for (int n = threadIdx.x; n < M; n += blockDim.x) {
+        float2 v = make_float2(0.f, 0.f);
+        if (2 * n + 1 < n_cols) {
+            v = vec ? reinterpret_cast<const float2 *>(src)[n] : make_float2(src[2 * n], src[2 * n + 1]);
+        } else if (2 * n < n_cols) {
+            v.x = src[2 * n];
+        }
+        buf[n] = v;
+    }
+    __syncthreads();
+    const float2 *Z = cta_fft<false>(buf, smem2 + p.M, p);
+    // X[k] = (Z[k] + conj Z[M-k]) / 2 - i exp(-2 pi i k / P) (Z[k] - conj Z[M-k]) / 2
+    float2 *out = spec + (int64_t)row * p.Fs;
+    for (int k = threadIdx.x; k < p.Fs; k += blockDim.x) {
+        float2 X = make_float2(0.f, 0.f);
+        if (k <= M) {
+            const float2 a = Z[k == M ? 0 : k];
+            const float2 b = conjf2(Z[k == 0 ? 0 : M - k]);
+            const float2 wd = cmul(__ldg(&p.rtw[k]), csub(a, b));
+            const float2 s = cadd(a, b);
+            X = make_float2(0.5f * (s.x + wd.y), 0.5f * (s.y - wd.x));
+        }
+        out[k] = X;
+    }
+}
+
+// ---- inverse: half spectrum -> real row (cropped), unnormalised (scale lives in Rt) -----
+__global__ void __launch_bounds__(512)
+k_row_c2r(FFTPlan p, const float2 *__restrict__ spec, float *__restrict__ out, int64_t out_stride, int n_cols) {
+    extern __shared__ float2 smem2[];
+    float2 *buf = smem2;
+    const int M = p.M;
+    const int row = blockIdx.x;
+    const float2 *X = spec + (int64_t)row * p.Fs;
+    // E = (X[k] + conj X[M-k]) / 2, O = exp(2 pi i k / P) (X[k] - conj X[M-k]) / 2, Z = E + i O
+    for (int k = threadIdx.x; k < M; k += blockDim.x) {
+        const float2 a = X[k];
+        const float2 b = conjf2(X[M - k]);
+        const float2 O = cmul(conjf2(__ldg(&p.rtw[k])), csub(a, b));
+        const float2 s = cadd(a, b);
+        buf[k] = make_float2(0.5f * (s.x - O.y), 0.5f * (s.y + O.x));
+    }
+    __syncthreads();
+    const float2 *z = cta_fft<true>(buf, smem2 + p.M, p);
+    float *dst = out + (int64_t)row * out_stride;
+    const bool vec = ((out_stride & 1) == 0) && ((reinterpret_cast<uintptr_t>(out) & 7) == 0);
+    for (int n = threadIdx.x; 2 * n < n_cols; n += blockDim.x) {
+        const float2 v = z[n];
+        if (2 * n + 1 < n_cols) {
+            if (vec) {
+                reinterpret_cast<float2 *>(dst)[n] = v;
+            } else {
+                dst[2 * n] = v.x;
+                dst[2 * n + 1] = v.y;
+            }
+        } else {
+            dst[2 * n] = v.x;
+        }
+    }
+}
+
+// ---- wire stage: 21-tap complex stencil across wires per frequency ----------------------
+constexpr int KW = WCT_MAX_RESPONSE_WIRES;   // 21
+constexpr int KC = KW / 2;                   // 10
+constexpr int kStageThreads = 128;
+constexpr int kStageRun = 64;                // wires per thread
+
+__global__ void __launch_bounds__(kStageThreads)
+k_wire_stage(const float2 *__restrict__ S, const float2 *__restrict__ Rt, int Fs, int n_wires,
+             float2 *__restrict__ T) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= Fs) return;
+    const int w0 = blockIdx.y * kStageRun;
+    const int w1 = min(w0 + kStageRun, n_wires);
+    const int n_in = (w1 - w0) + 2 * KC;
+    float2 r[KW], acc[KW];
+#pragma unroll
+    for (int k = 0; k < KW; ++k) {
+        r[k] = Rt[(int64_t)k * Fs + f];
+        acc[k] = make_float2(0.f, 0.f);
+    }
+    // Input row s = w0 - KC + m contributes S[s] * Rt[k] to output w = s - KC + k, i.e. output
+    // index i = m - 2 KC + k, kept in accumulator slot i mod KW; output i is complete once
+    // m = i + 2 KC (k = 0) has been added.
+    for (int mb = 0; mb < n_in; mb += KW) {
+#pragma unroll
+        for (int u = 0; u < KW; ++u) {
+            const int m = mb + u;
+            if (m < n_in) {
+                const int s = w0 - KC + m;
+                float2 x = make_float2(0.f, 0.f);
+                if (s >= 0 && s < n_wires) x = S[(int64_t)s * Fs + f];
+#pragma unroll
+                for (int k = 0; k < KW; ++k) {
+                    const int slot = (u + 1 + k) % KW;
+                    acc[slot].x = fmaf(x.x, r[k].x, fmaf(-x.y, r[k].y, acc[slot].x));
+                    acc[slot].y = fmaf(x.x, r[k].y, fmaf(x.y, r[k].x, acc[slot].y));
+                }
+                const int done = (u + 1) % KW;
+                if (m >= 2 * KC) T[(int64_t)(w0 + m - 2 * KC) * Fs + f] = acc[done];
+                acc[done] = make_float2(0.f, 0.f);
+            }
+        }
+    }
+}
+
+__global__ void k_scale(float2 *__restrict__ a, int64_t n, float s) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = cscale(a[i], s);
+}
+
+int pick_threads(int M) { return M >= 2048 ? 512 : (M >= 512 ? 256 : 128); }
+
+}  // namespace
+
+cudaError_t launch_row_r2c(const FFTPlan &p, const float *in, int64_t in_stride, int n_in_cols, int n_rows,
+                           float2 *spec, cudaStream_t s) {
+    if (n_rows <= 0) return cudaSuccess;
+    const int T = pick_threads(p.M);
+    const size_t smem = 2 * sizeof(float2) * (size_t)p.M;
+    cudaError_t e = cudaFuncSetAttribute(k_row_r2c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_row_r2c<<<n_rows, T, smem, s>>>(p, in, in_stride, n_in_cols, spec);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_row_c2r(const FFTPlan &p, const float2 *spec, int n_rows, float *out, int64_t out_stride,
+                           int n_out_cols, cudaStream_t s) {
+    if (n_rows <= 0) return cudaSuccess;
+    const int T = pick_threads(p.M);
+    const size_t smem = 2 * sizeof(float2) * (size_t)p.M;
+    cudaError_t e = cudaFuncSetAttribute(k_row_c2r, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_row_c2r<<<n_rows, T, smem, s>>>(p, spec, out, out_stride, n_out_cols);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wire_stage(const FFTPlan &p, const float2 *spec, const float2 *resp_spec, int n_wires, float2 *out,
+                              cudaStream_t s) {
+    if (n_wires <= 0) return cudaSuccess;
+    dim3 grid((p.Fs + kStageThreads - 1) / kStageThreads, (n_wires + kStageRun - 1) / kStageRun);
+    k_wire_stage<<<grid, kStageThreads, 0, s>>>(spec, resp_spec, p.Fs, n_wires, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_spectrum(float2 *spec, int64_t n, float scale, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_scale<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(spec, n, scale);
+    return cudaGetLastError();
+}
+
+}  // namespace wct

@@ -1,0 +1,424 @@
+// Rasterization (+ fluctuation) and scatter-add (paper §2, steps 1 and 2).
+//
+// Fused path, k_tile_raster_scatter: one CTA owns one output tile of TW wires x TT ticks in
+// shared memory.  Its warps take the depos binned to the tile (a depo is binned to every
+// tile its window overlaps), compute each depo's erf-difference weights in per-warp shared
+// memory, evaluate the patch folded onto wires (the sum over a wire's impact sub-bins of the
+// fluctuated bin charges), and add the part that falls in the tile with shared-memory
+// atomics.  The tile is then written to the grid once with coalesced 16-byte stores: every
+// grid element is written exactly once per call, and no global atomics are used (the paper's
+// scatter-add relies on global atomic adds, §2 and §5.2).
+//
+// The fluctuation renormalises each patch to its charge over the depo's whole window, so a
+// depo that straddles tiles is evaluated in full by every tile it touches (only its in-tile
+// part is added).  Because rescaling is linear, the fold is taken on the unscaled fluctuated
+// charges and the scale q / sum is applied afterwards.
+//
+// Unfused path: k_rasterize_patches (one warp per depo) writes every depo's full patch,
+// k_tile_scatter_patches sums caller-supplied patches per tile.
+#include "wct_internal.cuh"
+#include "wct_device.cuh"
+
+namespace wct {
+
+namespace {
+
+constexpr int kTileWarps = 8;
+constexpr int kWT = WCT_MAX_WINDOW_TICKS + 1;                 // per-warp time weights (+1 edge)
+constexpr int kWBuf = kWT + WCT_MAX_WINDOW_IMPACTS + 1;       // per-warp weight buffer (floats)
+constexpr int kMaxItemsPerLane = 4;                           // register-cached fold items
+
+// Warp-cooperative 1D weights of one axis: w[i] = (erf(x_{i+1}) - erf(x_i)) / 2 with
+// x_i = (i - mu) * inv (window-relative bin edges), normalised to sum 1.  inv == 0 marks a
+// point charge (single bin of weight 1).  `w` has room for n + 1 entries.
+__device__ __forceinline__ void axis_weights(float *w, int n, float mu, float inv, int lane) {
+    if (inv == 0.f) {
+        if (lane == 0) w[0] = 1.f;
+        __syncwarp();
+        return;
+    }
+    for (int i = lane; i <= n; i += 32) w[i] = erff(((float)i - mu) * inv);
+    __syncwarp();
+    float part = 0.f;
+    for (int base = 0; base < n; base += 32) {
+        const int i = base + lane;
+        float v = 0.f;
+        if (i < n) v = 0.5f * (w[i + 1] - w[i]);
+        __syncwarp();
+        if (i < n) w[i] = v;
+        part += v;
+        __syncwarp();
+    }
+    const float inv_sum = 1.f / warp_sum(part);
+    for (int i = lane; i < n; i += 32) w[i] *= inv_sum;
+    __syncwarp();
+}
+
+// One (tick, wire) item of a depo's window folded onto wires.
+struct Item {
+    int a;          // window-relative tick
+    int tick;       // absolute tick
+    int wire;       // absolute wire
+    int sub_lo;     // first sub-bin of the wire inside the window
+    int sub_hi;     // one past the last
+    int j_base;     // window-relative impact index of sub-bin 0 of this wire
+};
+
+__device__ __forceinline__ Item make_item(int it, int nw, int wl, const DepoDesc &d, int n_imp) {
+    Item f;
+    f.a = it / nw;
+    f.wire = wl + (it - f.a * nw);
+    f.tick = d.lo_t + f.a;
+    const int first = f.wire * n_imp;                     // absolute impact of sub-bin 0
+    f.j_base = first - d.lo_p;
+    f.sub_lo = max(first, d.lo_p) - first;
+    f.sub_hi = min(first + n_imp, d.lo_p + (int)d.np) - first;
+    return f;
+}
+
+__device__ __forceinline__ float fold_plain(const Item &f, const float *wt, const float *wp, float q) {
+    float s = 0.f;
+    for (int sub = f.sub_lo; sub < f.sub_hi; ++sub) s += wp[f.j_base + sub];
+    return q * wt[f.a] * s;
+}
+
+// Fluctuated, not yet rescaled, folded charge of one item: the sum over the wire's sub-bins
+// in the window of max(0, q w + sqrt(q w (1 - w)) z), w = w_t * w_p.  z comes from the
+// counter-based pool: Philox4x32-10 of (depo, tick, wire * G + group, c3) under the key;
+// a call serves a group of four sub-bins, lanes 0/1 from the Box-Muller pair of words 0/1
+// and lanes 2/3 from words 2/3.
+__device__ __forceinline__ float fold_fluct(const Item &f, const float *wt, const float *wp, float q, uint32_t depo,
+                                            const PlaneParams &pp, uint32_t c3) {
+    const int G = (pp.n_imp + 3) >> 2;
+    const float wa = wt[f.a];
+    float acc = 0.f;
+    const int g0 = f.sub_lo >> 2, g1 = (f.sub_hi - 1) >> 2;
+    for (int g = g0; g <= g1; ++g) {
+        const uint4 x = philox4x32_10(
+            make_uint4(depo, (uint32_t)f.tick, (uint32_t)(f.wire * G + g), c3), pp.key0, pp.key1);
+        const int sb = g << 2;
+        const int l0 = max(f.sub_lo - sb, 0), l1 = min(f.sub_hi - sb, 4);   // lanes [l0, l1)
+        float z[4];
+        if (l0 < 2) {
+            const float2 p = box_muller(x.x, x.y);
+            z[0] = p.x;
+            z[1] = p.y;
+        }
+        if (l1 > 2) {
+            const float2 p = box_muller(x.z, x.w);
+            z[2] = p.x;
+            z[3] = p.y;
+        }
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            if (l >= l0 && l < l1) {
+                const float w = wa * wp[f.j_base + sb + l];
+                const float m = q * w;
+                const float v = fmaf(sqrtf(m * (1.f - w)), z[l], m);
+                acc += fmaxf(v, 0.f);
+            }
+        }
+    }
+    return acc;
+}
+
+__device__ __forceinline__ uint32_t counter_c3(const PlaneParams &pp, uint32_t event_lo) {
+    return ((uint32_t)pp.plane_index << 24) | (event_lo & 0xFFFFFFu);
+}
+
+// ------------------------------------------------------------------------------------------
+// Fused rasterize + fluctuate + fold + tile scatter.
+// ------------------------------------------------------------------------------------------
+template <int TW, int TT>
+__global__ void __launch_bounds__(kTileWarps * 32)
+k_tile_raster_scatter(const DepoDesc *__restrict__ desc, const int32_t *__restrict__ tile_off,
+                      const int32_t *__restrict__ tile_list, int64_t list_cap, PlaneParams pp, uint32_t event_lo,
+                      float *__restrict__ grid) {
+    extern __shared__ float4 smem4[];
+    float *tile = reinterpret_cast<float *>(smem4);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float *wt = tile + TW * TT + warp * kWBuf;
+    float *wp = wt + kWT;
+
+    const int tile_id = blockIdx.x;
+    const int tw = tile_id / pp.n_tiles_t;
+    const int tt = tile_id - tw * pp.n_tiles_t;
+    const int wire0 = tw * TW, tick0 = tt * TT;
+    const int wire_end = min(wire0 + TW, pp.n_wires), tick_end = min(tick0 + TT, pp.n_ticks);
+
+    for (int i = threadIdx.x; i < TW * TT / 4; i += blockDim.x) smem4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+
+    const uint32_t c3 = counter_c3(pp, event_lo);
+    const int beg = tile_off[tile_id];
+    const int end = (int)min((int64_t)tile_off[tile_id + 1], list_cap);
+    for (int li = beg + warp; li < end; li += kTileWarps) {
+        const int di = tile_list[li];
+        const DepoDesc d = desc[di];
+        const int nt = d.nt, np = d.np;
+        axis_weights(wt, nt, d.mu_t, d.inv_t, lane);
+        axis_weights(wp, np, d.mu_p, d.inv_p, lane);
+        const int wl = floor_div(d.lo_p, pp.n_imp);
+        const int nw = floor_div(d.lo_p + np - 1, pp.n_imp) - wl + 1;
+        const int items = nt * nw;
+        const float q = d.q;
+        auto deposit = [&](const Item &f, float v) {
+            if (f.wire >= wire0 && f.wire < wire_end && f.tick >= tick0 && f.tick < tick_end)
+                atomicAdd(&tile[(f.wire - wire0) * TT + (f.tick - tick0)], v);
+        };
+        if (!pp.fluctuate) {
+            for (int it = lane; it < items; it += 32) {
+                const Item f = make_item(it, nw, wl, d, pp.n_imp);
+                if (f.wire >= wire0 && f.wire < wire_end && f.tick >= tick0 && f.tick < tick_end)
+                    deposit(f, fold_plain(f, wt, wp, q));
+            }
+        } else {
+            float vals[kMaxItemsPerLane];
+            float part = 0.f;
+#pragma unroll
+            for (int k = 0; k < kMaxItemsPerLane; ++k) {
+                const int it = lane + 32 * k;
+                float v = 0.f;
+                if (it < items) v = fold_fluct(make_item(it, nw, wl, d, pp.n_imp), wt, wp, q, (uint32_t)di, pp, c3);
+                vals[k] = v;
+                part += v;
+            }
+            for (int it = lane + 32 * kMaxItemsPerLane; it < items; it += 32)
+                part += fold_fluct(make_item(it, nw, wl, d, pp.n_imp), wt, wp, q, (uint32_t)di, pp, c3);
+            const float total = warp_sum(part);
+            const bool keep = total > 0.f;
+            const float scale = keep ? q / total : 0.f;
+#pragma unroll
+            for (int k = 0; k < kMaxItemsPerLane; ++k) {
+                const int it = lane + 32 * k;
+                if (it < items) {
+                    const Item f = make_item(it, nw, wl, d, pp.n_imp);
+                    deposit(f, keep ? vals[k] * scale : fold_plain(f, wt, wp, q));
+                }
+            }
+            for (int it = lane + 32 * kMaxItemsPerLane; it < items; it += 32) {
+                const Item f = make_item(it, nw, wl, d, pp.n_imp);
+                if (f.wire >= wire0 && f.wire < wire_end && f.tick >= tick0 && f.tick < tick_end)
+                    deposit(f, keep ? fold_fluct(f, wt, wp, q, (uint32_t)di, pp, c3) * scale : fold_plain(f, wt, wp, q));
+            }
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+
+    // Write the whole tile once (zeros included): coalesced 16-byte stores along ticks.
+    const bool vec = ((pp.n_ticks & 3) == 0) && ((reinterpret_cast<uintptr_t>(grid) & 15) == 0);
+    for (int i = threadIdx.x; i < TW * TT / 4; i += blockDim.x) {
+        const int r = i / (TT / 4);
+        const int c = (i - r * (TT / 4)) * 4;
+        const int wire = wire0 + r, tick = tick0 + c;
+        if (wire >= wire_end || tick >= tick_end) continue;
+        float *dst = grid + (int64_t)wire * pp.n_ticks + tick;
+        const float4 v = smem4[i];
+        if (vec) {
+            *reinterpret_cast<float4 *>(dst) = v;
+        } else {
+            dst[0] = v.x;
+            if (tick + 1 < tick_end) dst[1] = v.y;
+            if (tick + 2 < tick_end) dst[2] = v.z;
+            if (tick + 3 < tick_end) dst[3] = v.w;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Unfused: full patches, one warp per depo (grid-stride).  Patch row-major [tick][impact].
+// ------------------------------------------------------------------------------------------
+constexpr int kPatchWarps = 8;
+
+__device__ __forceinline__ float bin_normal(const PlaneParams &pp, uint32_t depo, int tick, int impact, uint32_t c3) {
+    const int G = (pp.n_imp + 3) >> 2;
+    const int wire = floor_div(impact, pp.n_imp);
+    const int sub = impact - wire * pp.n_imp;
+    const int g = sub >> 2, l = sub & 3;
+    const uint4 x = philox4x32_10(make_uint4(depo, (uint32_t)tick, (uint32_t)(wire * G + g), c3), pp.key0, pp.key1);
+    const float2 p = (l < 2) ? box_muller(x.x, x.y) : box_muller(x.z, x.w);
+    return (l & 1) ? p.y : p.x;
+}
+
+__global__ void __launch_bounds__(kPatchWarps * 32)
+k_rasterize_patches(int64_t n, const DepoDesc *__restrict__ desc, const int64_t *__restrict__ offsets,
+                    PlaneParams pp, uint32_t event_lo, float *__restrict__ patches) {
+    __shared__ float wbuf[kPatchWarps][kWBuf];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float *wt = wbuf[warp];
+    float *wp = wt + kWT;
+    const uint32_t c3 = counter_c3(pp, event_lo);
+    const int64_t nwarps = (int64_t)gridDim.x * kPatchWarps;
+    for (int64_t di = (int64_t)blockIdx.x * kPatchWarps + warp; di < n; di += nwarps) {
+        const DepoDesc d = desc[di];
+        const int nt = d.nt, np = d.np;
+        if (nt == 0) continue;
+        axis_weights(wt, nt, d.mu_t, d.inv_t, lane);
+        axis_weights(wp, np, d.mu_p, d.inv_p, lane);
+        float *out = patches + offsets[di];
+        const int bins = nt * np;
+        const float q = d.q;
+        if (!pp.fluctuate) {
+            for (int b = lane; b < bins; b += 32) {
+                const int a = b / np, j = b - a * np;
+                out[b] = q * wt[a] * wp[j];
+            }
+        } else {
+            float part = 0.f;
+            for (int b = lane; b < bins; b += 32) {
+                const int a = b / np, j = b - a * np;
+                const float w = wt[a] * wp[j];
+                const float m = q * w;
+                const float z = bin_normal(pp, (uint32_t)di, d.lo_t + a, d.lo_p + j, c3);
+                const float v = fmaxf(fmaf(sqrtf(m * (1.f - w)), z, m), 0.f);
+                out[b] = v;
+                part += v;
+            }
+            const float total = warp_sum(part);
+            for (int b = lane; b < bins; b += 32) {   // same lane -> same bins as above
+                const int a = b / np, j = b - a * np;
+                out[b] = total > 0.f ? out[b] * (q / total) : q * wt[a] * wp[j];
+            }
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void k_write_patch_desc(int64_t n, const DepoDesc *__restrict__ desc, const int64_t *__restrict__ offsets,
+                                   int64_t *__restrict__ pd) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const DepoDesc d = desc[i];
+    int64_t *e = pd + 5 * i;
+    e[0] = offsets[i];
+    e[1] = d.lo_t;
+    e[2] = d.lo_p;
+    e[3] = d.nt;
+    e[4] = d.np;
+}
+
+// Scatter caller-supplied patches: CTA per tile, items (tick, wire) fold the patch row.
+template <int TW, int TT>
+__global__ void __launch_bounds__(kTileWarps * 32)
+k_tile_scatter_patches(const int64_t *__restrict__ pd, const float *__restrict__ patches,
+                       const int32_t *__restrict__ tile_off, const int32_t *__restrict__ tile_list, int64_t list_cap,
+                       PlaneParams pp, float *__restrict__ grid) {
+    extern __shared__ float4 smem4[];
+    float *tile = reinterpret_cast<float *>(smem4);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tile_id = blockIdx.x;
+    const int tw = tile_id / pp.n_tiles_t;
+    const int tt = tile_id - tw * pp.n_tiles_t;
+    const int wire0 = tw * TW, tick0 = tt * TT;
+    const int wire_end = min(wire0 + TW, pp.n_wires), tick_end = min(tick0 + TT, pp.n_ticks);
+    for (int i = threadIdx.x; i < TW * TT / 4; i += blockDim.x) smem4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    const int beg = tile_off[tile_id];
+    const int end = (int)min((int64_t)tile_off[tile_id + 1], list_cap);
+    for (int li = beg + warp; li < end; li += kTileWarps) {
+        const int di = tile_list[li];
+        const int64_t *e = pd + 5 * (int64_t)di;
+        const int64_t off = e[0];
+        DepoDesc d;
+        d.lo_t = (int32_t)e[1];
+        d.lo_p = (int32_t)e[2];
+        d.nt = (int16_t)e[3];
+        d.np = (int16_t)e[4];
+        const int nt = d.nt, np = d.np;
+        const int wl = floor_div(d.lo_p, pp.n_imp);
+        const int nw = floor_div(d.lo_p + np - 1, pp.n_imp) - wl + 1;
+        const int items = nt * nw;
+        for (int it = lane; it < items; it += 32) {
+            const Item f = make_item(it, nw, wl, d, pp.n_imp);
+            if (f.wire >= wire0 && f.wire < wire_end && f.tick >= tick0 && f.tick < tick_end) {
+                const float *row = patches + off + (int64_t)f.a * np + f.j_base;
+                float s = 0.f;
+                for (int sub = f.sub_lo; sub < f.sub_hi; ++sub) s += row[sub];
+                atomicAdd(&tile[(f.wire - wire0) * TT + (f.tick - tick0)], s);
+            }
+        }
+    }
+    __syncthreads();
+    const bool vec = ((pp.n_ticks & 3) == 0) && ((reinterpret_cast<uintptr_t>(grid) & 15) == 0);
+    for (int i = threadIdx.x; i < TW * TT / 4; i += blockDim.x) {
+        const int r = i / (TT / 4);
+        const int c = (i - r * (TT / 4)) * 4;
+        const int wire = wire0 + r, tick = tick0 + c;
+        if (wire >= wire_end || tick >= tick_end) continue;
+        float *dst = grid + (int64_t)wire * pp.n_ticks + tick;
+        const float4 v = smem4[i];
+        if (vec) {
+            *reinterpret_cast<float4 *>(dst) = v;
+        } else {
+            dst[0] = v.x;
+            if (tick + 1 < tick_end) dst[1] = v.y;
+            if (tick + 2 < tick_end) dst[2] = v.z;
+            if (tick + 3 < tick_end) dst[3] = v.w;
+        }
+    }
+}
+
+__global__ void k_philox(const uint32_t *__restrict__ ctr, uint32_t k0, uint32_t k1, int64_t n,
+                         uint32_t *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint4 c = reinterpret_cast<const uint4 *>(ctr)[i];
+    reinterpret_cast<uint4 *>(out)[i] = philox4x32_10(c, k0, k1);
+}
+
+constexpr int kTileW = 32, kTileT = 256;
+
+size_t tile_smem_bytes() { return sizeof(float) * ((size_t)kTileW * kTileT + (size_t)kTileWarps * kWBuf); }
+
+}  // namespace
+
+int tile_wires() { return kTileW; }
+int tile_ticks() { return kTileT; }
+
+cudaError_t launch_tile_raster_scatter(const DepoDesc *desc, const int32_t *tile_off, const int32_t *tile_list,
+                                       int64_t list_cap, const PlaneParams &pp, uint32_t event_lo, float *grid,
+                                       cudaStream_t s) {
+    const int n_tiles = pp.n_tiles_w * pp.n_tiles_t;
+    if (n_tiles <= 0) return cudaSuccess;
+    const size_t smem = tile_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(k_tile_raster_scatter<kTileW, kTileT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_tile_raster_scatter<kTileW, kTileT><<<n_tiles, kTileWarps * 32, smem, s>>>(desc, tile_off, tile_list, list_cap,
+                                                                                 pp, event_lo, grid);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rasterize_patches(int64_t n, const DepoDesc *desc, const int64_t *offsets, const PlaneParams &pp,
+                                     uint32_t event_lo, float *patches, int64_t *patch_desc, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    if (patch_desc) {
+        k_write_patch_desc<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, desc, offsets, patch_desc);
+    }
+    if (patches) {
+        int64_t blocks = (n + kPatchWarps - 1) / kPatchWarps;
+        if (blocks > 152 * 16) blocks = 152 * 16;
+        k_rasterize_patches<<<(unsigned)blocks, kPatchWarps * 32, 0, s>>>(n, desc, offsets, pp, event_lo, patches);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tile_scatter_patches(const int64_t *patch_desc, const float *patches, const int32_t *tile_off,
+                                        const int32_t *tile_list, int64_t list_cap, const PlaneParams &pp, float *grid,
+                                        cudaStream_t s) {
+    const int n_tiles = pp.n_tiles_w * pp.n_tiles_t;
+    if (n_tiles <= 0) return cudaSuccess;
+    const size_t smem = sizeof(float) * (size_t)kTileW * kTileT;
+    k_tile_scatter_patches<kTileW, kTileT><<<n_tiles, kTileWarps * 32, smem, s>>>(patch_desc, patches, tile_off,
+                                                                                  tile_list, list_cap, pp, grid);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, int64_t n, uint32_t *out, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_philox<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ctr, k0, k1, n, out);
+    return cudaGetLastError();
+}
+
+}  // namespace wct

@@ -1,0 +1,82 @@
+// Internal declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/wct_sim.h"
+
+namespace wct {
+
+// ------------------------------------------------------------------------------------------
+// Per-depo descriptor produced by the prep kernel (32 bytes, two float4 loads).
+//   mu_t / mu_p : centre relative to the window's first bin, in bin units (FP64 -> FP32)
+//   inv_t/inv_p : 1 / (sqrt(2) sigma) in 1/bin, 0 for a point charge
+//   lo_t / lo_p : first window bin (absolute tick / impact bin)
+//   nt / np     : window extent; nt == 0 marks an invalid or empty depo
+// ------------------------------------------------------------------------------------------
+struct __align__(16) DepoDesc {
+    float mu_t, mu_p, inv_t, inv_p;
+    float q;
+    int32_t lo_t, lo_p;
+    int16_t nt, np;
+};
+static_assert(sizeof(DepoDesc) == 32, "DepoDesc must stay 32 bytes");
+
+// Geometry / physics constants of one plane, FP64 where the window is decided.
+struct PlaneParams {
+    double pitch, origin, cos_a, sin_a, tick, tw0, dp;   // dp = pitch / n_imp
+    double DL, DT, v, nsigma;                            // DL, DT in mm^2/us
+    int32_t n_imp, n_wires, n_ticks, plane_index;
+    int32_t fluctuate;
+    uint32_t key0, key1;
+    int32_t tile_w, tile_t, n_tiles_w, n_tiles_t;
+};
+
+// Device status word codes (same values as wct_status_t).
+enum : int32_t { ST_OK = 0, ST_EINVAL = 1, ST_ETIMEOUT = 4, ST_EDEVICE = 6 };
+
+// Radix plan of a complex FFT of length M = fft_length / 2 (Stockham, radices 2..8).
+struct FFTPlan {
+    int32_t M;            // complex length
+    int32_t n_stages;
+    int32_t radix[12];
+    int32_t fft_len;      // real length P = 2M
+    int32_t F;            // spectrum bins = M + 1
+    int32_t Fs;           // spectrum row stride (complex elements), even
+    float2 *tw;           // device: exp(-2 pi i k / M), k < M
+    float2 *rtw;          // device: exp(-2 pi i k / P), k <= M
+};
+
+// ---- launchers (stream-ordered; return cudaError_t of the launch) -------------------------
+cudaError_t launch_prep(const wct_depos_t &d, const PlaneParams &pp, DepoDesc *desc, int32_t *tile_count,
+                        int64_t *patch_size, int32_t *status, cudaStream_t s);
+cudaError_t launch_fill(int64_t n, const DepoDesc *desc, const PlaneParams &pp, const int32_t *tile_off,
+                        int32_t *tile_cursor, int32_t *tile_list, int64_t list_cap, int32_t *status, cudaStream_t s);
+cudaError_t launch_scan_i32(const int32_t *in, int32_t *out, int64_t n, int32_t *tmp, cudaStream_t s);
+cudaError_t launch_scan_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *tmp, cudaStream_t s);
+int64_t scan_tmp_elems(int64_t n);
+
+cudaError_t launch_tile_raster_scatter(const DepoDesc *desc, const int32_t *tile_off, const int32_t *tile_list,
+                                       int64_t list_cap, const PlaneParams &pp, uint32_t event_lo, float *grid,
+                                       cudaStream_t s);
+cudaError_t launch_rasterize_patches(int64_t n, const DepoDesc *desc, const int64_t *offsets, const PlaneParams &pp,
+                                     uint32_t event_lo, float *patches, int64_t *patch_desc, cudaStream_t s);
+cudaError_t launch_bin_patches(int64_t n, const int64_t *patch_desc, const PlaneParams &pp, int32_t *tile_count,
+                               int32_t *status, cudaStream_t s);
+cudaError_t launch_fill_patches(int64_t n, const int64_t *patch_desc, const PlaneParams &pp, const int32_t *tile_off,
+                                int32_t *tile_cursor, int32_t *tile_list, int64_t list_cap, int32_t *status,
+                                cudaStream_t s);
+cudaError_t launch_tile_scatter_patches(const int64_t *patch_desc, const float *patches, const int32_t *tile_off,
+                                        const int32_t *tile_list, int64_t list_cap, const PlaneParams &pp, float *grid,
+                                        cudaStream_t s);
+
+cudaError_t launch_row_r2c(const FFTPlan &p, const float *in, int64_t in_stride, int n_in_cols, int n_rows,
+                           float2 *spec, cudaStream_t s);
+cudaError_t launch_wire_stage(const FFTPlan &p, const float2 *spec, const float2 *resp_spec, int n_wires,
+                              float2 *out, cudaStream_t s);
+cudaError_t launch_row_c2r(const FFTPlan &p, const float2 *spec, int n_rows, float *out, int64_t out_stride,
+                           int n_out_cols, cudaStream_t s);
+cudaError_t launch_scale_spectrum(float2 *spec, int64_t n, float scale, cudaStream_t s);
+cudaError_t launch_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, int64_t n, uint32_t *out, cudaStream_t s);
+
+}  // namespace wct

@@ -1,0 +1,557 @@
+// Host runtime and C ABI: handle, FFT plans, response spectra, scratch under an HBM budget,
+// and the stream-ordered sequence of kernels for each entry point of include/wct_sim.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <new>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "wct_internal.cuh"
+
+namespace wct {
+int tile_wires();
+int tile_ticks();
+}  // namespace wct
+
+using namespace wct;
+
+namespace {
+
+constexpr int kMaxPlanes = 8;
+constexpr int kStages = 5;        // prep + binning, raster-scatter, row r2c, wire stage, row c2r
+constexpr int kMaxSlots = 4096;
+constexpr int kMaxM = 14336;   // largest complex FFT length: two M-point buffers in one CTA's shared memory
+
+struct PlaneState {
+    wct_plane_t g{};
+    PlaneParams pp{};
+    FFTPlan fft{};
+    float2 *resp_spec = nullptr;   // [WCT_MAX_RESPONSE_WIRES][Fs], scaled by 1/M
+    int n_tiles = 0;
+    int max_tiles_per_depo = 0;
+};
+
+}  // namespace
+
+struct wct_sim {
+    int device = 0;
+    int n_planes = 0;
+    PlaneState planes[kMaxPlanes];
+    wct_diffusion_t diff{};
+    wct_opts_t opts{};
+    // scratch
+    float2 *spec = nullptr, *spec2 = nullptr;
+    DepoDesc *desc = nullptr;
+    int64_t *patch_size = nullptr, *patch_off = nullptr, *scan64 = nullptr;
+    int64_t depo_cap = 0;
+    int32_t *tile_count = nullptr, *tile_off = nullptr, *tile_cursor = nullptr, *scan32 = nullptr;
+    int32_t *tile_list = nullptr;
+    int64_t list_cap = 0;
+    int32_t *status = nullptr;
+    size_t bytes = 0;
+    std::vector<void *> allocs;
+    std::string err;
+    // stage timing: one slot of kStages + 1 events per (run_event call, plane)
+    bool timing = false;
+    std::vector<std::array<cudaEvent_t, kStages + 1>> slots;
+    int slots_used = 0;
+    int events_timed = 0;
+    int64_t launches = 0;   // kernels launched by this handle
+};
+
+namespace {
+
+wct_status_t fail(wct_sim *s, wct_status_t code, const std::string &msg) {
+    if (s) s->err = msg;
+    return code;
+}
+
+wct_status_t cuda_fail(wct_sim *s, cudaError_t e, const char *where) {
+    return fail(s, WCT_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+wct_status_t dev_alloc(wct_sim *s, void **p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (s->opts.hbm_budget_bytes && s->bytes + bytes > s->opts.hbm_budget_bytes)
+        return fail(s, WCT_ENOMEM, "scratch would exceed the HBM budget");
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(s, WCT_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    s->bytes += bytes;
+    s->allocs.push_back(*p);
+    return WCT_OK;
+}
+
+void dev_free(wct_sim *s, void *p, size_t bytes) {
+    if (!p) return;
+    cudaFree(p);
+    s->bytes -= bytes;
+    for (auto &a : s->allocs)
+        if (a == p) a = nullptr;
+}
+
+bool smooth7(int64_t m) {
+    for (int p : {2, 3, 5, 7})
+        while (m % p == 0) m /= p;
+    return m == 1;
+}
+
+// FFT length: the smallest even P >= n_ticks + n_resp_ticks - 1 with P / 2 7-smooth, so
+// the circular convolution of length P equals the linear one on the kept ticks.
+bool plan_fft(int n_ticks, int kt, FFTPlan &p) {
+    const int64_t need = (int64_t)n_ticks + kt - 1;
+    int64_t M = (need + 1) / 2;
+    while (!smooth7(M)) ++M;
+    if (M > kMaxM) return false;
+    p.M = (int32_t)M;
+    p.fft_len = (int32_t)(2 * M);
+    p.F = (int32_t)(M + 1);
+    p.Fs = (int32_t)((M + 2) & ~1LL);
+    int64_t r = M;
+    int ns = 0;
+    const int order[] = {8, 4, 7, 5, 3, 2};
+    for (int rad : order) {
+        while (r % rad == 0) {
+            if (ns >= 12) return false;
+            p.radix[ns++] = rad;
+            r /= rad;
+        }
+    }
+    p.n_stages = ns;
+    return r == 1;
+}
+
+wct_status_t upload_twiddles(wct_sim *s, FFTPlan &p) {
+    std::vector<float2> tw(p.M), rtw(p.M + 1);
+    const double pi = 3.14159265358979323846;
+    for (int k = 0; k < p.M; ++k) {
+        const double a = -2.0 * pi * (double)k / (double)p.M;
+        tw[k] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+    for (int k = 0; k <= p.M; ++k) {
+        const double a = -2.0 * pi * (double)k / (double)p.fft_len;
+        rtw[k] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+    wct_status_t st = dev_alloc(s, (void **)&p.tw, sizeof(float2) * tw.size());
+    if (st) return st;
+    st = dev_alloc(s, (void **)&p.rtw, sizeof(float2) * rtw.size());
+    if (st) return st;
+    cudaError_t e = cudaMemcpy(p.tw, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p.rtw, rtw.data(), sizeof(float2) * rtw.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(s, e, "twiddle upload");
+    return WCT_OK;
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+wct_status_t check_depos(wct_sim *s, const wct_depos_t *d) {
+    if (!d) return fail(s, WCT_EINVAL, "depos is NULL");
+    if (d->n < 0) return fail(s, WCT_EINVAL, "negative depo count");
+    if (d->n > (int64_t)1 << 30) return fail(s, WCT_EINVAL, "more than 2^30 depos in one call");
+    if (d->n > 0 && (!d->t0_us || !d->x_mm || !d->y_mm || !d->z_mm || !d->q_e))
+        return fail(s, WCT_EINVAL, "a depo array pointer is NULL");
+    return WCT_OK;
+}
+
+wct_status_t ensure_depo_capacity(wct_sim *s, int64_t n) {
+    if (n <= s->depo_cap) return WCT_OK;
+    int64_t cap = n < 1024 ? 1024 : n;
+    if (s->depo_cap) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_fail(s, e, "sync before scratch growth");
+        dev_free(s, s->desc, sizeof(DepoDesc) * s->depo_cap);
+        dev_free(s, s->patch_size, sizeof(int64_t) * s->depo_cap);
+        dev_free(s, s->patch_off, sizeof(int64_t) * (s->depo_cap + 1));
+        dev_free(s, s->scan64, sizeof(int64_t) * scan_tmp_elems(s->depo_cap));
+        dev_free(s, s->tile_list, sizeof(int32_t) * s->list_cap);
+        s->desc = nullptr;
+        s->patch_size = s->patch_off = s->scan64 = nullptr;
+        s->tile_list = nullptr;
+        s->depo_cap = 0;
+        s->list_cap = 0;
+    }
+    int per = 1;
+    for (int p = 0; p < s->n_planes; ++p) per = std::max(per, s->planes[p].max_tiles_per_depo);
+    wct_status_t st;
+    if ((st = dev_alloc(s, (void **)&s->desc, sizeof(DepoDesc) * cap))) return st;
+    if ((st = dev_alloc(s, (void **)&s->patch_size, sizeof(int64_t) * cap))) return st;
+    if ((st = dev_alloc(s, (void **)&s->patch_off, sizeof(int64_t) * (cap + 1)))) return st;
+    if ((st = dev_alloc(s, (void **)&s->scan64, sizeof(int64_t) * scan_tmp_elems(cap)))) return st;
+    if ((st = dev_alloc(s, (void **)&s->tile_list, sizeof(int32_t) * cap * per))) return st;
+    s->depo_cap = cap;
+    s->list_cap = cap * per;
+    return WCT_OK;
+}
+
+PlaneParams plane_params(const wct_sim *s, int p) {
+    PlaneParams pp = s->planes[p].pp;
+    return pp;
+}
+
+wct_status_t plane_check(wct_sim *s, int plane) {
+    if (!s) return WCT_EINVAL;
+    if (plane < 0 || plane >= s->n_planes) return fail(s, WCT_EINVAL, "plane index out of range");
+    return WCT_OK;
+}
+
+// Index of a fresh timing slot (events created on first use), or -1 when not timing.
+int acquire_slot(wct_sim *s) {
+    if (!s->timing) return -1;
+    if (s->slots_used >= kMaxSlots) return -1;
+    if (s->slots_used == (int)s->slots.size()) {
+        std::array<cudaEvent_t, kStages + 1> ev{};
+        for (auto &e : ev)
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                cudaGetLastError();
+                return -1;
+            }
+        s->slots.push_back(ev);
+    }
+    return s->slots_used++;
+}
+
+void mark(wct_sim *s, int slot, int k, cudaStream_t st) {
+    if (slot >= 0) cudaEventRecord(s->slots[slot][k], st);
+}
+
+// Fused rasterize + scatter of one plane into `grid`.
+wct_status_t raster_scatter(wct_sim *s, int plane, const wct_depos_t *d, float *grid, cudaStream_t st, int slot) {
+    const PlaneState &ps = s->planes[plane];
+    const PlaneParams pp = plane_params(s, plane);
+    cudaError_t e = cudaMemsetAsync(s->tile_count, 0, sizeof(int32_t) * (ps.n_tiles + 1), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->tile_cursor, 0, sizeof(int32_t) * (ps.n_tiles + 1), st);
+    if (e == cudaSuccess) e = launch_prep(*d, pp, s->desc, s->tile_count, nullptr, s->status, st);
+    if (e == cudaSuccess) e = launch_scan_i32(s->tile_count, s->tile_off, ps.n_tiles, s->scan32, st);
+    if (e == cudaSuccess)
+        e = launch_fill(d->n, s->desc, pp, s->tile_off, s->tile_cursor, s->tile_list, s->list_cap, s->status, st);
+    if (e != cudaSuccess) return cuda_fail(s, e, "prep / binning");
+    mark(s, slot, 1, st);
+    e = launch_tile_raster_scatter(s->desc, s->tile_off, s->tile_list, s->list_cap, pp, (uint32_t)d->event_id, grid,
+                                   st);
+    if (e != cudaSuccess) return cuda_fail(s, e, "tile raster-scatter");
+    s->launches += 4 + (d->n > 0 ? 2 : 0);
+    mark(s, slot, 2, st);
+    return WCT_OK;
+}
+
+wct_status_t convolve_plane(wct_sim *s, int plane, const float *grid, float *wf, cudaStream_t st, int slot) {
+    const PlaneState &ps = s->planes[plane];
+    const int nw = ps.g.n_wires, nt = ps.g.n_ticks;
+    cudaError_t e = launch_row_r2c(ps.fft, grid, nt, nt, nw, s->spec, st);
+    if (e != cudaSuccess) return cuda_fail(s, e, "row r2c");
+    mark(s, slot, 3, st);
+    e = launch_wire_stage(ps.fft, s->spec, ps.resp_spec, nw, s->spec2, st);
+    if (e != cudaSuccess) return cuda_fail(s, e, "wire stage");
+    mark(s, slot, 4, st);
+    e = launch_row_c2r(ps.fft, s->spec2, nw, wf, nt, nt, st);
+    if (e != cudaSuccess) return cuda_fail(s, e, "row c2r");
+    s->launches += 3;
+    mark(s, slot, 5, st);
+    return WCT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+wct_status_t wct_sim_create(const wct_plane_t *planes, int n_planes, const wct_response_t *responses,
+                            const wct_diffusion_t *diffusion, const wct_opts_t *opts, wct_sim_t **out) {
+    if (!out) return WCT_EINVAL;
+    *out = nullptr;
+    if (!planes || !responses || !diffusion || n_planes < 1 || n_planes > kMaxPlanes) return WCT_EINVAL;
+    const wct_diffusion_t &df = *diffusion;
+    if (!finite_pos(df.v_drift_mm_us) || !std::isfinite(df.DL_cm2_s) || df.DL_cm2_s < 0 ||
+        !std::isfinite(df.DT_cm2_s) || df.DT_cm2_s < 0 || !finite_pos(df.nsigma))
+        return WCT_EINVAL;
+    for (int p = 0; p < n_planes; ++p) {
+        const wct_plane_t &g = planes[p];
+        const wct_response_t &r = responses[p];
+        if (g.n_wires < 1 || g.n_ticks < 1 || g.n_impact_per_pitch < 1 || g.n_impact_per_pitch > 4096) return WCT_EINVAL;
+        if (!finite_pos(g.pitch_mm) || !finite_pos(g.tick_us) || !std::isfinite(g.pitch_origin_mm) ||
+            !std::isfinite(g.wire_angle_rad) || !std::isfinite(g.t_window0_us))
+            return WCT_EINVAL;
+        if ((int64_t)g.n_wires * g.n_ticks > ((int64_t)1 << 31)) return WCT_EINVAL;
+        if (!r.host_data || r.n_wires_resp < 1 || (r.n_wires_resp & 1) == 0 ||
+            r.n_wires_resp > WCT_MAX_RESPONSE_WIRES || r.n_ticks_resp < 1 || r.n_ticks_resp > 65536)
+            return WCT_EINVAL;
+    }
+    wct_sim *s = new (std::nothrow) wct_sim();
+    if (!s) return WCT_ENOMEM;
+    cudaGetDevice(&s->device);
+    s->n_planes = n_planes;
+    s->diff = df;
+    if (opts) {
+        s->opts = *opts;
+    } else {
+        s->opts.hbm_budget_bytes = 0;
+        s->opts.schedule_id = -1;
+        s->opts.deterministic = 0;
+    }
+    wct_status_t st = WCT_OK;
+    size_t spec_elems = 0;
+    int max_tiles = 1;
+    for (int p = 0; p < n_planes && st == WCT_OK; ++p) {
+        PlaneState &ps = s->planes[p];
+        ps.g = planes[p];
+        const wct_plane_t &g = planes[p];
+        PlaneParams &pp = ps.pp;
+        pp.pitch = g.pitch_mm;
+        pp.origin = g.pitch_origin_mm;
+        pp.cos_a = std::cos(g.wire_angle_rad);
+        pp.sin_a = std::sin(g.wire_angle_rad);
+        pp.tick = g.tick_us;
+        pp.tw0 = g.t_window0_us;
+        pp.dp = g.pitch_mm / (double)g.n_impact_per_pitch;
+        pp.DL = df.DL_cm2_s * 1.0e-4;   // cm^2/s -> mm^2/us
+        pp.DT = df.DT_cm2_s * 1.0e-4;
+        pp.v = df.v_drift_mm_us;
+        pp.nsigma = df.nsigma;
+        pp.n_imp = g.n_impact_per_pitch;
+        pp.n_wires = g.n_wires;
+        pp.n_ticks = g.n_ticks;
+        pp.plane_index = p;
+        pp.fluctuate = df.fluctuate ? 1 : 0;
+        pp.key0 = (uint32_t)(df.seed & 0xFFFFFFFFu);
+        pp.key1 = (uint32_t)(df.seed >> 32);
+        pp.tile_w = tile_wires();
+        pp.tile_t = tile_ticks();
+        pp.n_tiles_w = (g.n_wires + pp.tile_w - 1) / pp.tile_w;
+        pp.n_tiles_t = (g.n_ticks + pp.tile_t - 1) / pp.tile_t;
+        ps.n_tiles = pp.n_tiles_w * pp.n_tiles_t;
+        max_tiles = std::max(max_tiles, ps.n_tiles);
+        const int max_wires = (WCT_MAX_WINDOW_IMPACTS - 1) / g.n_impact_per_pitch + 2;
+        const int tw_max = (max_wires + pp.tile_w - 2) / pp.tile_w + 1;
+        const int tt_max = (WCT_MAX_WINDOW_TICKS + pp.tile_t - 2) / pp.tile_t + 1;
+        ps.max_tiles_per_depo = tw_max * tt_max;
+        if (!plan_fft(g.n_ticks, responses[p].n_ticks_resp, ps.fft)) {
+            st = fail(s, WCT_EINVAL, "no FFT plan for this tick count (too long)");
+            break;
+        }
+        st = upload_twiddles(s, ps.fft);
+        spec_elems = std::max(spec_elems, (size_t)g.n_wires * ps.fft.Fs);
+    }
+    if (st == WCT_OK) st = dev_alloc(s, (void **)&s->spec, sizeof(float2) * spec_elems);
+    if (st == WCT_OK) st = dev_alloc(s, (void **)&s->spec2, sizeof(float2) * spec_elems);
+    if (st == WCT_OK) st = dev_alloc(s, (void **)&s->tile_count, sizeof(int32_t) * (max_tiles + 1));
+    if (st == WCT_OK) st = dev_alloc(s, (void **)&s->tile_off, sizeof(int32_t) * (max_tiles + 1));
+    if (st == WCT_OK) st = dev_alloc(s, (void **)&s->tile_cursor, sizeof(int32_t) * (max_tiles + 1));
+    if (st == WCT_OK) st = dev_alloc(s, (void **)&s->scan32, sizeof(int32_t) * scan_tmp_elems(max_tiles + 1));
+    if (st == WCT_OK) st = dev_alloc(s, (void **)&s->status, sizeof(int32_t));
+    if (st == WCT_OK) {
+        cudaError_t e = cudaMemset(s->status, 0, sizeof(int32_t));
+        if (e != cudaSuccess) st = cuda_fail(s, e, "status init");
+    }
+    // Response spectra: pad each response to 21 centred rows, real-FFT the rows along ticks
+    // with the same transform as the grid, and fold the inverse transform's 1/M into them.
+    for (int p = 0; p < n_planes && st == WCT_OK; ++p) {
+        PlaneState &ps = s->planes[p];
+        const wct_response_t &r = responses[p];
+        const int KW = WCT_MAX_RESPONSE_WIRES;
+        const int off = (KW - r.n_wires_resp) / 2;
+        std::vector<float> pad((size_t)KW * r.n_ticks_resp, 0.f);
+        for (int row = 0; row < r.n_wires_resp; ++row)
+            std::memcpy(&pad[(size_t)(row + off) * r.n_ticks_resp], r.host_data + (size_t)row * r.n_ticks_resp,
+                        sizeof(float) * r.n_ticks_resp);
+        float *d_resp = nullptr;
+        st = dev_alloc(s, (void **)&d_resp, sizeof(float) * pad.size());
+        if (st == WCT_OK) st = dev_alloc(s, (void **)&ps.resp_spec, sizeof(float2) * (size_t)KW * ps.fft.Fs);
+        if (st != WCT_OK) break;
+        cudaError_t e = cudaMemcpy(d_resp, pad.data(), sizeof(float) * pad.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = launch_row_r2c(ps.fft, d_resp, r.n_ticks_resp, r.n_ticks_resp, KW, ps.resp_spec, 0);
+        if (e == cudaSuccess)
+            e = launch_scale_spectrum(ps.resp_spec, (int64_t)KW * ps.fft.Fs, 1.0f / (float)ps.fft.M, 0);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        dev_free(s, d_resp, sizeof(float) * pad.size());
+        if (e != cudaSuccess) st = cuda_fail(s, e, "response spectrum");
+    }
+    if (st != WCT_OK) {
+        for (void *a : s->allocs)
+            if (a) cudaFree(a);
+        delete s;
+        return st;
+    }
+    *out = s;
+    return WCT_OK;
+}
+
+wct_status_t wct_sim_destroy(wct_sim_t *s) {
+    if (!s) return WCT_EINVAL;
+    cudaDeviceSynchronize();
+    for (void *a : s->allocs)
+        if (a) cudaFree(a);
+    for (auto &slot : s->slots)
+        for (auto &e : slot) cudaEventDestroy(e);
+    delete s;
+    return WCT_OK;
+}
+
+wct_status_t wct_sim_rasterize(wct_sim_t *s, int plane, const wct_depos_t *d, float *patches, int64_t capacity,
+                               int64_t *patch_desc, int64_t *total_bins, void *stream) {
+    wct_status_t st = plane_check(s, plane);
+    if (st) return st;
+    if ((st = check_depos(s, d))) return st;
+    if (!patch_desc || !total_bins) return fail(s, WCT_EINVAL, "patch_desc and total_bins are required");
+    cudaStream_t cs = (cudaStream_t)stream;
+    if ((st = ensure_depo_capacity(s, d->n))) return st;
+    const PlaneParams pp = plane_params(s, plane);
+    cudaError_t e = launch_prep(*d, pp, s->desc, nullptr, s->patch_size, s->status, cs);
+    if (e == cudaSuccess) e = launch_scan_i64(s->patch_size, s->patch_off, d->n, s->scan64, cs);
+    int64_t total = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&total, s->patch_off + d->n, sizeof(int64_t), cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) return cuda_fail(s, e, "rasterize sizing");
+    *total_bins = total;
+    const bool write = patches && total <= capacity;
+    e = launch_rasterize_patches(d->n, s->desc, s->patch_off, pp, (uint32_t)d->event_id, write ? patches : nullptr,
+                                 patch_desc, cs);
+    if (e != cudaSuccess) return cuda_fail(s, e, "rasterize");
+    s->launches += (d->n > 0 ? 3 : 0) + 3 + (write && d->n > 0 ? 1 : 0);
+    if (patches && !write) return fail(s, WCT_EINVAL, "patch buffer smaller than total_bins");
+    return WCT_OK;
+}
+
+wct_status_t wct_sim_scatter(wct_sim_t *s, int plane, const wct_depos_t *d, const float *patches,
+                             const int64_t *patch_desc, float *grid, void *stream) {
+    wct_status_t st = plane_check(s, plane);
+    if (st) return st;
+    if ((st = check_depos(s, d))) return st;
+    if (!grid) return fail(s, WCT_EINVAL, "grid is NULL");
+    cudaStream_t cs = (cudaStream_t)stream;
+    if ((st = ensure_depo_capacity(s, d->n))) return st;
+    if (!patches) return raster_scatter(s, plane, d, grid, cs, -1);
+    if (!patch_desc) return fail(s, WCT_EINVAL, "patch_desc is required with patches");
+    const PlaneState &ps = s->planes[plane];
+    const PlaneParams pp = plane_params(s, plane);
+    cudaError_t e = cudaMemsetAsync(s->tile_count, 0, sizeof(int32_t) * (ps.n_tiles + 1), cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->tile_cursor, 0, sizeof(int32_t) * (ps.n_tiles + 1), cs);
+    if (e == cudaSuccess) e = launch_bin_patches(d->n, patch_desc, pp, s->tile_count, s->status, cs);
+    if (e == cudaSuccess) e = launch_scan_i32(s->tile_count, s->tile_off, ps.n_tiles, s->scan32, cs);
+    if (e == cudaSuccess)
+        e = launch_fill_patches(d->n, patch_desc, pp, s->tile_off, s->tile_cursor, s->tile_list, s->list_cap,
+                                s->status, cs);
+    if (e == cudaSuccess)
+        e = launch_tile_scatter_patches(patch_desc, patches, s->tile_off, s->tile_list, s->list_cap, pp, grid, cs);
+    if (e != cudaSuccess) return cuda_fail(s, e, "scatter patches");
+    s->launches += 4 + (d->n > 0 ? 2 : 0);
+    return WCT_OK;
+}
+
+wct_status_t wct_sim_convolve(wct_sim_t *s, int plane, const float *grid, float *wf, void *stream) {
+    wct_status_t st = plane_check(s, plane);
+    if (st) return st;
+    if (!grid || !wf) return fail(s, WCT_EINVAL, "grid / waveform is NULL");
+    return convolve_plane(s, plane, grid, wf, (cudaStream_t)stream, -1);
+}
+
+wct_status_t wct_sim_run_event(wct_sim_t *s, const wct_depos_t *d, float *const *wfs, void *stream) {
+    if (!s) return WCT_EINVAL;
+    wct_status_t st = check_depos(s, d);
+    if (st) return st;
+    if (!wfs) return fail(s, WCT_EINVAL, "waveforms is NULL");
+    for (int p = 0; p < s->n_planes; ++p)
+        if (!wfs[p]) return fail(s, WCT_EINVAL, "a waveform pointer is NULL");
+    if ((st = ensure_depo_capacity(s, d->n))) return st;
+    cudaStream_t cs = (cudaStream_t)stream;
+    for (int p = 0; p < s->n_planes; ++p) {
+        const int slot = acquire_slot(s);
+        mark(s, slot, 0, cs);
+        if ((st = raster_scatter(s, p, d, wfs[p], cs, slot))) return st;
+        if ((st = convolve_plane(s, p, wfs[p], wfs[p], cs, slot))) return st;
+    }
+    if (s->timing) ++s->events_timed;
+    return WCT_OK;
+}
+
+wct_status_t wct_sim_run_batch(wct_sim_t *s, const wct_depos_t *events, int n_events, float *const *wfs,
+                               void *stream) {
+    if (!s) return WCT_EINVAL;
+    if (n_events < 0 || (n_events > 0 && (!events || !wfs))) return fail(s, WCT_EINVAL, "bad batch arguments");
+    for (int e = 0; e < n_events; ++e) {
+        wct_status_t st = wct_sim_run_event(s, &events[e], wfs + (size_t)e * s->n_planes, stream);
+        if (st) return st;
+    }
+    return WCT_OK;
+}
+
+wct_status_t wct_sim_sync(wct_sim_t *s, void *stream) {
+    if (!s) return WCT_EINVAL;
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "stream sync");
+    int32_t code = 0;
+    e = cudaMemcpy(&code, s->status, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(s->status, 0, sizeof(int32_t));
+    if (e != cudaSuccess) return cuda_fail(s, e, "status read");
+    if (code == ST_EINVAL) return fail(s, WCT_EINVAL, "invalid depo(s) skipped (non-finite, x<0, q<0 or window too large)");
+    if (code == ST_ETIMEOUT) return fail(s, WCT_ETIMEOUT, "a device-side wait timed out");
+    if (code != 0) return fail(s, WCT_EDEVICE, "device-side error");
+    return WCT_OK;
+}
+
+wct_status_t wct_sim_plane_info(const wct_sim_t *s, int plane, int64_t *info) {
+    if (!s || !info || plane < 0 || plane >= s->n_planes) return WCT_EINVAL;
+    const PlaneState &ps = s->planes[plane];
+    info[0] = ps.g.n_wires;
+    info[1] = ps.g.n_ticks;
+    info[2] = ps.fft.fft_len;
+    info[3] = ps.fft.F;
+    info[4] = ps.fft.Fs;
+    info[5] = ps.pp.tile_w;
+    info[6] = ps.pp.tile_t;
+    info[7] = ps.n_tiles;
+    return WCT_OK;
+}
+
+wct_status_t wct_sim_set_timing(wct_sim_t *s, int enable) {
+    if (!s) return WCT_EINVAL;
+    s->timing = enable != 0;
+    s->slots_used = 0;
+    s->events_timed = 0;
+    return WCT_OK;
+}
+
+wct_status_t wct_sim_stage_times(wct_sim_t *s, float *us, int n) {
+    if (!s || !us || n < 0) return WCT_EINVAL;
+    double acc[kStages] = {0, 0, 0, 0, 0};
+    for (int k = 0; k < s->slots_used; ++k) {
+        auto &ev = s->slots[k];
+        cudaError_t e = cudaEventSynchronize(ev[kStages]);
+        if (e != cudaSuccess) return cuda_fail(s, e, "stage events");
+        for (int j = 0; j < kStages; ++j) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ev[j], ev[j + 1]) == cudaSuccess) acc[j] += 1000.0 * ms;
+            else cudaGetLastError();
+        }
+    }
+    const double div = s->events_timed > 0 ? (double)s->events_timed : 1.0;
+    for (int j = 0; j < n && j < kStages; ++j) us[j] = (float)(acc[j] / div);
+    if (n > kStages) us[kStages] = (float)s->events_timed;
+    return WCT_OK;
+}
+
+wct_status_t wct_sim_counters(const wct_sim_t *s, int64_t *out, int n) {
+    if (!s || !out || n < 0) return WCT_EINVAL;
+    if (n > 0) out[0] = s->launches;
+    if (n > 1) out[1] = (int64_t)s->bytes;
+    return WCT_OK;
+}
+
+const char *wct_sim_last_error(const wct_sim_t *s) { return s ? s->err.c_str() : "null handle"; }
+
+wct_status_t wct_philox4x32_10(const uint32_t *ctr, uint64_t seed, int64_t n, uint32_t *out, void *stream) {
+    if (n < 0 || (n > 0 && (!ctr || !out))) return WCT_EINVAL;
+    if (((uintptr_t)ctr & 15) || ((uintptr_t)out & 15)) return WCT_EINVAL;
+    cudaError_t e = launch_philox(ctr, (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32), n, out,
+                                  (cudaStream_t)stream);
+    return e == cudaSuccess ? WCT_OK : WCT_ECUDA;
+}
+
+}  // extern "C"

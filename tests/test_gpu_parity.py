@@ -1,0 +1,275 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances (stated by the hot-path contract, FP32 on the GPU vs FP64 in the oracle):
+  window descriptors          bit-exact (integers decided in FP64 on both sides)
+  Philox words                bit-exact
+  patch and grid bins         |gpu - oracle| <= 1e-5 * max |oracle bin|
+  waveforms                   relative L2 <= 1e-4
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import BIN_TOL, WAVE_RTOL, make_sim, max_rel_bin, rel_l2, to_np
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2304_01841_gb300 as g
+    g.load(build_if_missing=True)
+
+
+def _dev(d):
+    import paper_2304_01841_gb300 as g
+    return g.DeviceDepos.from_host(d)
+
+
+# ------------------------------------------------------------------------------------------
+def test_philox_bit_exact():
+    import paper_2304_01841_gb300 as g
+    rng = np.random.default_rng(0)
+    ctr = rng.integers(0, 2**32, size=(4096, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[:4] = [[0, 0, 0, 0], [0xFFFFFFFF] * 4, [1, 2, 3, 4], [0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344]]
+    for seed in (0, 1, 0xA4093822299F31D0, 20230406):
+        want = oracle.philox4x32_10(ctr, (seed & 0xFFFFFFFF, seed >> 32))
+        got = g.philox4x32_10(torch.from_numpy(ctr.view(np.int32)).cuda(), seed)
+        torch.cuda.synchronize()
+        assert np.array_equal(to_np(got).view(np.uint32), want)
+
+
+# ------------------------------------------------------------------------------------------
+def _patch_parity(wl_name, fluct, n=None, diffusion=None, plane=None):
+    wl = synth.workload(wl_name)
+    pl = plane or wl.planes[0]
+    df = diffusion or synth.Diffusion(fluctuate=fluct, seed=777)
+    d = wl.depos(n_depos=n)
+    sim = make_sim([pl], [synth.make_response(pl.response_kind)], df)
+    desc, patches = sim.rasterize(0, _dev(d))
+    sim.sync()
+    ref = oracle.rasterize(d, pl, df)
+    assert np.array_equal(to_np(desc), ref.desc)
+    assert patches.numel() == ref.values.size
+    err = max_rel_bin(to_np(patches), ref.values)
+    assert err <= BIN_TOL, err
+    return sim, d, ref
+
+
+@pytest.mark.parametrize("fluct", [False, True])
+def test_patches_tiny(fluct):
+    _patch_parity("tiny", fluct)
+
+
+def test_patches_full_uboone_plane_fluct():
+    _patch_parity("uboone_plane", True)
+
+
+@pytest.mark.parametrize("fluct", [False, True])
+def test_fused_grid_matches_oracle_and_unfused(fluct):
+    wl = synth.workload("tiny")
+    pl = wl.planes[0]
+    df = synth.Diffusion(fluctuate=fluct, seed=4242)
+    d = wl.depos()
+    sim = make_sim([pl], wl.responses(), df)
+    dd = _dev(d)
+    grid = sim.scatter(0, dd)
+    desc, patches = sim.rasterize(0, dd)
+    grid2 = sim.scatter(0, dd, patches=patches, patch_desc=desc)
+    sim.sync()
+    ref = oracle.scatter(oracle.rasterize(d, pl, df), pl)
+    assert max_rel_bin(to_np(grid), ref) <= BIN_TOL
+    assert max_rel_bin(to_np(grid2), ref) <= BIN_TOL
+
+
+def test_fused_grid_full_uboone_plane():
+    wl = synth.workload("uboone_plane")
+    pl = wl.planes[0]
+    d = wl.depos()
+    sim = make_sim(wl.planes, wl.responses(), wl.diffusion)
+    grid = sim.scatter(0, _dev(d))
+    sim.sync()
+    ref = oracle.scatter(oracle.rasterize(d, pl, wl.diffusion), pl)
+    assert max_rel_bin(to_np(grid), ref) <= BIN_TOL
+    assert abs(float(grid.double().sum()) - ref.sum()) <= 1e-5 * ref.sum()
+
+
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("shape,kind", [((256, 1024), "bipolar"), ((3456, 9600), "bipolar"),
+                                        ((37, 1000), "unipolar"), ((5, 203), "bipolar")])
+def test_convolve_random_grid(shape, kind):
+    nw, nt = shape
+    pl = synth.Plane(nw, nt, response_kind=kind)
+    resp = synth.make_response(kind)
+    sim = make_sim([pl], [resp], synth.Diffusion())
+    g = np.random.default_rng(nw + nt).normal(size=shape).astype(np.float32)
+    out = sim.convolve(0, torch.from_numpy(g).cuda())
+    sim.sync()
+    ref = oracle.convolve_fft(g, resp, workers=4)
+    assert rel_l2(to_np(out), ref) <= WAVE_RTOL
+
+
+def test_convolve_small_response_and_in_place():
+    pl = synth.Plane(64, 500)
+    resp = np.random.default_rng(3).normal(size=(5, 37)).astype(np.float32)
+    sim = make_sim([pl], [resp], synth.Diffusion())
+    g = np.random.default_rng(4).normal(size=(64, 500)).astype(np.float32)
+    buf = torch.from_numpy(g.copy()).cuda()
+    sim.convolve(0, buf, out=buf)          # in place
+    sim.sync()
+    ref = oracle.convolve_direct(g, resp)
+    assert rel_l2(to_np(buf), ref) <= WAVE_RTOL
+
+
+def test_convolve_delta_response_is_identity():
+    pl = synth.Plane(40, 777)
+    resp = np.zeros((21, 200), np.float32)
+    resp[10, 0] = 1.0
+    sim = make_sim([pl], [resp], synth.Diffusion())
+    g = np.random.default_rng(5).normal(size=(40, 777)).astype(np.float32)
+    out = sim.convolve(0, torch.from_numpy(g).cuda())
+    sim.sync()
+    assert np.abs(to_np(out) - g).max() <= 1e-5 * np.abs(g).max()
+
+
+# ------------------------------------------------------------------------------------------
+def _event_parity(wl, d, check_grid=True):
+    sim = make_sim(wl.planes, wl.responses(), wl.diffusion)
+    dd = _dev(d)
+    wfs = sim.run_event(dd)
+    sim.sync()
+    for p, pl in enumerate(wl.planes):
+        pt, grid, wf = oracle.simulate_plane(d, pl, wl.diffusion, wl.responses()[p], plane_index=p)
+        err = rel_l2(to_np(wfs[p]), wf)
+        assert err <= WAVE_RTOL, (p, err)
+        if check_grid:
+            g = sim.scatter(p, dd)
+            sim.sync()
+            assert max_rel_bin(to_np(g), grid) <= BIN_TOL
+    return sim
+
+
+def test_event_tiny():
+    wl = synth.workload("tiny")
+    _event_parity(wl, wl.depos())
+
+
+def test_event_full_uboone_plane():
+    # the configuration the benchmark times: 3456 x 9600, 100k depos, fluctuation on
+    wl = synth.workload("uboone_plane")
+    _event_parity(wl, wl.depos())
+
+
+def test_event_three_plane_reduced():
+    # all three planes (angles +-60 deg, bipolar / unipolar), 100k depos of the 1M recipe
+    wl = synth.workload("three_plane")
+    _event_parity(wl, wl.depos(n_depos=100_000))
+
+
+# ------------------------------------------------------------------------------------------
+# Edge cases
+# ------------------------------------------------------------------------------------------
+def test_empty_event_gives_zero_waveforms():
+    wl = synth.workload("tiny")
+    sim = make_sim(wl.planes, wl.responses(), wl.diffusion)
+    d = wl.depos().subset(slice(0, 0))
+    wfs = sim.run_event(_dev(d), outs=[torch.full((256, 1024), 7.0, device="cuda")])
+    sim.sync()
+    assert float(wfs[0].abs().max()) == 0.0
+
+
+def test_invalid_depos_are_reported_and_skipped():
+    import paper_2304_01841_gb300 as g
+    wl = synth.workload("tiny")
+    pl = wl.planes[0]
+    d = wl.depos(n_depos=200)
+    d.x[5] = -1.0
+    d.q[9] = np.nan
+    d.x[11] = 1e7            # window far beyond the limits
+    sim = make_sim([pl], wl.responses(), wl.diffusion)
+    grid = sim.scatter(0, _dev(d))
+    with pytest.raises(g.WctError) as ei:
+        sim.sync()
+    assert ei.value.code == 1
+    sim.sync()               # status was cleared
+    ref_pt = oracle.rasterize(d, pl, wl.diffusion)
+    assert ref_pt.n_invalid == 3
+    assert max_rel_bin(to_np(grid), oracle.scatter(ref_pt, pl)) <= BIN_TOL
+
+
+@pytest.mark.parametrize("n_imp,nw,nt", [(7, 50, 1000), (10, 33, 257), (1, 40, 300), (4, 64, 513)])
+def test_ragged_geometry_and_fluctuation(n_imp, nw, nt):
+    pl = synth.Plane(nw, nt, n_impact_per_pitch=n_imp, pitch_mm=3.0)
+    df = synth.Diffusion(fluctuate=True, seed=99)
+    rng = np.random.default_rng(nw * nt)
+    n = 600
+    half = 0.5 * nw * 3.0
+    d = synth.Depos(np.zeros(n), rng.uniform(0, nt * 0.8, n), np.zeros(n), rng.uniform(-half - 20, half + 20, n),
+                    rng.lognormal(8.0, 0.5, n))
+    resp = synth.make_response("bipolar")
+    sim = make_sim([pl], [resp], df)
+    dd = _dev(d)
+    desc, patches = sim.rasterize(0, dd)
+    grid = sim.scatter(0, dd)
+    wf = sim.run_event(dd)[0]
+    sim.sync()
+    ref = oracle.rasterize(d, pl, df)
+    assert np.array_equal(to_np(desc), ref.desc)
+    assert max_rel_bin(to_np(patches), ref.values) <= BIN_TOL
+    g_ref = oracle.scatter(ref, pl)
+    assert max_rel_bin(to_np(grid), g_ref) <= BIN_TOL
+    assert rel_l2(to_np(wf), oracle.convolve_fft(g_ref, resp)) <= WAVE_RTOL
+
+
+def test_wide_windows_and_point_charges():
+    # large diffusion makes windows near the limits (many items per lane); x = 0 depos are
+    # point charges; some depos sit exactly on bin edges
+    pl = synth.Plane(120, 2000, pitch_origin_mm=0.0)
+    df = synth.Diffusion(DL_cm2_s=400.0, DT_cm2_s=300.0, fluctuate=True, seed=5)
+    n = 300
+    rng = np.random.default_rng(11)
+    x = rng.uniform(0, 1200, n)
+    x[:20] = 0.0
+    z = rng.uniform(10, 350, n)
+    z[20:40] = np.round(z[20:40] / 0.3) * 0.3
+    d = synth.Depos(np.zeros(n), x, np.zeros(n), z, np.full(n, 6000.0))
+    resp = synth.make_response("unipolar")
+    sim = make_sim([pl], [resp], df)
+    dd = _dev(d)
+    desc, patches = sim.rasterize(0, dd)
+    grid = sim.scatter(0, dd)
+    sim.sync()
+    ref = oracle.rasterize(d, pl, df)
+    assert ref.n_invalid == 0 and int(ref.desc[:, 3].max()) > 20 and int(ref.desc[:, 4].max()) > 150
+    assert np.array_equal(to_np(desc), ref.desc)
+    assert max_rel_bin(to_np(patches), ref.values) <= BIN_TOL
+    assert max_rel_bin(to_np(grid), oracle.scatter(ref, pl)) <= BIN_TOL
+
+
+def test_batch_equals_single_events():
+    wl = synth.workload("tiny")
+    sim = make_sim(wl.planes, wl.responses(), synth.Diffusion(fluctuate=True, seed=3))
+    evs = [wl.depos(n_depos=n, seed=s) for n, s in ((500, 1), (1500, 2), (0, 3), (900, 4))]
+    for i, e in enumerate(evs):
+        e.event_id = 100 + i
+    dev = [_dev(e) for e in evs]
+    batch = sim.run_batch(dev)
+    singles = [sim.run_event(e)[0].clone() for e in dev]
+    sim.sync()
+    for b, s in zip(batch, singles):
+        assert rel_l2(to_np(b[0]), to_np(s)) <= 1e-6 or float(s.abs().max()) == 0.0
+
+
+def test_hbm_budget_is_enforced():
+    import paper_2304_01841_gb300 as g
+    wl = synth.workload("uboone_plane")
+    with pytest.raises(g.WctError) as ei:
+        make_sim(wl.planes, wl.responses(), wl.diffusion, hbm_budget_bytes=64 << 20)
+    assert ei.value.code == 2
