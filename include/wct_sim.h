@@ -206,6 +206,32 @@ const char *wct_sim_last_error(const wct_sim_t *sim);
  * and out are DEVICE uint32 [n][4] and key = (seed low word, seed high word). */
 wct_status_t wct_philox4x32_10(const uint32_t *ctr, uint64_t seed, int64_t n, uint32_t *out, void *stream);
 
+/*
+ * Convolution that allocates no device memory (the paper has no counterpart; this entry
+ * point serves callers that may not call cudaMalloc at call time, e.g. code embedded in a
+ * host framework that owns every device allocation through its own pool and forbids direct
+ * cudaMalloc, or latency-critical paths where the implicit synchronisation of cudaMalloc is
+ * not acceptable).
+ *
+ * Computes the same result as wct_sim_convolve, without a handle: grid and waveform are
+ * DEVICE float32 [n_wires][n_ticks] (may be the same buffer); response is a DEVICE float32
+ * [n_wires_resp][n_ticks_resp] array in the layout of wct_response_t (odd n_wires_resp <=
+ * WCT_MAX_RESPONSE_WIRES).  The response spectrum is recomputed on every call.
+ *
+ * Scratch: one fixed array of WCT_CONVOLVE_STATIC_SCRATCH_BYTES in device memory, reserved
+ * on every GPU that loads the library and held until the process exits.  Sizes whose
+ * spectra and tables do not fit in it (roughly 2 * n_wires * (fft_length/2 + 2) * 8 bytes
+ * plus the response spectrum and twiddle tables) are rejected with WCT_EINVAL before any
+ * launch.  The first call on a device looks up the array's device address (with that device
+ * current); make that first call before any stream capture.  Every call shares the one
+ * array and leaves its contents behind: calls that overlap on the GPU (other streams, other
+ * host threads) race with each other and must be serialised by the caller.
+ * Returns WCT_OK, WCT_EINVAL (arguments, or too large) or WCT_ECUDA.
+ */
+#define WCT_CONVOLVE_STATIC_SCRATCH_BYTES (16u << 20)
+wct_status_t wct_convolve_static(const float *grid, int32_t n_wires, int32_t n_ticks, const float *response,
+                                 int32_t n_wires_resp, int32_t n_ticks_resp, float *waveform, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

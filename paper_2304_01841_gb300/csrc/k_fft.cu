@@ -315,6 +315,21 @@ k_wire_stage(const float2 *__restrict__ S, const float2 *__restrict__ Rt, int Fs
     }
 }
 
+// Twiddle tables on the device: tw[k] = exp(-2 pi i k / M) (k < M) and
+// rtw[k] = exp(-2 pi i k / (2M)) (k <= M), evaluated in double precision.
+__global__ void k_make_twiddles(float2 *__restrict__ tw, float2 *__restrict__ rtw, int M) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k <= M) {
+        double sn, cs;
+        sincospi(-(double)k / (double)M, &sn, &cs);          // angle -pi k / M
+        rtw[k] = make_float2((float)cs, (float)sn);
+        if (k < M) {
+            sincospi(-2.0 * (double)k / (double)M, &sn, &cs);  // angle -2 pi k / M
+            tw[k] = make_float2((float)cs, (float)sn);
+        }
+    }
+}
+
 __global__ void k_scale(float2 *__restrict__ a, int64_t n, float s) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) a[i] = cscale(a[i], s);
@@ -351,6 +366,11 @@ cudaError_t launch_wire_stage(const FFTPlan &p, const float2 *spec, const float2
     if (n_wires <= 0) return cudaSuccess;
     dim3 grid((p.Fs + kStageThreads - 1) / kStageThreads, (n_wires + kStageRun - 1) / kStageRun);
     k_wire_stage<<<grid, kStageThreads, 0, s>>>(spec, resp_spec, p.Fs, n_wires, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_make_twiddles(const FFTPlan &p, cudaStream_t s) {
+    k_make_twiddles<<<(p.M + 256) / 256, 256, 0, s>>>(p.tw, p.rtw, p.M);
     return cudaGetLastError();
 }
 

@@ -77,6 +77,7 @@ cudaError_t launch_wire_stage(const FFTPlan &p, const float2 *spec, const float2
 cudaError_t launch_row_c2r(const FFTPlan &p, const float2 *spec, int n_rows, float *out, int64_t out_stride,
                            int n_out_cols, cudaStream_t s);
 cudaError_t launch_scale_spectrum(float2 *spec, int64_t n, float scale, cudaStream_t s);
+cudaError_t launch_make_twiddles(const FFTPlan &p, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, int64_t n, uint32_t *out, cudaStream_t s);
 
 }  // namespace wct

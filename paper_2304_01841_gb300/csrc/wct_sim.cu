@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <mutex>
 #include <new>
 #include <cstdio>
 #include <cstring>
@@ -551,6 +552,82 @@ wct_status_t wct_philox4x32_10(const uint32_t *ctr, uint64_t seed, int64_t n, ui
     if (((uintptr_t)ctr & 15) || ((uintptr_t)out & 15)) return WCT_EINVAL;
     cudaError_t e = launch_philox(ctr, (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32), n, out,
                                   (cudaStream_t)stream);
+    return e == cudaSuccess ? WCT_OK : WCT_ECUDA;
+}
+
+// ------------------------------------------------------------------------------------------
+// Convolution that allocates nothing: its scratch is a fixed array reserved in device memory
+// when the library is loaded.  For callers that may not allocate device memory at call time.
+// ------------------------------------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+
+constexpr size_t kStaticElems = (size_t)WCT_CONVOLVE_STATIC_SCRATCH_BYTES / sizeof(float2);
+constexpr int kMaxDevices = 64;
+__device__ __align__(256) float2 g_convolve_scratch[kStaticElems];
+
+std::mutex g_static_mu;
+float2 *g_static_addr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device.  Looked up once per device
+// (with that device current) and cached; the name g_convolve_scratch itself is only a
+// host-side stand-in and must never be passed to a kernel.
+cudaError_t static_scratch(float2 **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_convolve_scratch);
+        if (e != cudaSuccess) return e;
+        g_static_addr[dev] = static_cast<float2 *>(p);
+    }
+    *out = g_static_addr[dev];
+    return cudaSuccess;
+}
+
+size_t round_up_256(size_t n_float2) { return (n_float2 + 31) & ~(size_t)31; }   // 32 float2 = 256 B
+
+}  // namespace
+
+extern "C" {
+
+wct_status_t wct_convolve_static(const float *grid, int32_t n_wires, int32_t n_ticks, const float *response,
+                                 int32_t n_wires_resp, int32_t n_ticks_resp, float *waveform, void *stream) {
+    if (!grid || !response || !waveform) return WCT_EINVAL;
+    if (n_wires < 1 || n_ticks < 1 || n_wires_resp < 1 || (n_wires_resp & 1) == 0 ||
+        n_wires_resp > WCT_MAX_RESPONSE_WIRES || n_ticks_resp < 1 || n_ticks_resp > 65536)
+        return WCT_EINVAL;
+    FFTPlan p{};
+    if (!plan_fft(n_ticks, n_ticks_resp, p)) return WCT_EINVAL;
+    const int KW = WCT_MAX_RESPONSE_WIRES;
+    const size_t n_tw = round_up_256((size_t)p.M), n_rtw = round_up_256((size_t)p.M + 1);
+    const size_t n_resp = round_up_256((size_t)KW * p.Fs);
+    const size_t n_spec = round_up_256((size_t)n_wires * p.Fs);
+    if (n_tw + n_rtw + n_resp + 2 * n_spec > kStaticElems) return WCT_EINVAL;   // beyond the reserved scratch
+    float2 *base = nullptr;
+    if (static_scratch(&base) != cudaSuccess) {
+        cudaGetLastError();
+        return WCT_ECUDA;
+    }
+    p.tw = base;
+    p.rtw = base + n_tw;
+    float2 *resp_spec = p.rtw + n_rtw;
+    float2 *S = resp_spec + n_resp;
+    float2 *T = S + n_spec;
+    cudaStream_t cs = (cudaStream_t)stream;
+    const int off = (KW - n_wires_resp) / 2;
+    cudaError_t e = launch_make_twiddles(p, cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(resp_spec, 0, sizeof(float2) * (size_t)KW * p.Fs, cs);
+    if (e == cudaSuccess)
+        e = launch_row_r2c(p, response, n_ticks_resp, n_ticks_resp, n_wires_resp, resp_spec + (size_t)off * p.Fs, cs);
+    if (e == cudaSuccess) e = launch_scale_spectrum(resp_spec, (int64_t)KW * p.Fs, 1.0f / (float)p.M, cs);
+    if (e == cudaSuccess) e = launch_row_r2c(p, grid, n_ticks, n_ticks, n_wires, S, cs);
+    if (e == cudaSuccess) e = launch_wire_stage(p, S, resp_spec, n_wires, T, cs);
+    if (e == cudaSuccess) e = launch_row_c2r(p, T, n_wires, waveform, n_ticks, n_ticks, cs);
     return e == cudaSuccess ? WCT_OK : WCT_ECUDA;
 }
 
