@@ -5,7 +5,7 @@
 // scan, which the OpenMP port removed (§4.3).  Here:
 //   k_prep      one thread per depo: FP64 drift / diffusion, window bounds, a 32-byte
 //               descriptor, and a count of the output tiles the window overlaps;
-//   k_fill      one thread per depo: appends the depo to each overlapped tile's list;
+//   k_bin_patches / k_fill_patches  tile binning of caller-supplied patch descriptors;
 //   scans       three-phase exclusive scans (tile-list offsets, patch offsets).
 #include "wct_internal.cuh"
 #include "wct_device.cuh"
@@ -15,21 +15,6 @@ namespace wct {
 namespace {
 
 constexpr int kPrepThreads = 256;
-
-// +-nsigma window on one axis, decided in FP64 with explicitly rounded operations so the
-// bounds match a host FP64 evaluation of the same expressions bit for bit.
-__device__ __forceinline__ void axis_window(double mu, double s, double nsigma, long long &lo, long long &n) {
-    if (s < 1e-6) {
-        lo = (long long)floor(mu);
-        n = 1;
-        return;
-    }
-    const double ns = __dmul_rn(nsigma, s);
-    const double a = __dsub_rn(mu, ns);
-    const double b = __dadd_rn(mu, ns);
-    lo = (long long)floor(a);
-    n = (long long)floor(b) - lo + 1;
-}
 
 struct TileRange {
     int tw0, tw1, tt0, tt1;   // inclusive; tw0 > tw1 when empty
@@ -60,44 +45,8 @@ k_prep(const float *__restrict__ t0, const float *__restrict__ x, const float *_
        int32_t *status) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double T0 = t0[i], X = x[i], Y = y[i], Z = z[i], Q = q[i];
     DepoDesc d;
-    d.mu_t = d.mu_p = d.inv_t = d.inv_p = 0.f;
-    d.q = 0.f;
-    d.lo_t = d.lo_p = 0;
-    d.nt = d.np = 0;
-    bool ok = isfinite(T0) && isfinite(X) && isfinite(Y) && isfinite(Z) && isfinite(Q) && X >= 0.0 && Q >= 0.0;
-    if (ok) {
-        const double td = __ddiv_rn(X, pp.v);
-        const double arrival = __dadd_rn(T0, td);
-        const double sigL = __dsqrt_rn(__dmul_rn(__dmul_rn(2.0, pp.DL), td));
-        const double sigT = __dsqrt_rn(__dmul_rn(__dmul_rn(2.0, pp.DT), td));
-        const double mu_t = __ddiv_rn(__dsub_rn(arrival, pp.tw0), pp.tick);
-        const double s_t = __ddiv_rn(__ddiv_rn(sigL, pp.v), pp.tick);
-        const double p = __dadd_rn(__dmul_rn(Z, pp.cos_a), __dmul_rn(Y, pp.sin_a));
-        const double mu_p = __ddiv_rn(__dsub_rn(p, pp.origin), pp.dp);
-        const double s_p = __ddiv_rn(sigT, pp.dp);
-        long long lo_t = 0, n_t = 0, lo_p = 0, n_p = 0;
-        const double big = 1099511627776.0;   // 2^40 bins: keeps floor() within int64
-        if (!(fabs(mu_t) < big && fabs(mu_p) < big && s_t < big && s_p < big)) ok = false;
-        axis_window(mu_t, s_t, pp.nsigma, lo_t, n_t);
-        axis_window(mu_p, s_p, pp.nsigma, lo_p, n_p);
-        const long long lim = 1LL << 30;
-        if (!ok || n_t > WCT_MAX_WINDOW_TICKS || n_p > WCT_MAX_WINDOW_IMPACTS || lo_t < -lim || lo_t > lim ||
-            lo_p < -lim || lo_p > lim) {
-            ok = false;
-        } else {
-            d.lo_t = (int32_t)lo_t;
-            d.lo_p = (int32_t)lo_p;
-            d.nt = (int16_t)n_t;
-            d.np = (int16_t)n_p;
-            d.mu_t = (float)__dsub_rn(mu_t, (double)lo_t);
-            d.mu_p = (float)__dsub_rn(mu_p, (double)lo_p);
-            d.inv_t = (s_t < 1e-6) ? 0.f : (float)__drcp_rn(__dmul_rn(1.4142135623730951, s_t));
-            d.inv_p = (s_p < 1e-6) ? 0.f : (float)__drcp_rn(__dmul_rn(1.4142135623730951, s_p));
-            d.q = (float)Q;
-        }
-    }
+    const bool ok = depo_window(t0[i], x[i], y[i], z[i], q[i], pp, d);
     if (!ok) set_status(status, ST_EINVAL);
     desc[i] = d;
     if (patch_size) patch_size[i] = (int64_t)d.nt * (int64_t)d.np;
@@ -106,22 +55,6 @@ k_prep(const float *__restrict__ t0, const float *__restrict__ x, const float *_
         for (int tw = r.tw0; tw <= r.tw1; ++tw)
             for (int tt = r.tt0; tt <= r.tt1; ++tt) atomicAdd(&tile_count[tw * pp.n_tiles_t + tt], 1);
     }
-}
-
-__global__ void __launch_bounds__(kPrepThreads)
-k_fill(int64_t n, const DepoDesc *__restrict__ desc, PlaneParams pp, const int32_t *__restrict__ tile_off,
-       int32_t *__restrict__ cursor, int32_t *__restrict__ list, int64_t list_cap, int32_t *status) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const DepoDesc d = desc[i];
-    const TileRange r = tile_range(d.lo_t, d.nt, d.lo_p, d.np, pp);
-    for (int tw = r.tw0; tw <= r.tw1; ++tw)
-        for (int tt = r.tt0; tt <= r.tt1; ++tt) {
-            const int tile = tw * pp.n_tiles_t + tt;
-            const int64_t pos = (int64_t)tile_off[tile] + atomicAdd(&cursor[tile], 1);
-            if (pos < list_cap) list[pos] = (int32_t)i;
-            else set_status(status, ST_EDEVICE);
-        }
 }
 
 // A caller-supplied patch descriptor is usable if its window is within the library limits.
@@ -279,14 +212,6 @@ cudaError_t launch_prep(const wct_depos_t &d, const PlaneParams &pp, DepoDesc *d
     if (d.n <= 0) return cudaSuccess;
     k_prep<<<blocks_for(d.n, kPrepThreads), kPrepThreads, 0, s>>>(d.t0_us, d.x_mm, d.y_mm, d.z_mm, d.q_e, d.n, pp,
                                                                    desc, tile_count, patch_size, status);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_fill(int64_t n, const DepoDesc *desc, const PlaneParams &pp, const int32_t *tile_off,
-                        int32_t *tile_cursor, int32_t *tile_list, int64_t list_cap, int32_t *status, cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    k_fill<<<blocks_for(n, kPrepThreads), kPrepThreads, 0, s>>>(n, desc, pp, tile_off, tile_cursor, tile_list,
-                                                                 list_cap, status);
     return cudaGetLastError();
 }
 

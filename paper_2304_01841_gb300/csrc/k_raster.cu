@@ -1,21 +1,20 @@
 // Rasterization (+ fluctuation) and scatter-add (paper §2, steps 1 and 2).
 //
-// Fused path, k_tile_raster_scatter: one CTA owns one output tile of TW wires x TT ticks in
-// shared memory.  Its warps take the depos binned to the tile (a depo is binned to every
-// tile its window overlaps), compute each depo's erf-difference weights in per-warp shared
-// memory, evaluate the patch folded onto wires (the sum over a wire's impact sub-bins of the
-// fluctuated bin charges), and add the part that falls in the tile with shared-memory
-// atomics.  The tile is then written to the grid once with coalesced 16-byte stores: every
-// grid element is written exactly once per call, and no global atomics are used (the paper's
-// scatter-add relies on global atomic adds, §2 and §5.2).
+// Fused path, k_raster_chunks (below): depo-parallel, the patch of each depo is evaluated
+// folded onto wires (the sum over a wire's impact sub-bins of the fluctuated bin charges),
+// accumulated in shared memory per chunk of depos and then added to the grid.  The paper's
+// scatter-add adds every patch bin with a global atomic (§2, §5.2); here a chunk of track
+// depos shares one shared-memory box, so the global adds shrink to one per touched bin.
 //
-// The fluctuation renormalises each patch to its charge over the depo's whole window, so a
-// depo that straddles tiles is evaluated in full by every tile it touches (only its in-tile
-// part is added).  Because rescaling is linear, the fold is taken on the unscaled fluctuated
-// charges and the scale q / sum is applied afterwards.
+// The fluctuation renormalises each patch to its charge over the depo's whole window.
+// Because rescaling is linear, the fold is taken on the unscaled fluctuated charges and the
+// scale q / sum is applied afterwards.
 //
-// Unfused path: k_rasterize_patches (one warp per depo) writes every depo's full patch,
-// k_tile_scatter_patches sums caller-supplied patches per tile.
+// Unfused path: k_rasterize_patches (one warp per depo) writes every depo's full patch;
+// k_tile_scatter_patches sums caller-supplied patches per output tile in shared memory and
+// writes each tile once.
+#include <climits>
+
 #include "wct_internal.cuh"
 #include "wct_device.cuh"
 
@@ -26,7 +25,6 @@ namespace {
 constexpr int kTileWarps = 8;
 constexpr int kWT = WCT_MAX_WINDOW_TICKS + 1;                 // per-warp time weights (+1 edge)
 constexpr int kWBuf = kWT + WCT_MAX_WINDOW_IMPACTS + 1;       // per-warp weight buffer (floats)
-constexpr int kMaxItemsPerLane = 4;                           // register-cached fold items
 
 // Warp-cooperative 1D weights of one axis: w[i] = (erf(x_{i+1}) - erf(x_i)) / 2 with
 // x_i = (i - mu) * inv (window-relative bin edges), normalised to sum 1.  inv == 0 marks a
@@ -127,102 +125,206 @@ __device__ __forceinline__ uint32_t counter_c3(const PlaneParams &pp, uint32_t e
 }
 
 // ------------------------------------------------------------------------------------------
-// Fused rasterize + fluctuate + fold + tile scatter.
+// Fused rasterize + fluctuate + fold + scatter, balanced over depos.
+//
+// One CTA takes a chunk of kChunk consecutive depos (consecutive depos of a track are close
+// in space).  Its threads (1) compute every depo's FP64 window, (2) compute all erf bin
+// weights of the chunk, flattened over (depo, bin), (3) evaluate all (tick, wire) items of
+// the chunk, flattened over (depo, item) so every lane has work, summing each depo's
+// fluctuated charge with a segmented warp reduction, (4) add the rescaled items into a
+// shared-memory box covering the chunk's footprint on the grid, and (5) add the box to the
+// grid in global memory, one atomic per touched bin.  A chunk whose footprint does not fit
+// the box (scattered depos) adds its items to global memory directly.  The grid is zeroed
+// before the launch.
 // ------------------------------------------------------------------------------------------
-template <int TW, int TT>
-__global__ void __launch_bounds__(kTileWarps * 32)
-k_tile_raster_scatter(const DepoDesc *__restrict__ desc, const int32_t *__restrict__ tile_off,
-                      const int32_t *__restrict__ tile_list, int64_t list_cap, PlaneParams pp, uint32_t event_lo,
-                      float *__restrict__ grid) {
-    extern __shared__ float4 smem4[];
-    float *tile = reinterpret_cast<float *>(smem4);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float *wt = tile + TW * TT + warp * kWBuf;
-    float *wp = wt + kWT;
+constexpr int kChunkThreads = 256;
+constexpr int kChunk = 64;
+constexpr int kItemCap = 7168;     // items cached per pass (a wider single depo is recomputed)
+constexpr int kWCap = 2048;        // >= 128 + 512, the weights of the largest window
+constexpr int kBoxCap = 8192;      // wires x ticks accumulated in shared memory
 
-    const int tile_id = blockIdx.x;
-    const int tw = tile_id / pp.n_tiles_t;
-    const int tt = tile_id - tw * pp.n_tiles_t;
-    const int wire0 = tw * TW, tick0 = tt * TT;
-    const int wire_end = min(wire0 + TW, pp.n_wires), tick_end = min(tick0 + TT, pp.n_ticks);
+struct ChunkSmem {
+    DepoDesc d[kChunk];
+    int item_off[kChunk + 1];
+    int w_off[kChunk + 1];
+    int wl[kChunk];
+    int nw[kChunk];
+    float nrm_t[kChunk];
+    float nrm_p[kChunk];
+    float sum[kChunk];
+    int pass_end;
+    int use_box, box_w0, box_t0, box_nw, box_nt;
+    float w[kWCap];
+    float val[kItemCap];
+    float box[kBoxCap];
+};
 
-    for (int i = threadIdx.x; i < TW * TT / 4; i += blockDim.x) smem4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    __syncthreads();
+// largest j in [lo, hi) with off[j] <= k (off non-decreasing, off[lo] <= k)
+__device__ __forceinline__ int find_slot(const int *off, int lo, int hi, int k) {
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= k) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
 
+// Segmented warp sum over lanes with equal (sorted) keys; the last lane of each segment adds
+// the segment's total to sums[key].  Keys < 0 are ignored.
+__device__ __forceinline__ void segmented_add(int key, float v, float *sums) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float vv = __shfl_up_sync(0xffffffffu, v, o);
+        const int kk = __shfl_up_sync(0xffffffffu, key, o);
+        if (lane >= o && kk == key) v += vv;
+    }
+    const int next = __shfl_down_sync(0xffffffffu, key, 1);
+    if (key >= 0 && (lane == 31 || next != key)) atomicAdd(&sums[key], v);
+}
+
+__global__ void __launch_bounds__(kChunkThreads)
+k_raster_chunks(const float *__restrict__ t0, const float *__restrict__ x, const float *__restrict__ y,
+                const float *__restrict__ z, const float *__restrict__ q, int64_t n, PlaneParams pp,
+                uint32_t event_lo, float *__restrict__ grid, int32_t *status) {
+    extern __shared__ float4 smem_raw[];
+    ChunkSmem &S = *reinterpret_cast<ChunkSmem *>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int64_t c0 = (int64_t)blockIdx.x * kChunk;
+    const int cn = (int)((n - c0) < kChunk ? (n - c0) : kChunk);
     const uint32_t c3 = counter_c3(pp, event_lo);
-    const int beg = tile_off[tile_id];
-    const int end = (int)min((int64_t)tile_off[tile_id + 1], list_cap);
-    for (int li = beg + warp; li < end; li += kTileWarps) {
-        const int di = tile_list[li];
-        const DepoDesc d = desc[di];
-        const int nt = d.nt, np = d.np;
-        axis_weights(wt, nt, d.mu_t, d.inv_t, lane);
-        axis_weights(wp, np, d.mu_p, d.inv_p, lane);
-        const int wl = floor_div(d.lo_p, pp.n_imp);
-        const int nw = floor_div(d.lo_p + np - 1, pp.n_imp) - wl + 1;
-        const int items = nt * nw;
-        const float q = d.q;
-        auto deposit = [&](const Item &f, float v) {
-            if (f.wire >= wire0 && f.wire < wire_end && f.tick >= tick0 && f.tick < tick_end)
-                atomicAdd(&tile[(f.wire - wire0) * TT + (f.tick - tick0)], v);
-        };
-        if (!pp.fluctuate) {
-            for (int it = lane; it < items; it += 32) {
-                const Item f = make_item(it, nw, wl, d, pp.n_imp);
-                if (f.wire >= wire0 && f.wire < wire_end && f.tick >= tick0 && f.tick < tick_end)
-                    deposit(f, fold_plain(f, wt, wp, q));
-            }
-        } else {
-            float vals[kMaxItemsPerLane];
-            float part = 0.f;
-#pragma unroll
-            for (int k = 0; k < kMaxItemsPerLane; ++k) {
-                const int it = lane + 32 * k;
-                float v = 0.f;
-                if (it < items) v = fold_fluct(make_item(it, nw, wl, d, pp.n_imp), wt, wp, q, (uint32_t)di, pp, c3);
-                vals[k] = v;
-                part += v;
-            }
-            for (int it = lane + 32 * kMaxItemsPerLane; it < items; it += 32)
-                part += fold_fluct(make_item(it, nw, wl, d, pp.n_imp), wt, wp, q, (uint32_t)di, pp, c3);
-            const float total = warp_sum(part);
-            const bool keep = total > 0.f;
-            const float scale = keep ? q / total : 0.f;
-#pragma unroll
-            for (int k = 0; k < kMaxItemsPerLane; ++k) {
-                const int it = lane + 32 * k;
-                if (it < items) {
-                    const Item f = make_item(it, nw, wl, d, pp.n_imp);
-                    deposit(f, keep ? vals[k] * scale : fold_plain(f, wt, wp, q));
-                }
-            }
-            for (int it = lane + 32 * kMaxItemsPerLane; it < items; it += 32) {
-                const Item f = make_item(it, nw, wl, d, pp.n_imp);
-                if (f.wire >= wire0 && f.wire < wire_end && f.tick >= tick0 && f.tick < tick_end)
-                    deposit(f, keep ? fold_fluct(f, wt, wp, q, (uint32_t)di, pp, c3) * scale : fold_plain(f, wt, wp, q));
-            }
+
+    if (tid < cn) {
+        const int64_t i = c0 + tid;
+        DepoDesc d;
+        if (!depo_window(t0[i], x[i], y[i], z[i], q[i], pp, d)) set_status(status, ST_EINVAL);
+        S.d[tid] = d;
+        int wl = 0, nw = 0;
+        if (d.nt > 0) {
+            wl = floor_div(d.lo_p, pp.n_imp);
+            nw = floor_div(d.lo_p + d.np - 1, pp.n_imp) - wl + 1;
         }
-        __syncwarp();
+        S.wl[tid] = wl;
+        S.nw[tid] = nw;
+        // sum of a window's unnormalised weights telescopes to (erf(x_n) - erf(x_0)) / 2
+        S.nrm_t[tid] = d.inv_t == 0.f ? 1.f : 1.f / (erff(((float)d.nt - d.mu_t) * d.inv_t) - erff(-d.mu_t * d.inv_t));
+        S.nrm_p[tid] = d.inv_p == 0.f ? 1.f : 1.f / (erff(((float)d.np - d.mu_p) * d.inv_p) - erff(-d.mu_p * d.inv_p));
+        S.sum[tid] = 0.f;
     }
     __syncthreads();
 
-    // Write the whole tile once (zeros included): coalesced 16-byte stores along ticks.
-    const bool vec = ((pp.n_ticks & 3) == 0) && ((reinterpret_cast<uintptr_t>(grid) & 15) == 0);
-    for (int i = threadIdx.x; i < TW * TT / 4; i += blockDim.x) {
-        const int r = i / (TT / 4);
-        const int c = (i - r * (TT / 4)) * 4;
-        const int wire = wire0 + r, tick = tick0 + c;
-        if (wire >= wire_end || tick >= tick_end) continue;
-        float *dst = grid + (int64_t)wire * pp.n_ticks + tick;
-        const float4 v = smem4[i];
-        if (vec) {
-            *reinterpret_cast<float4 *>(dst) = v;
-        } else {
-            dst[0] = v.x;
-            if (tick + 1 < tick_end) dst[1] = v.y;
-            if (tick + 2 < tick_end) dst[2] = v.z;
-            if (tick + 3 < tick_end) dst[3] = v.w;
+    for (int s = 0; s < cn;) {
+        if (tid == 0) {
+            // pack depos [s, e) whose items and weights fit, and bound their footprint
+            int it = 0, ww = 0, e = s;
+            int w0 = INT_MAX, w1 = INT_MIN, t0b = INT_MAX, t1b = INT_MIN;
+            for (; e < cn; ++e) {
+                const DepoDesc &d = S.d[e];
+                const int ni = (int)d.nt * S.nw[e], nwt = (int)d.nt + (int)d.np;
+                if (e > s && (it + ni > kItemCap || ww + nwt > kWCap)) break;
+                S.item_off[e] = it;
+                S.w_off[e] = ww;
+                it += ni;
+                ww += nwt;
+                if (d.nt > 0) {
+                    const int a0 = max(S.wl[e], 0), a1 = min(S.wl[e] + S.nw[e] - 1, pp.n_wires - 1);
+                    const int b0 = max(d.lo_t, 0), b1 = min(d.lo_t + (int)d.nt - 1, pp.n_ticks - 1);
+                    if (a0 <= a1 && b0 <= b1) {
+                        w0 = min(w0, a0); w1 = max(w1, a1);
+                        t0b = min(t0b, b0); t1b = max(t1b, b1);
+                    }
+                }
+            }
+            S.item_off[e] = it;
+            S.w_off[e] = ww;
+            S.pass_end = e;
+            const bool any = w0 <= w1;
+            const int64_t area = any ? (int64_t)(w1 - w0 + 1) * (t1b - t0b + 1) : 0;
+            S.use_box = any && area <= kBoxCap;
+            S.box_w0 = w0;
+            S.box_t0 = t0b;
+            S.box_nw = any ? w1 - w0 + 1 : 0;
+            S.box_nt = any ? t1b - t0b + 1 : 0;
         }
+        __syncthreads();
+        const int e = S.pass_end;
+        const int n_items = S.item_off[e] - S.item_off[s];
+        const int i_base = S.item_off[s];
+        const int n_w = S.w_off[e] - S.w_off[s];
+        const int w_base = S.w_off[s];
+        const bool use_box = S.use_box;
+        const int bnt = S.box_nt, bw0 = S.box_w0, bt0 = S.box_t0;
+        if (use_box)
+            for (int k = tid; k < S.box_nw * bnt; k += kChunkThreads) S.box[k] = 0.f;
+        // (2) bin weights, flattened over (depo, bin): w = (erf(x_{i+1}) - erf(x_i)) * nrm
+        for (int k = tid; k < n_w; k += kChunkThreads) {
+            const int j = find_slot(S.w_off, s, e, w_base + k);
+            const DepoDesc &d = S.d[j];
+            const int r = w_base + k - S.w_off[j];
+            float w;
+            if (r < d.nt) {
+                w = d.inv_t == 0.f ? 1.f
+                                   : (erff(((float)(r + 1) - d.mu_t) * d.inv_t) - erff(((float)r - d.mu_t) * d.inv_t)) *
+                                         S.nrm_t[j];
+            } else {
+                const int rr = r - d.nt;
+                w = d.inv_p == 0.f ? 1.f
+                                   : (erff(((float)(rr + 1) - d.mu_p) * d.inv_p) - erff(((float)rr - d.mu_p) * d.inv_p)) *
+                                         S.nrm_p[j];
+            }
+            S.w[k] = w;
+        }
+        __syncthreads();
+        // (3) items, flattened over (depo, item)
+        for (int base = tid - lane; base < n_items; base += kChunkThreads) {
+            const int k = base + lane;
+            int j = -1;
+            float v = 0.f;
+            if (k < n_items) {
+                j = find_slot(S.item_off, s, e, i_base + k);
+                const DepoDesc &d = S.d[j];
+                const Item f = make_item(i_base + k - S.item_off[j], S.nw[j], S.wl[j], d, pp.n_imp);
+                const float *wt = S.w + (S.w_off[j] - w_base);
+                const float *wp = wt + d.nt;
+                v = pp.fluctuate ? fold_fluct(f, wt, wp, d.q, (uint32_t)(c0 + j), pp, c3) : fold_plain(f, wt, wp, d.q);
+                if (k < kItemCap) S.val[k] = v;   // a single very wide depo may exceed the cache
+            }
+            if (pp.fluctuate) segmented_add(j, v, S.sum);
+        }
+        __syncthreads();
+        // (4) rescale and accumulate (box in shared memory, or the grid directly)
+        for (int k = tid; k < n_items; k += kChunkThreads) {
+            const int j = find_slot(S.item_off, s, e, i_base + k);
+            const DepoDesc &d = S.d[j];
+            const Item f = make_item(i_base + k - S.item_off[j], S.nw[j], S.wl[j], d, pp.n_imp);
+            if (f.wire < 0 || f.wire >= pp.n_wires || f.tick < 0 || f.tick >= pp.n_ticks) continue;
+            const float *wt = S.w + (S.w_off[j] - w_base);
+            float v;
+            if (k < kItemCap) v = S.val[k];
+            else v = pp.fluctuate ? fold_fluct(f, wt, wt + d.nt, d.q, (uint32_t)(c0 + j), pp, c3)
+                                  : fold_plain(f, wt, wt + d.nt, d.q);
+            if (pp.fluctuate) {
+                const float sm = S.sum[j];
+                if (sm > 0.f) v *= d.q / sm;
+                else v = fold_plain(f, wt, wt + d.nt, d.q);
+            }
+            if (use_box) atomicAdd(&S.box[(f.wire - bw0) * bnt + (f.tick - bt0)], v);
+            else atomicAdd(&grid[(int64_t)f.wire * pp.n_ticks + f.tick], v);
+        }
+        __syncthreads();
+        // (5) the box's touched bins to the grid
+        if (use_box) {
+            const int area = S.box_nw * bnt;
+            for (int k = tid; k < area; k += kChunkThreads) {
+                const float v = S.box[k];
+                if (v != 0.f) {
+                    const int r = k / bnt;
+                    atomicAdd(&grid[(int64_t)(bw0 + r) * pp.n_ticks + bt0 + (k - r * bnt)], v);
+                }
+            }
+        }
+        __syncthreads();
+        s = e;
     }
 }
 
@@ -369,24 +471,21 @@ __global__ void k_philox(const uint32_t *__restrict__ ctr, uint32_t k0, uint32_t
 
 constexpr int kTileW = 32, kTileT = 256;
 
-size_t tile_smem_bytes() { return sizeof(float) * ((size_t)kTileW * kTileT + (size_t)kTileWarps * kWBuf); }
 
 }  // namespace
 
 int tile_wires() { return kTileW; }
 int tile_ticks() { return kTileT; }
 
-cudaError_t launch_tile_raster_scatter(const DepoDesc *desc, const int32_t *tile_off, const int32_t *tile_list,
-                                       int64_t list_cap, const PlaneParams &pp, uint32_t event_lo, float *grid,
-                                       cudaStream_t s) {
-    const int n_tiles = pp.n_tiles_w * pp.n_tiles_t;
-    if (n_tiles <= 0) return cudaSuccess;
-    const size_t smem = tile_smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(k_tile_raster_scatter<kTileW, kTileT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t launch_raster_chunks(const wct_depos_t &d, const PlaneParams &pp, uint32_t event_lo, float *grid,
+                                 int32_t *status, cudaStream_t s) {
+    if (d.n <= 0) return cudaSuccess;
+    const size_t smem = sizeof(ChunkSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_raster_chunks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_tile_raster_scatter<kTileW, kTileT><<<n_tiles, kTileWarps * 32, smem, s>>>(desc, tile_off, tile_list, list_cap,
-                                                                                 pp, event_lo, grid);
+    const int64_t blocks = (d.n + kChunk - 1) / kChunk;
+    k_raster_chunks<<<(unsigned)blocks, kChunkThreads, smem, s>>>(d.t0_us, d.x_mm, d.y_mm, d.z_mm, d.q_e, d.n, pp,
+                                                                  event_lo, grid, status);
     return cudaGetLastError();
 }
 

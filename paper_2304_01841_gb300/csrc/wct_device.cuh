@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "wct_internal.cuh"
+
 namespace wct {
 
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  Each of the ten rounds multiplies
@@ -45,6 +47,65 @@ __device__ __forceinline__ int floor_div(int a, int b) {   // b > 0
 
 __device__ __forceinline__ void set_status(int32_t *status, int32_t code) {
     if (status) atomicCAS(status, 0, code);
+}
+
+// +-nsigma window on one axis, decided in FP64 with explicitly rounded operations so the
+// bounds match a host FP64 evaluation of the same expressions bit for bit.
+__device__ __forceinline__ void axis_window(double mu, double s, double nsigma, long long &lo, long long &n) {
+    if (s < 1e-6) {
+        lo = (long long)floor(mu);
+        n = 1;
+        return;
+    }
+    const double ns = __dmul_rn(nsigma, s);
+    const double a = __dsub_rn(mu, ns);
+    const double b = __dadd_rn(mu, ns);
+    lo = (long long)floor(a);
+    n = (long long)floor(b) - lo + 1;
+}
+
+// Drift, diffusion and +-nsigma window of one depo (FP64), packed into a DepoDesc.
+// Returns false (and an empty descriptor) for an invalid depo: a non-finite value, x < 0,
+// q < 0, a window over the limits, or one that starts more than 2^30 bins from the origin.
+//   t_d = x / v, arrival = t0 + t_d, sigma_L,T = sqrt(2 D_L,T t_d)
+//   mu_t = (arrival - t_window0) / tick, s_t = (sigma_L / v) / tick
+//   mu_p = (z cos a + y sin a - origin) / (pitch / n_imp), s_p = sigma_T / (pitch / n_imp)
+__device__ __forceinline__ bool depo_window(double T0, double X, double Y, double Z, double Q, const PlaneParams &pp,
+                                            DepoDesc &d) {
+    d.mu_t = d.mu_p = d.inv_t = d.inv_p = 0.f;
+    d.q = 0.f;
+    d.lo_t = d.lo_p = 0;
+    d.nt = d.np = 0;
+    bool ok = isfinite(T0) && isfinite(X) && isfinite(Y) && isfinite(Z) && isfinite(Q) && X >= 0.0 && Q >= 0.0;
+    if (!ok) return false;
+    const double td = __ddiv_rn(X, pp.v);
+    const double arrival = __dadd_rn(T0, td);
+    const double sigL = __dsqrt_rn(__dmul_rn(__dmul_rn(2.0, pp.DL), td));
+    const double sigT = __dsqrt_rn(__dmul_rn(__dmul_rn(2.0, pp.DT), td));
+    const double mu_t = __ddiv_rn(__dsub_rn(arrival, pp.tw0), pp.tick);
+    const double s_t = __ddiv_rn(__ddiv_rn(sigL, pp.v), pp.tick);
+    const double p = __dadd_rn(__dmul_rn(Z, pp.cos_a), __dmul_rn(Y, pp.sin_a));
+    const double mu_p = __ddiv_rn(__dsub_rn(p, pp.origin), pp.dp);
+    const double s_p = __ddiv_rn(sigT, pp.dp);
+    const double big = 1099511627776.0;   // 2^40 bins: keeps floor() within int64
+    if (!(fabs(mu_t) < big && fabs(mu_p) < big && s_t < big && s_p < big)) return false;
+    long long lo_t = 0, n_t = 0, lo_p = 0, n_p = 0;
+    axis_window(mu_t, s_t, pp.nsigma, lo_t, n_t);
+    axis_window(mu_p, s_p, pp.nsigma, lo_p, n_p);
+    const long long lim = 1LL << 30;
+    if (n_t > WCT_MAX_WINDOW_TICKS || n_p > WCT_MAX_WINDOW_IMPACTS || lo_t < -lim || lo_t > lim || lo_p < -lim ||
+        lo_p > lim)
+        return false;
+    d.lo_t = (int32_t)lo_t;
+    d.lo_p = (int32_t)lo_p;
+    d.nt = (int16_t)n_t;
+    d.np = (int16_t)n_p;
+    d.mu_t = (float)__dsub_rn(mu_t, (double)lo_t);
+    d.mu_p = (float)__dsub_rn(mu_p, (double)lo_p);
+    d.inv_t = (s_t < 1e-6) ? 0.f : (float)__drcp_rn(__dmul_rn(1.4142135623730951, s_t));
+    d.inv_p = (s_p < 1e-6) ? 0.f : (float)__drcp_rn(__dmul_rn(1.4142135623730951, s_p));
+    d.q = (float)Q;
+    return true;
 }
 
 __device__ __forceinline__ float warp_sum(float v) {

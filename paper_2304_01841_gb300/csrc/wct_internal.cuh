@@ -50,15 +50,12 @@ struct FFTPlan {
 // ---- launchers (stream-ordered; return cudaError_t of the launch) -------------------------
 cudaError_t launch_prep(const wct_depos_t &d, const PlaneParams &pp, DepoDesc *desc, int32_t *tile_count,
                         int64_t *patch_size, int32_t *status, cudaStream_t s);
-cudaError_t launch_fill(int64_t n, const DepoDesc *desc, const PlaneParams &pp, const int32_t *tile_off,
-                        int32_t *tile_cursor, int32_t *tile_list, int64_t list_cap, int32_t *status, cudaStream_t s);
 cudaError_t launch_scan_i32(const int32_t *in, int32_t *out, int64_t n, int32_t *tmp, cudaStream_t s);
 cudaError_t launch_scan_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *tmp, cudaStream_t s);
 int64_t scan_tmp_elems(int64_t n);
 
-cudaError_t launch_tile_raster_scatter(const DepoDesc *desc, const int32_t *tile_off, const int32_t *tile_list,
-                                       int64_t list_cap, const PlaneParams &pp, uint32_t event_lo, float *grid,
-                                       cudaStream_t s);
+cudaError_t launch_raster_chunks(const wct_depos_t &d, const PlaneParams &pp, uint32_t event_lo, float *grid,
+                                 int32_t *status, cudaStream_t s);
 cudaError_t launch_rasterize_patches(int64_t n, const DepoDesc *desc, const int64_t *offsets, const PlaneParams &pp,
                                      uint32_t event_lo, float *patches, int64_t *patch_desc, cudaStream_t s);
 cudaError_t launch_bin_patches(int64_t n, const int64_t *patch_desc, const PlaneParams &pp, int32_t *tile_count,

@@ -224,22 +224,16 @@ void mark(wct_sim *s, int slot, int k, cudaStream_t st) {
     if (slot >= 0) cudaEventRecord(s->slots[slot][k], st);
 }
 
-// Fused rasterize + scatter of one plane into `grid`.
+// Fused rasterize + scatter of one plane into `grid` (zeroed first, then accumulated).
 wct_status_t raster_scatter(wct_sim *s, int plane, const wct_depos_t *d, float *grid, cudaStream_t st, int slot) {
     const PlaneState &ps = s->planes[plane];
     const PlaneParams pp = plane_params(s, plane);
-    cudaError_t e = cudaMemsetAsync(s->tile_count, 0, sizeof(int32_t) * (ps.n_tiles + 1), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(s->tile_cursor, 0, sizeof(int32_t) * (ps.n_tiles + 1), st);
-    if (e == cudaSuccess) e = launch_prep(*d, pp, s->desc, s->tile_count, nullptr, s->status, st);
-    if (e == cudaSuccess) e = launch_scan_i32(s->tile_count, s->tile_off, ps.n_tiles, s->scan32, st);
-    if (e == cudaSuccess)
-        e = launch_fill(d->n, s->desc, pp, s->tile_off, s->tile_cursor, s->tile_list, s->list_cap, s->status, st);
-    if (e != cudaSuccess) return cuda_fail(s, e, "prep / binning");
+    cudaError_t e = cudaMemsetAsync(grid, 0, sizeof(float) * (size_t)ps.g.n_wires * ps.g.n_ticks, st);
+    if (e != cudaSuccess) return cuda_fail(s, e, "grid clear");
     mark(s, slot, 1, st);
-    e = launch_tile_raster_scatter(s->desc, s->tile_off, s->tile_list, s->list_cap, pp, (uint32_t)d->event_id, grid,
-                                   st);
-    if (e != cudaSuccess) return cuda_fail(s, e, "tile raster-scatter");
-    s->launches += 4 + (d->n > 0 ? 2 : 0);
+    e = launch_raster_chunks(*d, pp, (uint32_t)d->event_id, grid, s->status, st);
+    if (e != cudaSuccess) return cuda_fail(s, e, "raster-scatter");
+    s->launches += d->n > 0 ? 1 : 0;
     mark(s, slot, 2, st);
     return WCT_OK;
 }
