@@ -16,6 +16,9 @@
 //   k_row_c2r   one CTA per wire row: inverse of k_row_r2c, cropped to n_ticks.
 #include "wct_internal.cuh"
 #include "wct_device.cuh"
+#include "wct_tma.cuh"
+
+#include <algorithm>
 
 namespace wct {
 
@@ -164,7 +167,7 @@ __device__ __forceinline__ void fft_stage(const float2 *__restrict__ in, float2 
         if (Ns > 1) {
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                float2 w = __ldg(&tw[r * k * stride]);
+                float2 w = tw[r * k * stride];
                 if (INV) w.y = -w.y;
                 v[r] = cmul(v[r], w);
             }
@@ -177,27 +180,38 @@ __device__ __forceinline__ void fft_stage(const float2 *__restrict__ in, float2 
     __syncthreads();
 }
 
-// Complex FFT of length M in shared memory, ping-ponging between a and b; returns the
-// buffer holding the result.
+__device__ __forceinline__ int plan_radix(const FFTPlan &p, int s) { return (int)((p.radix_code >> (4 * s)) & 15u); }
+
+// Stages [s_begin, s_end) of the complex FFT of length M in shared memory.  The first of them
+// reads `src`; each stage writes whichever of x / y it is not reading.  tw is the
+// exp(-2 pi i k / M) table (shared or global memory).  Returns the buffer holding the result.
 template <bool INV>
-__device__ float2 *cta_fft(float2 *a, float2 *b, const FFTPlan &p) {
+__device__ const float2 *cta_fft_range(const float2 *src, float2 *x, float2 *y, const FFTPlan &p,
+                                       const float2 *tw, int s_begin, int s_end) {
     int Ns = 1;
-    for (int s = 0; s < p.n_stages; ++s) {
-        const int R = p.radix[s];
+    for (int s = 0; s < s_begin; ++s) Ns *= plan_radix(p, s);
+    const float2 *in = src;
+    for (int s = s_begin; s < s_end; ++s) {
+        const int R = plan_radix(p, s);
+        float2 *out = (in == x) ? y : x;
         switch (R) {
-            case 2: fft_stage<2, INV>(a, b, p.M, Ns, p.tw); break;
-            case 3: fft_stage<3, INV>(a, b, p.M, Ns, p.tw); break;
-            case 4: fft_stage<4, INV>(a, b, p.M, Ns, p.tw); break;
-            case 5: fft_stage<5, INV>(a, b, p.M, Ns, p.tw); break;
-            case 7: fft_stage<7, INV>(a, b, p.M, Ns, p.tw); break;
-            default: fft_stage<8, INV>(a, b, p.M, Ns, p.tw); break;
+            case 2: fft_stage<2, INV>(in, out, p.M, Ns, tw); break;
+            case 3: fft_stage<3, INV>(in, out, p.M, Ns, tw); break;
+            case 4: fft_stage<4, INV>(in, out, p.M, Ns, tw); break;
+            case 5: fft_stage<5, INV>(in, out, p.M, Ns, tw); break;
+            case 7: fft_stage<7, INV>(in, out, p.M, Ns, tw); break;
+            default: fft_stage<8, INV>(in, out, p.M, Ns, tw); break;
         }
-        float2 *t = a;
-        a = b;
-        b = t;
+        in = out;
         Ns *= R;
     }
-    return a;
+    return in;
+}
+
+// Complex FFT of length M in shared memory, ping-ponging between a and b.
+template <bool INV>
+__device__ const float2 *cta_fft(float2 *a, float2 *b, const FFTPlan &p) {
+    return cta_fft_range<INV>(a, a, b, p, p.tw, 0, p.n_stages);
 }
 
 // ---- forward: real row -> half spectrum -------------------------------------------------
@@ -270,6 +284,139 @@ k_row_c2r(FFTPlan p, const float2 *__restrict__ spec, float *__restrict__ out, i
     }
 }
 
+// ---- persistent row transforms: one CTA per SM, rows streamed in by bulk copies ---------
+// Shared memory: A (staging row, M + 2 entries), B, C (ping-pong, M each), TW (M twiddles),
+// RTW (M + 1 real-split twiddles, padded to M + 2), one mbarrier.  The twiddle tables are
+// loaded once per CTA.  While the transform of row r runs on B / C, the bulk copy of row
+// r + gridDim.x lands in A.
+constexpr int kRowThreads = 512;
+
+size_t row_tma_smem_bytes(int M) { return sizeof(float2) * (5 * (size_t)M + 4) + 16; }
+
+struct RowSmem {
+    float2 *A, *B, *C, *TW, *RTW;
+    uint64_t *bar;
+    __device__ __forceinline__ RowSmem(float4 *base, int M) {
+        A = reinterpret_cast<float2 *>(base);
+        B = A + M + 2;
+        C = B + M;
+        TW = C + M;
+        RTW = TW + M;
+        bar = reinterpret_cast<uint64_t *>(RTW + M + 2);
+    }
+};
+
+__device__ __forceinline__ void row_tma_init(const FFTPlan &p, float2 *TW, float2 *RTW, uint64_t *bar) {
+    for (int k = threadIdx.x; k < p.M; k += blockDim.x) TW[k] = p.tw[k];
+    for (int k = threadIdx.x; k <= p.M; k += blockDim.x) RTW[k] = p.rtw[k];
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+}
+
+// All threads wait for the row; if any thread's bounded wait ran out, thread 0 records the
+// timeout, waits once more (bounded) for the copy in flight, and every thread leaves.
+__device__ __forceinline__ bool row_tma_wait(uint64_t *bar, uint32_t parity, int32_t *status) {
+    const bool ok = mbar_wait(bar, parity);
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) {
+            set_status(status, ST_ETIMEOUT);
+            mbar_wait(bar, parity);
+        }
+        return false;
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(kRowThreads, 1)
+k_row_r2c_tma(FFTPlan p, const float *__restrict__ in, int n_rows, int n_cols, float2 *__restrict__ spec,
+              int32_t *status) {
+    extern __shared__ float4 sm4[];
+    const int M = p.M;
+    const RowSmem L(sm4, M);
+    float2 *A = L.A, *B = L.B, *C = L.C, *TW = L.TW, *RTW = L.RTW;
+    uint64_t *bar = L.bar;
+    const int half = n_cols >> 1;                      // n_cols % 4 == 0
+    const uint32_t bytes = (uint32_t)n_cols * 4u;
+    row_tma_init(p, TW, RTW, bar);
+    for (int k = half + threadIdx.x; k < M + 2; k += blockDim.x) A[k] = make_float2(0.f, 0.f);   // zero pad, kept
+    __syncthreads();
+    int row = blockIdx.x;
+    if (threadIdx.x == 0 && row < n_rows) {
+        mbar_arrive_expect_tx(bar, bytes);
+        bulk_g2s(A, in + (size_t)row * n_cols, bytes, bar);
+    }
+    uint32_t parity = 0;
+    for (; row < n_rows; row += gridDim.x) {
+        if (!row_tma_wait(bar, parity, status)) return;
+        parity ^= 1u;
+        cta_fft_range<false>(A, B, C, p, TW, 0, 1);    // A -> B, ends with a CTA barrier
+        const int next = row + gridDim.x;
+        if (threadIdx.x == 0 && next < n_rows) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(bar, bytes);
+            bulk_g2s(A, in + (size_t)next * n_cols, bytes, bar);
+        }
+        const float2 *Z = cta_fft_range<false>(B, B, C, p, TW, 1, p.n_stages);
+        float2 *out = spec + (size_t)row * p.Fs;
+        for (int k = threadIdx.x; k < p.Fs; k += blockDim.x) {
+            float2 X = make_float2(0.f, 0.f);
+            if (k <= M) {
+                const float2 a = Z[k == M ? 0 : k];
+                const float2 b = conjf2(Z[k == 0 ? 0 : M - k]);
+                const float2 wd = cmul(RTW[k], csub(a, b));
+                const float2 sm = cadd(a, b);
+                X = make_float2(0.5f * (sm.x + wd.y), 0.5f * (sm.y - wd.x));
+            }
+            out[k] = X;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kRowThreads, 1)
+k_row_c2r_tma(FFTPlan p, const float2 *__restrict__ spec, int n_rows, float *__restrict__ out, int n_cols,
+              int32_t *status) {
+    extern __shared__ float4 sm4[];
+    const int M = p.M;
+    const RowSmem L(sm4, M);
+    float2 *A = L.A, *B = L.B, *C = L.C, *TW = L.TW, *RTW = L.RTW;
+    uint64_t *bar = L.bar;
+    const uint32_t bytes = (uint32_t)p.Fs * 8u;        // Fs <= M + 2
+    row_tma_init(p, TW, RTW, bar);
+    __syncthreads();
+    int row = blockIdx.x;
+    if (threadIdx.x == 0 && row < n_rows) {
+        mbar_arrive_expect_tx(bar, bytes);
+        bulk_g2s(A, spec + (size_t)row * p.Fs, bytes, bar);
+    }
+    uint32_t parity = 0;
+    for (; row < n_rows; row += gridDim.x) {
+        if (!row_tma_wait(bar, parity, status)) return;
+        parity ^= 1u;
+        // Z[k] = E + i O, E = (X[k] + conj X[M-k]) / 2, O = exp(2 pi i k / P)(X[k] - conj X[M-k]) / 2
+        for (int k = threadIdx.x; k < M; k += blockDim.x) {
+            const float2 a = A[k];
+            const float2 b = conjf2(A[M - k]);
+            const float2 O = cmul(conjf2(RTW[k]), csub(a, b));
+            const float2 sm = cadd(a, b);
+            B[k] = make_float2(0.5f * (sm.x - O.y), 0.5f * (sm.y + O.x));
+        }
+        __syncthreads();
+        const int next = row + gridDim.x;
+        if (threadIdx.x == 0 && next < n_rows) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(bar, bytes);
+            bulk_g2s(A, spec + (size_t)next * p.Fs, bytes, bar);
+        }
+        const float2 *z = cta_fft_range<true>(B, B, C, p, TW, 0, p.n_stages);
+        float *dst = out + (size_t)row * n_cols;
+        for (int n2 = threadIdx.x; 2 * n2 < n_cols; n2 += blockDim.x) reinterpret_cast<float2 *>(dst)[n2] = z[n2];
+        __syncthreads();
+    }
+}
+
 // ---- wire stage: 21-tap complex stencil across wires per frequency ----------------------
 constexpr int KW = WCT_MAX_RESPONSE_WIRES;   // 21
 constexpr int KC = KW / 2;                   // 10
@@ -315,6 +462,97 @@ k_wire_stage(const float2 *__restrict__ S, const float2 *__restrict__ Rt, int Fs
     }
 }
 
+// ---- wire stage fed by bulk copies -------------------------------------------------------
+// CTA = kStageFB consecutive frequencies x a run of kStageWires output wires.  A producer warp
+// streams the input rows' frequency slices (kStageFB complex = 1 KB each) into a ring of
+// kRing shared-memory slots with bulk copies; the consumer threads (one per frequency) run
+// the same push-form 21-tap stencil as k_wire_stage, reading each input row once from shared
+// memory.  full[s] completes when a slot's copy landed, empty[s] when all consumers read it.
+constexpr int kStageFB = 128;
+constexpr int kStageWires = 128;
+constexpr int kRing = 24;
+
+__global__ void __launch_bounds__(kStageFB + 32)
+k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, int Fs, int n_wires,
+                 float2 *__restrict__ T, int32_t *status) {
+    __shared__ __align__(16) float2 ring[kRing][kStageFB];
+    __shared__ uint64_t full[kRing], empty[kRing];
+    const int tid = threadIdx.x;
+    const int f0 = blockIdx.x * kStageFB;
+    const int nf = min(kStageFB, Fs - f0);             // even (Fs even, f0 multiple of 128)
+    const uint32_t bytes = (uint32_t)nf * 8u;
+    const int w0 = blockIdx.y * kStageWires;
+    const int w1 = min(w0 + kStageWires, n_wires);
+    const int n_in = (w1 - w0) + 2 * KC;               // input rows s = w0 - KC + m
+    const int m_lo = max(0, KC - w0);                  // rows inside the plane: [m_lo, m_hi)
+    const int m_hi = min(n_in, n_wires - w0 + KC);
+    if (tid == 0) {
+        for (int i = 0; i < kRing; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], kStageFB);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid >= kStageFB) {
+        // producer warp: lane 0 issues the copies in order, reusing a slot once it was read
+        if (tid == kStageFB) {
+            for (int m = m_lo; m < m_hi; ++m) {
+                const int idx = m - m_lo, slot = idx % kRing, use = idx / kRing;
+                if (use > 0 && !mbar_wait(&empty[slot], (use - 1) & 1)) {
+                    set_status(status, ST_ETIMEOUT);
+                    break;
+                }
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&full[slot], bytes);
+                bulk_g2s(ring[slot], S + (size_t)(w0 - KC + m) * Fs + f0, bytes, &full[slot]);
+            }
+        }
+        return;
+    }
+    const int f = f0 + tid;
+    const bool live = tid < nf;
+    float2 r[KW], acc[KW];
+#pragma unroll
+    for (int k = 0; k < KW; ++k) {
+        r[k] = live ? Rt[(size_t)k * Fs + f] : make_float2(0.f, 0.f);
+        acc[k] = make_float2(0.f, 0.f);
+    }
+    bool ok = true;
+    for (int mb = 0; mb < n_in; mb += KW) {
+#pragma unroll
+        for (int u = 0; u < KW; ++u) {
+            const int m = mb + u;
+            if (m < n_in) {
+                float2 x = make_float2(0.f, 0.f);
+                if (m >= m_lo && m < m_hi) {
+                    const int idx = m - m_lo, slot = idx % kRing;
+                    if (ok && !mbar_wait(&full[slot], (idx / kRing) & 1)) {
+                        set_status(status, ST_ETIMEOUT);
+                        ok = false;
+                    }
+                    if (ok && live) x = ring[slot][tid];
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[slot])) : "memory");
+                }
+#pragma unroll
+                for (int k = 0; k < KW; ++k) {
+                    const int sl = (u + 1 + k) % KW;
+                    acc[sl].x = fmaf(x.x, r[k].x, fmaf(-x.y, r[k].y, acc[sl].x));
+                    acc[sl].y = fmaf(x.x, r[k].y, fmaf(x.y, r[k].x, acc[sl].y));
+                }
+                const int done = (u + 1) % KW;
+                if (m >= 2 * KC && live) T[(size_t)(w0 + m - 2 * KC) * Fs + f] = acc[done];
+                acc[done] = make_float2(0.f, 0.f);
+            }
+        }
+    }
+    if (!ok && tid == 0) {
+        // after a timeout, wait (bounded) for the last copy this CTA issued before leaving
+        const int idx = m_hi - 1 - m_lo;
+        mbar_wait(&full[idx % kRing], (idx / kRing) & 1);
+    }
+}
+
 // Twiddle tables on the device: tw[k] = exp(-2 pi i k / M) (k < M) and
 // rtw[k] = exp(-2 pi i k / (2M)) (k <= M), evaluated in double precision.
 __global__ void k_make_twiddles(float2 *__restrict__ tw, float2 *__restrict__ rtw, int M) {
@@ -339,9 +577,45 @@ int pick_threads(int M) { return M >= 2048 ? 512 : (M >= 512 ? 256 : 128); }
 
 }  // namespace
 
+namespace {
+
+int device_sms() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+size_t device_smem_optin() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return 0;
+    return (size_t)n;
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+// The persistent bulk-copy kernels need 16-byte aligned rows (n_cols % 4 == 0, dense rows)
+// and their five row-sized buffers in one CTA's shared memory.
+bool use_row_tma(const FFTPlan &p, int64_t stride, int n_cols, const void *ptr) {
+    return (n_cols % 4 == 0) && stride == n_cols && aligned16(ptr) && row_tma_smem_bytes(p.M) <= device_smem_optin() &&
+           device_sms() > 0;
+}
+
+}  // namespace
+
 cudaError_t launch_row_r2c(const FFTPlan &p, const float *in, int64_t in_stride, int n_in_cols, int n_rows,
-                           float2 *spec, cudaStream_t s) {
+                           float2 *spec, cudaStream_t s, int32_t *status) {
     if (n_rows <= 0) return cudaSuccess;
+    if (use_row_tma(p, in_stride, n_in_cols, in) && aligned16(spec)) {
+        const size_t smem = row_tma_smem_bytes(p.M);
+        cudaError_t e = cudaFuncSetAttribute(k_row_r2c_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        const int grid = std::min(n_rows, device_sms());
+        k_row_r2c_tma<<<grid, kRowThreads, smem, s>>>(p, in, n_rows, n_in_cols, spec, status);
+        return cudaGetLastError();
+    }
     const int T = pick_threads(p.M);
     const size_t smem = 2 * sizeof(float2) * (size_t)p.M;
     cudaError_t e = cudaFuncSetAttribute(k_row_r2c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -351,8 +625,16 @@ cudaError_t launch_row_r2c(const FFTPlan &p, const float *in, int64_t in_stride,
 }
 
 cudaError_t launch_row_c2r(const FFTPlan &p, const float2 *spec, int n_rows, float *out, int64_t out_stride,
-                           int n_out_cols, cudaStream_t s) {
+                           int n_out_cols, cudaStream_t s, int32_t *status) {
     if (n_rows <= 0) return cudaSuccess;
+    if (use_row_tma(p, out_stride, n_out_cols, out) && aligned16(spec)) {
+        const size_t smem = row_tma_smem_bytes(p.M);
+        cudaError_t e = cudaFuncSetAttribute(k_row_c2r_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        const int grid = std::min(n_rows, device_sms());
+        k_row_c2r_tma<<<grid, kRowThreads, smem, s>>>(p, spec, n_rows, out, n_out_cols, status);
+        return cudaGetLastError();
+    }
     const int T = pick_threads(p.M);
     const size_t smem = 2 * sizeof(float2) * (size_t)p.M;
     cudaError_t e = cudaFuncSetAttribute(k_row_c2r, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -362,8 +644,13 @@ cudaError_t launch_row_c2r(const FFTPlan &p, const float2 *spec, int n_rows, flo
 }
 
 cudaError_t launch_wire_stage(const FFTPlan &p, const float2 *spec, const float2 *resp_spec, int n_wires, float2 *out,
-                              cudaStream_t s) {
+                              cudaStream_t s, int32_t *status) {
     if (n_wires <= 0) return cudaSuccess;
+    if (aligned16(spec) && (p.Fs % 2) == 0) {
+        dim3 grid((p.Fs + kStageFB - 1) / kStageFB, (n_wires + kStageWires - 1) / kStageWires);
+        k_wire_stage_tma<<<grid, kStageFB + 32, 0, s>>>(spec, resp_spec, p.Fs, n_wires, out, status);
+        return cudaGetLastError();
+    }
     dim3 grid((p.Fs + kStageThreads - 1) / kStageThreads, (n_wires + kStageRun - 1) / kStageRun);
     k_wire_stage<<<grid, kStageThreads, 0, s>>>(spec, resp_spec, p.Fs, n_wires, out);
     return cudaGetLastError();

@@ -40,6 +40,7 @@ struct FFTPlan {
     int32_t M;            // complex length
     int32_t n_stages;
     int32_t radix[12];
+    uint64_t radix_code;  // radix[s] in bits [4s, 4s+4): read in registers, no local-memory array
     int32_t fft_len;      // real length P = 2M
     int32_t F;            // spectrum bins = M + 1
     int32_t Fs;           // spectrum row stride (complex elements), even
@@ -68,11 +69,11 @@ cudaError_t launch_tile_scatter_patches(const int64_t *patch_desc, const float *
                                         cudaStream_t s);
 
 cudaError_t launch_row_r2c(const FFTPlan &p, const float *in, int64_t in_stride, int n_in_cols, int n_rows,
-                           float2 *spec, cudaStream_t s);
+                           float2 *spec, cudaStream_t s, int32_t *status = nullptr);
 cudaError_t launch_wire_stage(const FFTPlan &p, const float2 *spec, const float2 *resp_spec, int n_wires,
-                              float2 *out, cudaStream_t s);
+                              float2 *out, cudaStream_t s, int32_t *status = nullptr);
 cudaError_t launch_row_c2r(const FFTPlan &p, const float2 *spec, int n_rows, float *out, int64_t out_stride,
-                           int n_out_cols, cudaStream_t s);
+                           int n_out_cols, cudaStream_t s, int32_t *status = nullptr);
 cudaError_t launch_scale_spectrum(float2 *spec, int64_t n, float scale, cudaStream_t s);
 cudaError_t launch_make_twiddles(const FFTPlan &p, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, int64_t n, uint32_t *out, cudaStream_t s);

@@ -128,6 +128,8 @@ bool plan_fft(int n_ticks, int kt, FFTPlan &p) {
         }
     }
     p.n_stages = ns;
+    p.radix_code = 0;
+    for (int k = 0; k < ns; ++k) p.radix_code |= (uint64_t)p.radix[k] << (4 * k);
     return r == 1;
 }
 
@@ -241,13 +243,13 @@ wct_status_t raster_scatter(wct_sim *s, int plane, const wct_depos_t *d, float *
 wct_status_t convolve_plane(wct_sim *s, int plane, const float *grid, float *wf, cudaStream_t st, int slot) {
     const PlaneState &ps = s->planes[plane];
     const int nw = ps.g.n_wires, nt = ps.g.n_ticks;
-    cudaError_t e = launch_row_r2c(ps.fft, grid, nt, nt, nw, s->spec, st);
+    cudaError_t e = launch_row_r2c(ps.fft, grid, nt, nt, nw, s->spec, st, s->status);
     if (e != cudaSuccess) return cuda_fail(s, e, "row r2c");
     mark(s, slot, 3, st);
-    e = launch_wire_stage(ps.fft, s->spec, ps.resp_spec, nw, s->spec2, st);
+    e = launch_wire_stage(ps.fft, s->spec, ps.resp_spec, nw, s->spec2, st, s->status);
     if (e != cudaSuccess) return cuda_fail(s, e, "wire stage");
     mark(s, slot, 4, st);
-    e = launch_row_c2r(ps.fft, s->spec2, nw, wf, nt, nt, st);
+    e = launch_row_c2r(ps.fft, s->spec2, nw, wf, nt, nt, st, s->status);
     if (e != cudaSuccess) return cuda_fail(s, e, "row c2r");
     s->launches += 3;
     mark(s, slot, 5, st);
