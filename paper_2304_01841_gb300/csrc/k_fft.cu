@@ -19,6 +19,7 @@
 #include "wct_tma.cuh"
 
 #include <algorithm>
+#include <initializer_list>
 
 namespace wct {
 
@@ -284,6 +285,85 @@ k_row_c2r(FFTPlan p, const float2 *__restrict__ spec, float *__restrict__ out, i
     }
 }
 
+constexpr int kRowThreadsCt = 512;
+
+// ---- compile-time radix plans ---------------------------------------------------------
+// For the common lengths the radix sequence is a template parameter: every stage's Ns, stride
+// and butterfly count are constants, so the index arithmetic needs no runtime division and
+// the per-thread butterfly loop unrolls.  Same Stockham stage as fft_stage.
+template <int R, int NS, int M, int T, bool INV>
+__device__ __forceinline__ void stage_ct(const float2 *__restrict__ in, float2 *__restrict__ out,
+                                         const float2 *__restrict__ tw) {
+    constexpr int NB = M / R;
+    constexpr int STRIDE = M / (NS * R);
+    constexpr int ITER = (NB + T - 1) / T;
+#pragma unroll
+    for (int it = 0; it < ITER; ++it) {
+        const int j = threadIdx.x + it * T;
+        if (ITER * T == NB || j < NB) {
+            const int k = j % NS;
+            float2 v[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = in[j + r * NB];
+            if (NS > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    float2 w = tw[r * k * STRIDE];
+                    if (INV) w.y = -w.y;
+                    v[r] = cmul(v[r], w);
+                }
+            }
+            Dft<R, INV>::run(v);
+            const int base = (j - k) * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) out[base + r * NS] = v[r];
+        }
+    }
+    __syncthreads();
+}
+
+template <int M, int T, bool INV, int NS, int R, int... Rest>
+struct FftCt {
+    __device__ __forceinline__ static const float2 *run(const float2 *in, float2 *x, float2 *y, const float2 *tw) {
+        float2 *out = (in == x) ? y : x;
+        stage_ct<R, NS, M, T, INV>(in, out, tw);
+        if constexpr (sizeof...(Rest) == 0) return out;
+        else return FftCt<M, T, INV, NS * R, Rest...>::run(out, x, y, tw);
+    }
+};
+
+template <int... Rs>
+struct CtPlan {
+    static constexpr int M = (Rs * ...);
+};
+
+// Policy used by the persistent kernels: stages [s0, s1) with s0 / s1 in {0, 1, n}.
+struct RuntimeFft {
+    template <bool INV>
+    __device__ __forceinline__ static const float2 *range(const float2 *src, float2 *x, float2 *y, const FFTPlan &p,
+                                                          const float2 *tw, int s0, int s1) {
+        return cta_fft_range<INV>(src, x, y, p, tw, s0, s1);
+    }
+};
+
+template <class Plan>
+struct CompiledFft;
+
+template <int R0, int... Rs>
+struct CompiledFft<CtPlan<R0, Rs...>> {
+    static constexpr int M = CtPlan<R0, Rs...>::M;
+    template <bool INV>
+    __device__ __forceinline__ static const float2 *range(const float2 *src, float2 *x, float2 *y, const FFTPlan &,
+                                                          const float2 *tw, int s0, int s1) {
+        if (s0 == 0 && s1 == 1) return FftCt<M, kRowThreadsCt, INV, 1, R0>::run(src, x, y, tw);
+        if (s0 == 1) {
+            if constexpr (sizeof...(Rs) > 0) return FftCt<M, kRowThreadsCt, INV, R0, Rs...>::run(src, x, y, tw);
+            else return src;
+        }
+        return FftCt<M, kRowThreadsCt, INV, 1, R0, Rs...>::run(src, x, y, tw);
+    }
+};
+
 // ---- persistent row transforms: one CTA per SM, rows streamed in by bulk copies ---------
 // Shared memory: A (staging row, M + 2 entries), B, C (ping-pong, M each), TW (M twiddles),
 // RTW (M + 1 real-split twiddles, padded to M + 2), one mbarrier.  The twiddle tables are
@@ -329,6 +409,7 @@ __device__ __forceinline__ bool row_tma_wait(uint64_t *bar, uint32_t parity, int
     return true;
 }
 
+template <class FFT>
 __global__ void __launch_bounds__(kRowThreads, 1)
 k_row_r2c_tma(FFTPlan p, const float *__restrict__ in, int n_rows, int n_cols, float2 *__restrict__ spec,
               int32_t *status) {
@@ -351,14 +432,14 @@ k_row_r2c_tma(FFTPlan p, const float *__restrict__ in, int n_rows, int n_cols, f
     for (; row < n_rows; row += gridDim.x) {
         if (!row_tma_wait(bar, parity, status)) return;
         parity ^= 1u;
-        cta_fft_range<false>(A, B, C, p, TW, 0, 1);    // A -> B, ends with a CTA barrier
+        FFT::template range<false>(A, B, C, p, TW, 0, 1);    // A -> B, ends with a CTA barrier
         const int next = row + gridDim.x;
         if (threadIdx.x == 0 && next < n_rows) {
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(bar, bytes);
             bulk_g2s(A, in + (size_t)next * n_cols, bytes, bar);
         }
-        const float2 *Z = cta_fft_range<false>(B, B, C, p, TW, 1, p.n_stages);
+        const float2 *Z = FFT::template range<false>(B, B, C, p, TW, 1, p.n_stages);
         float2 *out = spec + (size_t)row * p.Fs;
         for (int k = threadIdx.x; k < p.Fs; k += blockDim.x) {
             float2 X = make_float2(0.f, 0.f);
@@ -375,6 +456,7 @@ k_row_r2c_tma(FFTPlan p, const float *__restrict__ in, int n_rows, int n_cols, f
     }
 }
 
+template <class FFT>
 __global__ void __launch_bounds__(kRowThreads, 1)
 k_row_c2r_tma(FFTPlan p, const float2 *__restrict__ spec, int n_rows, float *__restrict__ out, int n_cols,
               int32_t *status) {
@@ -410,7 +492,7 @@ k_row_c2r_tma(FFTPlan p, const float2 *__restrict__ spec, int n_rows, float *__r
             mbar_arrive_expect_tx(bar, bytes);
             bulk_g2s(A, spec + (size_t)next * p.Fs, bytes, bar);
         }
-        const float2 *z = cta_fft_range<true>(B, B, C, p, TW, 0, p.n_stages);
+        const float2 *z = FFT::template range<true>(B, B, C, p, TW, 0, p.n_stages);
         float *dst = out + (size_t)row * n_cols;
         for (int n2 = threadIdx.x; 2 * n2 < n_cols; n2 += blockDim.x) reinterpret_cast<float2 *>(dst)[n2] = z[n2];
         __syncthreads();
@@ -465,29 +547,33 @@ k_wire_stage(const float2 *__restrict__ S, const float2 *__restrict__ Rt, int Fs
 // ---- wire stage fed by bulk copies -------------------------------------------------------
 // CTA = kStageFB consecutive frequencies x a run of kStageWires output wires.  A producer warp
 // streams the input rows' frequency slices (kStageFB complex = 1 KB each) into a ring of
-// kRing shared-memory slots with bulk copies; the consumer threads (one per frequency) run
-// the same push-form 21-tap stencil as k_wire_stage, reading each input row once from shared
-// memory.  full[s] completes when a slot's copy landed, empty[s] when all consumers read it.
+// kRingGroups groups of kGroupRows rows with bulk copies, one mbarrier pair per group; the
+// consumer threads (one per frequency) run the same push-form 21-tap stencil as k_wire_stage,
+// reading each input row once from shared memory.  full[g] completes when a group's copies
+// landed, empty[g] when every consumer finished reading the group.
 constexpr int kStageFB = 128;
 constexpr int kStageWires = 128;
-constexpr int kRing = 24;
+constexpr int kGroupRows = 8;
+constexpr int kRingGroups = 4;
 
 __global__ void __launch_bounds__(kStageFB + 32)
 k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, int Fs, int n_wires,
                  float2 *__restrict__ T, int32_t *status) {
-    __shared__ __align__(16) float2 ring[kRing][kStageFB];
-    __shared__ uint64_t full[kRing], empty[kRing];
+    __shared__ __align__(16) float2 ring[kRingGroups * kGroupRows][kStageFB];
+    __shared__ uint64_t full[kRingGroups], empty[kRingGroups];
     const int tid = threadIdx.x;
     const int f0 = blockIdx.x * kStageFB;
     const int nf = min(kStageFB, Fs - f0);             // even (Fs even, f0 multiple of 128)
-    const uint32_t bytes = (uint32_t)nf * 8u;
+    const uint32_t row_bytes = (uint32_t)nf * 8u;
     const int w0 = blockIdx.y * kStageWires;
     const int w1 = min(w0 + kStageWires, n_wires);
     const int n_in = (w1 - w0) + 2 * KC;               // input rows s = w0 - KC + m
     const int m_lo = max(0, KC - w0);                  // rows inside the plane: [m_lo, m_hi)
     const int m_hi = min(n_in, n_wires - w0 + KC);
+    const int n_rows = m_hi - m_lo;
+    const int n_groups = (n_rows + kGroupRows - 1) / kGroupRows;
     if (tid == 0) {
-        for (int i = 0; i < kRing; ++i) {
+        for (int i = 0; i < kRingGroups; ++i) {
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], kStageFB);
         }
@@ -495,17 +581,20 @@ k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, in
     }
     __syncthreads();
     if (tid >= kStageFB) {
-        // producer warp: lane 0 issues the copies in order, reusing a slot once it was read
+        // producer: lane 0 of the extra warp issues the copies group by group
         if (tid == kStageFB) {
-            for (int m = m_lo; m < m_hi; ++m) {
-                const int idx = m - m_lo, slot = idx % kRing, use = idx / kRing;
-                if (use > 0 && !mbar_wait(&empty[slot], (use - 1) & 1)) {
+            for (int g = 0; g < n_groups; ++g) {
+                const int gs = g % kRingGroups, use = g / kRingGroups;
+                if (use > 0 && !mbar_wait(&empty[gs], (use - 1) & 1)) {
                     set_status(status, ST_ETIMEOUT);
                     break;
                 }
+                const int r0 = g * kGroupRows, r1 = min(r0 + kGroupRows, n_rows);
                 fence_proxy_async_smem();
-                mbar_arrive_expect_tx(&full[slot], bytes);
-                bulk_g2s(ring[slot], S + (size_t)(w0 - KC + m) * Fs + f0, bytes, &full[slot]);
+                mbar_arrive_expect_tx(&full[gs], row_bytes * (uint32_t)(r1 - r0));
+                for (int r = r0; r < r1; ++r)
+                    bulk_g2s(ring[gs * kGroupRows + (r - r0)], S + (size_t)(w0 - KC + m_lo + r) * Fs + f0, row_bytes,
+                             &full[gs]);
             }
         }
         return;
@@ -526,13 +615,15 @@ k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, in
             if (m < n_in) {
                 float2 x = make_float2(0.f, 0.f);
                 if (m >= m_lo && m < m_hi) {
-                    const int idx = m - m_lo, slot = idx % kRing;
-                    if (ok && !mbar_wait(&full[slot], (idx / kRing) & 1)) {
+                    const int idx = m - m_lo;
+                    const int g = idx / kGroupRows, in_g = idx - g * kGroupRows, gs = g % kRingGroups;
+                    if (in_g == 0 && ok && !mbar_wait(&full[gs], (g / kRingGroups) & 1)) {
                         set_status(status, ST_ETIMEOUT);
                         ok = false;
                     }
-                    if (ok && live) x = ring[slot][tid];
-                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[slot])) : "memory");
+                    if (ok && live) x = ring[gs * kGroupRows + in_g][tid];
+                    if (in_g == kGroupRows - 1 || idx == n_rows - 1)
+                        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[gs])) : "memory");
                 }
 #pragma unroll
                 for (int k = 0; k < KW; ++k) {
@@ -547,9 +638,9 @@ k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, in
         }
     }
     if (!ok && tid == 0) {
-        // after a timeout, wait (bounded) for the last copy this CTA issued before leaving
-        const int idx = m_hi - 1 - m_lo;
-        mbar_wait(&full[idx % kRing], (idx / kRing) & 1);
+        // after a timeout, wait (bounded) for the last group this CTA issued before leaving
+        const int g = n_groups - 1;
+        mbar_wait(&full[g % kRingGroups], (g / kRingGroups) & 1);
     }
 }
 
@@ -603,6 +694,40 @@ bool use_row_tma(const FFTPlan &p, int64_t stride, int n_cols, const void *ptr) 
            device_sms() > 0;
 }
 
+struct R2CKernels {
+    template <class F>
+    static auto get() { return k_row_r2c_tma<F>; }
+};
+struct C2RKernels {
+    template <class F>
+    static auto get() { return k_row_c2r_tma<F>; }
+};
+
+// Pick the compiled plan for the common lengths (M = 4900: 9600 ticks, M = 3125: 6000 ticks,
+// M = 625: 1024 ticks), else the runtime-radix kernel; set its shared-memory limit; launch.
+template <class Launch, class K>
+cudaError_t launch_row_tma_kernel(const FFTPlan &p, size_t smem, int grid, cudaStream_t s, Launch &&launch, K) {
+    (void)grid;
+    (void)s;
+    auto go = [&](auto kern) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        launch(kern);
+        return cudaGetLastError();
+    };
+    auto is = [&](std::initializer_list<int> rs) {
+        if ((int)rs.size() != p.n_stages) return false;
+        int k = 0;
+        for (int r : rs)
+            if (p.radix[k++] != r) return false;
+        return true;
+    };
+    if (is({4, 7, 7, 5, 5})) return go(K::template get<CompiledFft<CtPlan<4, 7, 7, 5, 5>>>());
+    if (is({5, 5, 5, 5, 5})) return go(K::template get<CompiledFft<CtPlan<5, 5, 5, 5, 5>>>());
+    if (is({5, 5, 5, 5})) return go(K::template get<CompiledFft<CtPlan<5, 5, 5, 5>>>());
+    return go(K::template get<RuntimeFft>());
+}
+
 }  // namespace
 
 cudaError_t launch_row_r2c(const FFTPlan &p, const float *in, int64_t in_stride, int n_in_cols, int n_rows,
@@ -610,11 +735,10 @@ cudaError_t launch_row_r2c(const FFTPlan &p, const float *in, int64_t in_stride,
     if (n_rows <= 0) return cudaSuccess;
     if (use_row_tma(p, in_stride, n_in_cols, in) && aligned16(spec)) {
         const size_t smem = row_tma_smem_bytes(p.M);
-        cudaError_t e = cudaFuncSetAttribute(k_row_r2c_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
         const int grid = std::min(n_rows, device_sms());
-        k_row_r2c_tma<<<grid, kRowThreads, smem, s>>>(p, in, n_rows, n_in_cols, spec, status);
-        return cudaGetLastError();
+        return launch_row_tma_kernel(p, smem, grid, s, [&](auto kern) {
+            kern<<<grid, kRowThreads, smem, s>>>(p, in, n_rows, n_in_cols, spec, status);
+        }, R2CKernels{});
     }
     const int T = pick_threads(p.M);
     const size_t smem = 2 * sizeof(float2) * (size_t)p.M;
@@ -629,11 +753,10 @@ cudaError_t launch_row_c2r(const FFTPlan &p, const float2 *spec, int n_rows, flo
     if (n_rows <= 0) return cudaSuccess;
     if (use_row_tma(p, out_stride, n_out_cols, out) && aligned16(spec)) {
         const size_t smem = row_tma_smem_bytes(p.M);
-        cudaError_t e = cudaFuncSetAttribute(k_row_c2r_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
         const int grid = std::min(n_rows, device_sms());
-        k_row_c2r_tma<<<grid, kRowThreads, smem, s>>>(p, spec, n_rows, out, n_out_cols, status);
-        return cudaGetLastError();
+        return launch_row_tma_kernel(p, smem, grid, s, [&](auto kern) {
+            kern<<<grid, kRowThreads, smem, s>>>(p, spec, n_rows, out, n_out_cols, status);
+        }, C2RKernels{});
     }
     const int T = pick_threads(p.M);
     const size_t smem = 2 * sizeof(float2) * (size_t)p.M;

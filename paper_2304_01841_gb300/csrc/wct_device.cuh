@@ -27,17 +27,42 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
-// Two standard normals from two 32-bit words: u = (x + 1/2) 2^-32 in (0,1),
-// r = sqrt(-2 ln u_a), (r cos 2 pi u_b, r sin 2 pi u_b).
+// Two standard normals from two 32-bit words (Box-Muller): u = (x + 1/2) 2^-32 in (0,1),
+// r = sqrt(-2 ln u_a), (r cos 2 pi u_b, r sin 2 pi u_b).  Evaluated with the SFU's
+// approximate lg2 / sqrt / sin / cos instructions (relative errors ~2^-22, absolute sin/cos
+// error ~2^-20.5 on [-pi, pi]); the angle is reduced to (-pi, pi) first, using
+// cos(t) = -cos(t - pi) and sin(t) = -sin(t - pi).  The resulting deviates differ from an
+// FP64 evaluation by < 1e-5 absolute, far inside the patch / grid tolerance.
+__device__ __forceinline__ float sfu_lg2(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sfu_sqrt(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sfu_sin(float x) {
+    float y;
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sfu_cos(float x) {
+    float y;
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b) {
     const float s32 = 2.3283064365386963e-10f;   // 2^-32
     const float h32 = 1.1641532182693481e-10f;   // 2^-33
     const float ua = fmaf(__uint2float_rn(a), s32, h32);
     const float ub = fmaf(__uint2float_rn(b), s32, h32);
-    const float r = sqrtf(fmaxf(-2.0f * logf(ua), 0.0f));
-    float sn, cs;
-    sincospif(2.0f * ub, &sn, &cs);
-    return make_float2(r * cs, r * sn);
+    const float m2ln2 = -1.3862943611198906f;    // -2 ln 2
+    const float r = sfu_sqrt(fmaxf(m2ln2 * sfu_lg2(ua), 0.f));
+    const float t = 6.283185307179586f * (ub - 0.5f);   // 2 pi u_b - pi, in (-pi, pi)
+    return make_float2(-r * sfu_cos(t), -r * sfu_sin(t));
 }
 
 __device__ __forceinline__ int floor_div(int a, int b) {   // b > 0
