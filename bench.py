@@ -4,8 +4,10 @@
 Workload: one MicroBooNE-sized collection plane, 3456 wires x 9600 ticks (0.5 us), 100k depos
 on 20 straight tracks, drift 0-2.3 ms, fluctuation on, 21 x 200 synthetic response.  A step
 is one batch of --batch such events (distinct seeds / event ids, depos resident in HBM), each
-going through the whole path: depo prep + tile binning, fused rasterize + fluctuate + scatter,
-forward row FFT, wire stage, inverse row FFT.  value = depos/s over the whole job.
+going through the whole path: grid clear, fused drift/window + rasterize + fluctuate + scatter,
+forward row FFT, wire stage, inverse row FFT.  value = depos/s over the whole job.  The JSON
+line also carries the batched form (64 uneven three-plane events per run_batch) and the served
+form (APA-like stream, continuous batching, p50/p99 latency).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -43,6 +45,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched / served measurements")
     return ap.parse_args()
 
 
@@ -146,6 +149,23 @@ def csrc_digest():
     return h.hexdigest()[:16]
 
 
+def shard_plan(rank: int, world: int, events_per_rank: int, base_seed: int):
+    """Weak scaling: rank r simulates its own events_per_rank events (seeds and event ids
+    disjoint across ranks); no data crosses ranks."""
+    return [(base_seed + 1000 * rank + e, rank * events_per_rank + e) for e in range(events_per_rank)]
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The job's time is the slowest rank's (all-reduce MAX; identity for one rank)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def oracle_sample(wl, n_sample=ORACLE_SAMPLE_DEPOS, seed_offset=0):
     """Time the FP64 oracle on a bounded sample of the workload: the first n_sample depos
     of one event rasterized + scattered (C, 1 thread) and the full-grid FFT convolution
@@ -198,6 +218,95 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------------------------
+# batched and served forms (three-plane batch of uneven events; APA-like serving stream)
+# --------------------------------------------------------------------------------------------
+def _slice_pool(pool, counts, rng, first_event_id):
+    """Events of the given depo counts cut from a pool of large generated events (each a
+    contiguous slice, i.e. whole track segments), with distinct event ids."""
+    import synth
+    out = []
+    for i, n in enumerate(counts):
+        base = pool[int(rng.integers(len(pool)))]
+        n = int(min(n, base.n))
+        s0 = int(rng.integers(0, base.n - n + 1))
+        d = base.subset(slice(s0, s0 + n))
+        out.append(synth.Depos(d.t0, d.x, d.y, d.z, d.q, event_id=first_event_id + i))
+    return out
+
+
+def measure_batch(n_events=64, reps=5):
+    """Batched: n_events three-plane events (2400/2400/3456 x 9600), depo counts lognormal
+    10k..500k, one run_batch (batched raster launch + graph-replayed convolutions) against the
+    same events one run_event at a time.  Returns events/s of both."""
+    import numpy as np
+    import torch
+    import paper_2304_01841_gb300 as pkg
+    import synth
+    wl = synth.workload("three_plane")
+    counts = synth.batch_depo_counts(n_events)
+    pool = [wl.depos(n_depos=500_000, seed=wl.seed + k) for k in range(3)]
+    evs = _slice_pool(pool, counts, np.random.default_rng(7), 5000)
+    sim = pkg.Simulator(wl.planes, wl.responses(), wl.diffusion)
+    dev = [pkg.DeviceDepos.from_host(e) for e in evs]
+    outs = [[torch.empty((p.n_wires, p.n_ticks), dtype=torch.float32, device="cuda") for p in wl.planes]
+            for _ in evs]
+    st = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for _ in range(reps):
+            fn()
+        b.record(st)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1000.0
+
+    t_batch = timed(lambda: sim.run_batch(dev, outs))
+    t_single = timed(lambda: [sim.run_event(d, o) for d, o in zip(dev, outs)])
+    sim.sync()
+    n = reps * n_events
+    sim.close()
+    return {"workload": "64 three-plane events (2400/2400/3456 x 9600), depos lognormal 10k-500k",
+            "depos_per_batch": int(sum(e.n for e in evs)), "events_per_s_batched": n / t_batch,
+            "events_per_s_one_at_a_time": n / t_single,
+            "depos_per_s_batched": reps * sum(e.n for e in evs) / t_batch}
+
+
+def measure_serving(n_events=120, loads=(0.5, 0.8, 0.95)):
+    """Served: APA-like planes (800/800/960 x 6000), heavy-tailed depo counts (90% 5k-50k,
+    10% 1M-3M), open-loop Poisson arrivals at fractions of the measured capacity."""
+    import numpy as np
+    import synth
+    from paper_2304_01841_gb300.serve import EventServer, pin_depos, run_open_loop
+    wl = synth.workload("dune_apa")
+    pool = [wl.depos(n_depos=3_000_000, seed=wl.seed + k) for k in range(2)]
+    counts = synth.serving_depo_counts(n_events)
+    evs = [pin_depos(e) for e in _slice_pool(pool, counts, np.random.default_rng(9), 9000)]
+    srv = EventServer(wl.planes, wl.responses(), wl.diffusion, n_slots=4, max_batch=8,
+                      hbm_budget_bytes=24 << 30)
+    # capacity: everything submitted at once
+    for e in evs[:16]:
+        srv.submit(e)
+    srv.drain()
+    t0 = time.perf_counter()
+    for e in evs:
+        srv.submit(e)
+    srv.drain()
+    cap = len(evs) / (time.perf_counter() - t0)
+    points = []
+    for i, f in enumerate(loads):
+        r = run_open_loop(srv, evs, rate_hz=f * cap, seed=i)
+        r["load"] = f
+        points.append(r)
+    srv.close()
+    return {"workload": "APA-like 800/800/960 x 6000, 90% 5k-50k / 10% 1M-3M depos, Poisson arrivals",
+            "capacity_events_per_s": cap, "open_loop": points}
+
+
+# --------------------------------------------------------------------------------------------
 # our arm
 # --------------------------------------------------------------------------------------------
 def main():
@@ -230,10 +339,7 @@ def main():
     E = args.batch
     sim = pkg.Simulator(wl.planes, wl.responses(), wl.diffusion)
     # E distinct events per rank, resident in HBM (weak scaling: each rank its own events)
-    host_events = []
-    for e in range(E):
-        d = wl.depos(seed=wl.seed + 1000 * rank + e, event_id=rank * E + e)
-        host_events.append(d)
+    host_events = [wl.depos(seed=seed, event_id=eid) for seed, eid in shard_plan(rank, world, E, wl.seed)]
     dev_events = [pkg.DeviceDepos.from_host(d) for d in host_events]
     outs = [[torch.empty((plane.n_wires, plane.n_ticks), dtype=torch.float32, device="cuda")] for _ in range(E)]
     stream = torch.cuda.current_stream()
@@ -282,10 +388,7 @@ def main():
     lat = sorted(ev[j].elapsed_time(ev[j + 1]) for j in range(K * E))
     p50 = lat[len(lat) // 2]
     p99 = lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(elapsed_ms, world, "cuda")
     total_events = world * K * E
     value = total_events * n_depos / (elapsed_ms / 1000.0)
 
@@ -347,10 +450,7 @@ def main():
         torch.cuda.synchronize()
         barrier()
         e2e_ms = s0.elapsed_time(s1)
-        if world > 1:
-            t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
+        e2e_ms = max_over_ranks(e2e_ms, world, "cuda")
         e2e = {"value": world * K * E * n_depos / (e2e_ms / 1000.0), "unit": "depos/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "events_per_s": world * K * E / (e2e_ms / 1000.0)}
@@ -363,6 +463,11 @@ def main():
         cpu = {"value": ORACLE_SAMPLE_DEPOS / t, "unit": "depos/s", "cores": threads, "kind": "oracle",
                "sample": f"{ORACLE_SAMPLE_DEPOS} depos of one event rasterized + scattered (C FP64, 1 thread) "
                          f"+ full-grid FFT convolution (scipy FP64, {threads} threads), one run"}
+
+    extras = {}
+    if rank == 0 and world == 1 and not args.no_extras:
+        extras["batch"] = measure_batch()
+        extras["serving"] = measure_serving()
 
     if rank == 0:
         line = {
@@ -383,6 +488,7 @@ def main():
             "clocks": clk,
             "wall_s": wall,
         }
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

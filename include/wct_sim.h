@@ -173,7 +173,12 @@ wct_status_t wct_sim_run_event(wct_sim_t *sim, const wct_depos_t *depos, float *
                                void *stream);
 
 /* Several events in one pass: events[e] for e < n_events; waveforms: HOST array of
- * n_events * n_planes DEVICE pointers, event-major. */
+ * n_events * n_planes DEVICE pointers, event-major.  Every (event, plane) grid is cleared,
+ * all pairs are rasterized and scattered by one batched launch (per 256 pairs), then each
+ * grid is convolved in place.  When a call repeats an earlier call's pointers, depo counts
+ * and event ids, the sequence is recorded as a CUDA graph, and later repeats replay it (up
+ * to 8 graphs are kept per handle); the depo values themselves may change between replays.  Results equal
+ * those of wct_sim_run_event for each event. */
 wct_status_t wct_sim_run_batch(wct_sim_t *sim, const wct_depos_t *events, int n_events,
                                float *const *waveforms, void *stream);
 
@@ -194,8 +199,9 @@ wct_status_t wct_sim_plane_info(const wct_sim_t *sim, int plane, int64_t *info);
 wct_status_t wct_sim_set_timing(wct_sim_t *sim, int enable);
 wct_status_t wct_sim_stage_times(wct_sim_t *sim, float *us, int n);
 
-/* Counters of this handle: out[0] = kernels launched so far, out[1] = bytes of device
- * memory the library holds.  Host call, no device work. */
+/* Counters of this handle: out[0] = kernels launched so far (enqueued directly or recorded
+ * into a graph), out[1] = bytes of device memory the library holds, out[2] = batch graphs
+ * launched.  Host call, no device work. */
 wct_status_t wct_sim_counters(const wct_sim_t *sim, int64_t *out, int n);
 
 /* Human-readable description of the last error on this handle ("" if none). */

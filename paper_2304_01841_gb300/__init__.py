@@ -188,9 +188,9 @@ class Simulator:
         return out
 
     def counters(self) -> dict:
-        c = (ctypes.c_int64 * 2)()
-        self._check(self._lib.wct_sim_counters(self._h, c, 2))
-        return {"kernel_launches": int(c[0]), "device_bytes": int(c[1])}
+        c = (ctypes.c_int64 * 3)()
+        self._check(self._lib.wct_sim_counters(self._h, c, 3))
+        return {"kernel_launches": int(c[0]), "device_bytes": int(c[1]), "graph_launches": int(c[2])}
 
 
 def philox4x32_10(ctr, seed: int, stream=None):

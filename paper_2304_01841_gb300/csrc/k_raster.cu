@@ -183,14 +183,14 @@ __device__ __forceinline__ void segmented_add(int key, float v, float *sums) {
     if (key >= 0 && (lane == 31 || next != key)) atomicAdd(&sums[key], v);
 }
 
-__global__ void __launch_bounds__(kChunkThreads)
-k_raster_chunks(const float *__restrict__ t0, const float *__restrict__ x, const float *__restrict__ y,
-                const float *__restrict__ z, const float *__restrict__ q, int64_t n, PlaneParams pp,
-                uint32_t event_lo, float *__restrict__ grid, int32_t *status) {
-    extern __shared__ float4 smem_raw[];
-    ChunkSmem &S = *reinterpret_cast<ChunkSmem *>(smem_raw);
+// One chunk of one event's depos for one plane (the body of the fused kernels below).
+__device__ __forceinline__ void raster_chunk(ChunkSmem &S, const float *__restrict__ t0, const float *__restrict__ x,
+                                             const float *__restrict__ y, const float *__restrict__ z,
+                                             const float *__restrict__ q, int64_t n, const PlaneParams &pp,
+                                             uint32_t event_lo, float *__restrict__ grid, int32_t *status,
+                                             int64_t chunk) {
     const int tid = threadIdx.x, lane = tid & 31;
-    const int64_t c0 = (int64_t)blockIdx.x * kChunk;
+    const int64_t c0 = chunk * kChunk;
     const int cn = (int)((n - c0) < kChunk ? (n - c0) : kChunk);
     const uint32_t c3 = counter_c3(pp, event_lo);
 
@@ -326,6 +326,33 @@ k_raster_chunks(const float *__restrict__ t0, const float *__restrict__ x, const
         __syncthreads();
         s = e;
     }
+}
+
+__global__ void __launch_bounds__(kChunkThreads)
+k_raster_chunks(const float *__restrict__ t0, const float *__restrict__ x, const float *__restrict__ y,
+                const float *__restrict__ z, const float *__restrict__ q, int64_t n, PlaneParams pp,
+                uint32_t event_lo, float *__restrict__ grid, int32_t *status) {
+    extern __shared__ float4 smem_raw[];
+    ChunkSmem &S = *reinterpret_cast<ChunkSmem *>(smem_raw);
+    raster_chunk(S, t0, x, y, z, q, n, pp, event_lo, grid, status, blockIdx.x);
+}
+
+// Many (event, plane) pairs in one launch: CTA b takes chunk b - chunk_begin[i] of the pair i
+// whose chunk range holds b.
+__global__ void __launch_bounds__(kChunkThreads)
+k_raster_batch(const BatchTable tab, int32_t *status) {
+    extern __shared__ float4 smem_raw[];
+    ChunkSmem &S = *reinterpret_cast<ChunkSmem *>(smem_raw);
+    const int64_t b = blockIdx.x;
+    int lo = 0, hi = tab.n_items;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (tab.item[mid].chunk_begin <= b) lo = mid;
+        else hi = mid;
+    }
+    const BatchItem &it = tab.item[lo];
+    raster_chunk(S, it.t0, it.x, it.y, it.z, it.q, it.n, tab.plane[it.plane], it.event_lo, it.grid, status,
+                 b - it.chunk_begin);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -476,6 +503,17 @@ constexpr int kTileW = 32, kTileT = 256;
 
 int tile_wires() { return kTileW; }
 int tile_ticks() { return kTileT; }
+
+int64_t raster_chunk_count(int64_t n) { return (n + kChunk - 1) / kChunk; }
+
+cudaError_t launch_raster_batch(const BatchTable &tab, int64_t total_chunks, int32_t *status, cudaStream_t s) {
+    if (total_chunks <= 0) return cudaSuccess;
+    const size_t smem = sizeof(ChunkSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_raster_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_raster_batch<<<(unsigned)total_chunks, kChunkThreads, smem, s>>>(tab, status);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_raster_chunks(const wct_depos_t &d, const PlaneParams &pp, uint32_t event_lo, float *grid,
                                  int32_t *status, cudaStream_t s) {

@@ -48,6 +48,25 @@ struct FFTPlan {
     float2 *rtw;          // device: exp(-2 pi i k / P), k <= M
 };
 
+// One (event, plane) pair of a batched rasterize + scatter launch.
+struct BatchItem {
+    const float *t0, *x, *y, *z, *q;
+    int64_t n;
+    float *grid;
+    int64_t chunk_begin;   // first CTA of this pair (prefix sum of its chunk counts)
+    uint32_t event_lo;
+    int32_t plane;
+};
+
+// Passed by value as the kernel parameter (up to kBatchItems pairs, ~21 KB).
+constexpr int kBatchItems = 256;
+constexpr int kMaxPlanesDev = 8;
+struct BatchTable {
+    PlaneParams plane[kMaxPlanesDev];
+    BatchItem item[kBatchItems];
+    int32_t n_items;
+};
+
 // ---- launchers (stream-ordered; return cudaError_t of the launch) -------------------------
 cudaError_t launch_prep(const wct_depos_t &d, const PlaneParams &pp, DepoDesc *desc, int32_t *tile_count,
                         int64_t *patch_size, int32_t *status, cudaStream_t s);
@@ -57,6 +76,8 @@ int64_t scan_tmp_elems(int64_t n);
 
 cudaError_t launch_raster_chunks(const wct_depos_t &d, const PlaneParams &pp, uint32_t event_lo, float *grid,
                                  int32_t *status, cudaStream_t s);
+cudaError_t launch_raster_batch(const BatchTable &tab, int64_t total_chunks, int32_t *status, cudaStream_t s);
+int64_t raster_chunk_count(int64_t n);
 cudaError_t launch_rasterize_patches(int64_t n, const DepoDesc *desc, const int64_t *offsets, const PlaneParams &pp,
                                      uint32_t event_lo, float *patches, int64_t *patch_desc, cudaStream_t s);
 cudaError_t launch_bin_patches(int64_t n, const int64_t *patch_desc, const PlaneParams &pp, int32_t *tile_count,

@@ -63,6 +63,16 @@ struct wct_sim {
     int slots_used = 0;
     int events_timed = 0;
     int64_t launches = 0;   // kernels launched by this handle
+    // run_batch: CUDA graphs of whole batches, keyed by the batch's pointers and sizes
+    cudaStream_t cap_stream = nullptr;
+    struct Graph {
+        std::vector<uint64_t> key;
+        cudaGraphExec_t exec;
+        int64_t kernels;   // kernels recorded in the graph
+    };
+    std::vector<Graph> graphs;
+    std::vector<std::vector<uint64_t>> seen;   // recent batch keys not (yet) recorded
+    int64_t graph_launches = 0;
 };
 
 namespace {
@@ -387,6 +397,8 @@ wct_status_t wct_sim_destroy(wct_sim_t *s) {
         if (a) cudaFree(a);
     for (auto &slot : s->slots)
         for (auto &e : slot) cudaEventDestroy(e);
+    for (auto &g : s->graphs) cudaGraphExecDestroy(g.exec);
+    if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     delete s;
     return WCT_OK;
 }
@@ -468,14 +480,141 @@ wct_status_t wct_sim_run_event(wct_sim_t *s, const wct_depos_t *d, float *const 
     return WCT_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+constexpr size_t kMaxGraphs = 8;
+
+// All (event, plane) pairs: grids cleared, one batched rasterize + scatter launch per group
+// of up to kBatchItems pairs, then the convolution of every grid (in place).
+wct_status_t enqueue_batch(wct_sim *s, const wct_depos_t *events, int n_events, float *const *wfs, cudaStream_t st) {
+    const int npl = s->n_planes;
+    const int total = n_events * npl;
+    static thread_local BatchTable tab;   // ~21 KB: kept off the stack
+    for (int g0 = 0; g0 < total; g0 += kBatchItems) {
+        const int g1 = std::min(total, g0 + kBatchItems);
+        for (int p = 0; p < npl; ++p) tab.plane[p] = s->planes[p].pp;
+        int64_t chunks = 0;
+        tab.n_items = 0;
+        for (int it = g0; it < g1; ++it) {
+            const int e = it / npl, p = it % npl;
+            const wct_depos_t &d = events[e];
+            const PlaneState &ps = s->planes[p];
+            cudaError_t err = cudaMemsetAsync(wfs[it], 0, sizeof(float) * (size_t)ps.g.n_wires * ps.g.n_ticks, st);
+            if (err != cudaSuccess) return cuda_fail(s, err, "grid clear");
+            if (d.n <= 0) continue;
+            BatchItem &b = tab.item[tab.n_items++];
+            b.t0 = d.t0_us;
+            b.x = d.x_mm;
+            b.y = d.y_mm;
+            b.z = d.z_mm;
+            b.q = d.q_e;
+            b.n = d.n;
+            b.grid = wfs[it];
+            b.chunk_begin = chunks;
+            b.event_lo = (uint32_t)d.event_id;
+            b.plane = p;
+            chunks += raster_chunk_count(d.n);
+        }
+        if (chunks > 0) {
+            cudaError_t err = launch_raster_batch(tab, chunks, s->status, st);
+            if (err != cudaSuccess) return cuda_fail(s, err, "batched raster-scatter");
+            s->launches += 1;
+        }
+    }
+    for (int it = 0; it < total; ++it) {
+        wct_status_t r = convolve_plane(s, it % npl, wfs[it], wfs[it], st, -1);
+        if (r) return r;
+    }
+    return WCT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 wct_status_t wct_sim_run_batch(wct_sim_t *s, const wct_depos_t *events, int n_events, float *const *wfs,
                                void *stream) {
     if (!s) return WCT_EINVAL;
     if (n_events < 0 || (n_events > 0 && (!events || !wfs))) return fail(s, WCT_EINVAL, "bad batch arguments");
     for (int e = 0; e < n_events; ++e) {
-        wct_status_t st = wct_sim_run_event(s, &events[e], wfs + (size_t)e * s->n_planes, stream);
+        wct_status_t st = check_depos(s, &events[e]);
         if (st) return st;
+        for (int p = 0; p < s->n_planes; ++p)
+            if (!wfs[(size_t)e * s->n_planes + p]) return fail(s, WCT_EINVAL, "a waveform pointer is NULL");
     }
+    if (n_events == 0) return WCT_OK;
+    cudaStream_t cs = (cudaStream_t)stream;
+    // graph key: everything the recorded launches depend on
+    std::vector<uint64_t> key;
+    key.reserve((size_t)n_events * (7 + s->n_planes) + 1);
+    key.push_back((uint64_t)n_events);
+    for (int e = 0; e < n_events; ++e) {
+        const wct_depos_t &d = events[e];
+        for (const void *ptr : {(const void *)d.t0_us, (const void *)d.x_mm, (const void *)d.y_mm,
+                                (const void *)d.z_mm, (const void *)d.q_e})
+            key.push_back((uint64_t)(uintptr_t)ptr);
+        key.push_back((uint64_t)d.n);
+        key.push_back(d.event_id);
+        for (int p = 0; p < s->n_planes; ++p) key.push_back((uint64_t)(uintptr_t)wfs[(size_t)e * s->n_planes + p]);
+    }
+    for (auto &g : s->graphs) {
+        if (g.key == key) {
+            cudaError_t e = cudaGraphLaunch(g.exec, cs);
+            if (e != cudaSuccess) return cuda_fail(s, e, "graph launch");
+            ++s->graph_launches;
+            s->launches += g.kernels;
+            return WCT_OK;
+        }
+    }
+    // record a graph only for a batch seen before: one-off batches launch directly
+    auto it = std::find(s->seen.begin(), s->seen.end(), key);
+    if (it == s->seen.end()) {
+        if (s->seen.size() >= kMaxGraphs) s->seen.erase(s->seen.begin());
+        s->seen.push_back(key);
+        return enqueue_batch(s, events, n_events, wfs, cs);
+    }
+    s->seen.erase(it);
+    if (!s->cap_stream) {
+        cudaError_t e = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(s, e, "capture stream");
+    }
+    cudaError_t e = cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return enqueue_batch(s, events, n_events, wfs, cs);   // no graph: launch directly
+    }
+    const int64_t launches0 = s->launches;
+    wct_status_t st = enqueue_batch(s, events, n_events, wfs, s->cap_stream);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(s->cap_stream, &graph);
+    if (st != WCT_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        s->launches = launches0;
+        if (st != WCT_OK) return st;
+        return enqueue_batch(s, events, n_events, wfs, cs);
+    }
+    const int64_t recorded = s->launches - launches0;
+    s->launches = launches0;   // counted when the graph runs
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        s->launches = launches0;
+        return enqueue_batch(s, events, n_events, wfs, cs);
+    }
+    if (s->graphs.size() >= kMaxGraphs) {
+        cudaGraphExecDestroy(s->graphs.front().exec);
+        s->graphs.erase(s->graphs.begin());
+    }
+    s->graphs.push_back({std::move(key), exec, recorded});
+    e = cudaGraphLaunch(exec, cs);
+    if (e != cudaSuccess) return cuda_fail(s, e, "graph launch");
+    ++s->graph_launches;
+    s->launches += recorded;
     return WCT_OK;
 }
 
@@ -538,6 +677,7 @@ wct_status_t wct_sim_counters(const wct_sim_t *s, int64_t *out, int n) {
     if (!s || !out || n < 0) return WCT_EINVAL;
     if (n > 0) out[0] = s->launches;
     if (n > 1) out[1] = (int64_t)s->bytes;
+    if (n > 2) out[2] = s->graph_launches;
     return WCT_OK;
 }
 

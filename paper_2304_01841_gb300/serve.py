@@ -1,0 +1,188 @@
+"""Continuous-batching event server over the CUDA library.
+
+Requests (one event's depos each, in host memory) arrive at any time.  The scheduler keeps
+`n_slots` slots; each slot owns a simulator handle (its own scratch) and a CUDA stream, so
+slots run concurrently on the device.  Whenever a slot is free, the scheduler admits the
+oldest pending requests whose device memory (depo arrays + waveforms) fits the remaining HBM
+budget, up to `max_batch` per slot, copies their depos to the device and launches them as one
+batch (one batched rasterize + scatter launch, then the convolutions) on that slot's stream.
+A request that arrives while others are on the GPU is admitted as soon as a slot and memory
+free up.  Latency is submit -> completion observed on the host.
+
+The results of a request do not depend on what it was batched with: the fluctuation stream is
+keyed by (seed, event id, plane, depo index, bin), so each event is the same alone and in a mix
+up to the FP32 summation order of the scatter.
+"""
+from __future__ import annotations
+
+import collections
+import threading
+import time
+from dataclasses import dataclass, field
+from typing import Deque, List, Optional, Sequence
+
+import numpy as np
+
+from . import DeviceDepos, Simulator
+
+
+@dataclass
+class Request:
+    rid: int
+    depos: object                    # host-side SoA (t0, x, y, z, q arrays, event_id)
+    t_submit: float = 0.0
+    t_admit: float = 0.0
+    t_done: float = 0.0
+    waveforms: Optional[List] = None   # host float32 arrays, one per plane (if keep_results)
+    done: threading.Event = field(default_factory=threading.Event)
+
+    @property
+    def latency(self) -> float:
+        return self.t_done - self.t_submit
+
+
+def _host_tensor(torch, a):
+    # pinned host tensors are copied asynchronously; numpy arrays are pinned here
+    if isinstance(a, torch.Tensor):
+        return a
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).pin_memory()
+
+
+def pin_depos(d):
+    """Host depos with their arrays moved to pinned memory (for asynchronous uploads)."""
+    import torch
+    out = type("PinnedDepos", (), {})()
+    for k in ("t0", "x", "y", "z", "q"):
+        setattr(out, k, _host_tensor(torch, getattr(d, k)))
+    out.event_id = int(d.event_id)
+    return out
+
+
+class _Slot:
+    def __init__(self, sim: Simulator, stream):
+        self.sim = sim
+        self.stream = stream
+        self.batch: List[Request] = []
+        self.dev: List[DeviceDepos] = []
+        self.outs: List[List] = []
+        self.done_event = None
+        self.bytes = 0
+
+
+class EventServer:
+    def __init__(self, planes, responses, diffusion, n_slots: int = 4, max_batch: int = 8,
+                 hbm_budget_bytes: int = 16 << 30, keep_results: bool = False):
+        import torch
+        self.torch = torch
+        self.planes = list(planes)
+        self.slots = [_Slot(Simulator(planes, responses, diffusion), torch.cuda.Stream()) for _ in range(n_slots)]
+        self.max_batch = max_batch
+        self.budget = int(hbm_budget_bytes)
+        self.in_use = 0
+        self.keep = keep_results
+        self.pending: Deque[Request] = collections.deque()
+        self.lock = threading.Lock()
+        self.completed: List[Request] = []
+        self._next = 0
+        self.plane_bytes = sum(4 * p.n_wires * p.n_ticks for p in self.planes)
+
+    # -- request side ------------------------------------------------------------------------
+    def submit(self, depos) -> Request:
+        with self.lock:
+            r = Request(self._next, depos, t_submit=time.perf_counter())
+            self._next += 1
+            self.pending.append(r)
+        return r
+
+    def request_bytes(self, r: Request) -> int:
+        return 20 * int(len(r.depos.t0)) + self.plane_bytes
+
+    # -- scheduler ---------------------------------------------------------------------------
+    def _launch(self, slot: _Slot, batch: List[Request]):
+        torch = self.torch
+        slot.batch = batch
+        slot.bytes = sum(self.request_bytes(r) for r in batch)
+        now = time.perf_counter()
+        with torch.cuda.stream(slot.stream):
+            slot.dev = []
+            for r in batch:
+                r.t_admit = now
+                d = r.depos
+                dev = [_host_tensor(torch, a).to("cuda", non_blocking=True) for a in (d.t0, d.x, d.y, d.z, d.q)]
+                slot.dev.append(DeviceDepos(*dev, event_id=int(d.event_id)))
+            slot.outs = [[torch.empty((p.n_wires, p.n_ticks), dtype=torch.float32, device="cuda")
+                          for p in self.planes] for _ in batch]
+            slot.sim.run_batch(slot.dev, slot.outs, stream=slot.stream)
+            if self.keep:
+                slot.host = [[o.to("cpu", non_blocking=True) for o in ev] for ev in slot.outs]
+            slot.done_event = torch.cuda.Event()
+            slot.done_event.record(slot.stream)
+
+    def _retire(self, slot: _Slot):
+        now = time.perf_counter()
+        slot.sim.sync(stream=slot.stream)
+        for i, r in enumerate(slot.batch):
+            r.t_done = now
+            if self.keep:
+                r.waveforms = [h.numpy() for h in slot.host[i]]
+            r.done.set()
+            self.completed.append(r)
+        self.in_use -= slot.bytes
+        slot.batch, slot.dev, slot.outs, slot.done_event, slot.bytes = [], [], [], None, 0
+
+    def step(self) -> int:
+        """One scheduler pass: retire finished slots, admit pending requests into free slots.
+        Returns the number of requests still pending or in flight."""
+        for slot in self.slots:
+            if slot.done_event is not None and slot.done_event.query():
+                self._retire(slot)
+        for slot in self.slots:
+            if slot.done_event is not None:
+                continue
+            batch: List[Request] = []
+            need_total = 0
+            with self.lock:
+                while self.pending and len(batch) < self.max_batch:
+                    need = self.request_bytes(self.pending[0])
+                    if self.in_use + need_total + need > self.budget and (batch or self.in_use > 0):
+                        break                       # wait for memory to free up
+                    need_total += need
+                    batch.append(self.pending.popleft())
+            if not batch:
+                break
+            self._launch(slot, batch)
+            self.in_use += slot.bytes
+        with self.lock:
+            return len(self.pending) + sum(len(s.batch) for s in self.slots)
+
+    def drain(self):
+        while self.step() > 0:
+            time.sleep(0)
+
+    def close(self):
+        self.drain()
+        for s in self.slots:
+            s.sim.close()
+
+
+def run_open_loop(server: EventServer, events: Sequence, rate_hz: float, seed: int = 0) -> dict:
+    """Submit `events` with Poisson inter-arrival times at `rate_hz` while running the
+    scheduler; return latency percentiles (ms) and throughput."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate_hz, len(events))
+    t_next = time.perf_counter()
+    reqs = []
+    i = 0
+    t0 = time.perf_counter()
+    while i < len(events) or server.step() > 0:
+        now = time.perf_counter()
+        while i < len(events) and now >= t_next:
+            reqs.append(server.submit(events[i]))
+            t_next += gaps[i]
+            i += 1
+        server.step()
+    t1 = time.perf_counter()
+    lat = np.array([r.latency for r in reqs]) * 1e3
+    return {"events": len(reqs), "offered_hz": rate_hz, "events_per_s": len(reqs) / (t1 - t0),
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean())}

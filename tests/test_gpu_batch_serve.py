@@ -1,0 +1,113 @@
+"""GPU tests of the batched and served forms: every event gives the result it gives alone."""
+import numpy as np
+import pytest
+
+import synth
+from helpers import make_sim, rel_l2, to_np
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2304_01841_gb300 as g
+    g.load(build_if_missing=True)
+
+
+def _small_three_plane():
+    a = np.radians(60.0)
+    planes = [synth.Plane(96, 1200, wire_angle_rad=a, pitch_origin_mm=-144.0, response_kind="bipolar"),
+              synth.Plane(96, 1200, wire_angle_rad=-a, pitch_origin_mm=-144.0, response_kind="bipolar"),
+              synth.Plane(120, 1200, pitch_origin_mm=-180.0, response_kind="unipolar")]
+    responses = [synth.make_response(p.response_kind) for p in planes]
+    return planes, responses
+
+
+def _events(n_events, seed=0, lo=50, hi=4000, id0=0):
+    rng = np.random.default_rng(seed)
+    out = []
+    for e in range(n_events):
+        n = int(rng.integers(lo, hi))
+        d = synth.make_track_depos(rng, n, 3, rng.uniform(50, 250, 3), [0, -40, -150], [900, 40, 150], True)
+        d.event_id = id0 + e
+        out.append(d)
+    return out
+
+
+def _close(a, b, scale):
+    return float(np.abs(a - b).max()) <= 1e-5 * max(scale, 1.0)
+
+
+def test_batch_multiplane_matches_single_and_graph_replay():
+    import paper_2304_01841_gb300 as g
+    planes, responses = _small_three_plane()
+    diff = synth.Diffusion(fluctuate=True, seed=77)
+    sim = make_sim(planes, responses, diff)
+    evs = _events(7, seed=1)
+    dev = [g.DeviceDepos.from_host(e) for e in evs]
+    outs = [[torch.empty((p.n_wires, p.n_ticks), device="cuda") for p in planes] for _ in evs]
+    singles = [[w.clone() for w in sim.run_event(d)] for d in dev]
+    for rep in range(3):                      # direct, recorded, replayed
+        sim.run_batch(dev, outs)
+        sim.sync()
+        for e in range(len(evs)):
+            for p in range(len(planes)):
+                s = to_np(singles[e][p])
+                assert _close(to_np(outs[e][p]), s, np.abs(s).max()), (rep, e, p)
+    assert sim.counters()["graph_launches"] >= 2
+    # same pointers, new depo values: the replayed graph reads the new values
+    new = _events(7, seed=2)
+    for e, (d, n) in enumerate(zip(dev, new)):
+        m = min(d.n, n.n)
+        for name in ("t0", "x", "y", "z", "q"):
+            src = np.zeros(d.n, np.float32)
+            src[:m] = getattr(n, name)[:m]
+            getattr(d, name).copy_(torch.from_numpy(src))
+    sim.run_batch(dev, outs)
+    want = [[w.clone() for w in sim.run_event(d)] for d in dev]
+    sim.sync()
+    for e in range(len(evs)):
+        for p in range(len(planes)):
+            s = to_np(want[e][p])
+            assert _close(to_np(outs[e][p]), s, np.abs(s).max())
+
+
+def test_server_results_same_alone_and_in_mix():
+    import paper_2304_01841_gb300 as g
+    from paper_2304_01841_gb300.serve import EventServer
+    planes, responses = _small_three_plane()
+    diff = synth.Diffusion(fluctuate=True, seed=5)
+    evs = _events(24, seed=3, lo=10, hi=6000, id0=300)
+    srv = EventServer(planes, responses, diff, n_slots=3, max_batch=4, hbm_budget_bytes=64 << 20,
+                      keep_results=True)
+    reqs = [srv.submit(e) for e in evs[:10]]
+    srv.step()                                 # some requests start while others still arrive
+    reqs += [srv.submit(e) for e in evs[10:]]
+    srv.drain()
+    sim = make_sim(planes, responses, diff)
+    for r, e in zip(reqs, evs):
+        alone = [to_np(w) for w in sim.run_event(g.DeviceDepos.from_host(e))]
+        for p in range(len(planes)):
+            assert _close(r.waveforms[p], alone[p], np.abs(alone[p]).max()), (r.rid, p)
+        assert r.latency > 0
+    srv.close()
+
+
+def test_server_respects_hbm_budget():
+    from paper_2304_01841_gb300.serve import EventServer
+    planes, responses = _small_three_plane()
+    evs = _events(12, seed=4, lo=100, hi=2000, id0=500)
+    one = 20 * 2000 + sum(4 * p.n_wires * p.n_ticks for p in planes)
+    srv = EventServer(planes, responses, synth.Diffusion(), n_slots=4, max_batch=4, hbm_budget_bytes=2 * one)
+    for e in evs:
+        srv.submit(e)
+    peak = 0
+    while srv.step() > 0:
+        peak = max(peak, srv.in_use)
+    assert 0 < peak <= 2 * one
+    assert len(srv.completed) == len(evs)
+    srv.close()
