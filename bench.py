@@ -105,13 +105,21 @@ class ClockSampler:
 # --------------------------------------------------------------------------------------------
 # helpers
 # --------------------------------------------------------------------------------------------
-def measured_hbm_peak():
+def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(p) as f:
-            return float(json.load(f)["hbm_gbs"]), "measured"
+            j = json.load(f)
+        return float(j["hbm_gbs"]), float(j.get("sm_max_mhz", 2070.0)), "measured"
     except Exception:
-        return FALLBACK_HBM_GBS, "fallback"
+        return FALLBACK_HBM_GBS, 2070.0, "fallback"
+
+
+# The rasterize kernel is bound by instruction issue (Philox integer multiplies, SFU, shared
+# memory), not by HBM: its roofline is the issue rate, 4 warp-instructions per clock per SM
+# (one per scheduler) x 152 SMs x the maximum SM clock.
+N_SMS = 152
+ISSUE_PER_SM_CLK = 4
 
 
 def stage_bytes(plane, n_depos, resp_ticks=200):
@@ -130,8 +138,10 @@ def stage_bytes(plane, n_depos, resp_ticks=200):
     }
 
 
-def dram_traffic_record():
-    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+def kernel_counters():
+    """ncu counters per launch of the main kernels (profiles/kernel_counters.json), valid only
+    while the CUDA sources are unchanged (csrc digest)."""
+    p = os.path.join(ROOT, "profiles", "kernel_counters.json")
     try:
         with open(p) as f:
             return json.load(f)
@@ -393,26 +403,49 @@ def main():
     value = total_events * n_depos / (elapsed_ms / 1000.0)
 
     # ---- roofline of the dominant kernel -----------------------------------------------
-    peak, peak_kind = measured_hbm_peak()
+    peak_gbs, sm_mhz_max, peak_kind = measured_peaks()
+    issue_peak = N_SMS * ISSUE_PER_SM_CLK * sm_mhz_max * 1e6          # warp-instructions / s
     sb = stage_bytes(plane, n_depos)
     kern = {k: stages[k] for k in ("raster_scatter", "row_r2c", "wire_stage", "row_c2r")}
     dom = max(kern, key=kern.get)
+    cnt = kernel_counters()
+    valid = cnt.get("csrc_digest") == csrc_digest()
+    kname = {"raster_scatter": "k_raster_chunks", "row_r2c": "k_row_r2c_tma", "wire_stage": "k_wire_stage_tma",
+             "row_c2r": "k_row_c2r_tma"}
     stage_report = {}
-    for k, us in list(kern.items()) + [("prep_binning", stages["prep_binning"])]:
-        gbs = sb[k] / (us * 1e-6) / 1e9 if us > 0 else None
-        stage_report[k] = {"us": round(us, 2), "alg_bytes": sb[k], "GB/s": round(gbs, 1) if gbs else None,
-                           "frac": round(gbs / peak, 4) if gbs else None}
+    for k, us in list(kern.items()) + [("grid_clear", stages["prep_binning"])]:
+        if k == "raster_scatter":
+            insts = cnt.get("kernels", {}).get(kname[k], {}).get("warp_instructions_per_launch") if valid else None
+            ach = insts / (us * 1e-6) if (insts and us > 0) else None
+            stage_report[k] = {"us": round(us, 2), "bound": "alu", "warp_inst_per_s": ach,
+                               "frac_of_issue_peak": round(ach / issue_peak, 4) if ach else None}
+            continue
+        alg = sb[k] if k != "grid_clear" else 4 * plane.n_wires * plane.n_ticks
+        gbs = alg / (us * 1e-6) / 1e9 if us > 0 else None
+        stage_report[k] = {"us": round(us, 2), "bound": "hbm", "alg_bytes": alg, "GB/s": round(gbs, 1) if gbs else None,
+                           "frac": round(gbs / peak_gbs, 4) if gbs else None}
     conv_us = kern["row_r2c"] + kern["wire_stage"] + kern["row_c2r"]
     conv_gbs = sb["convolve"] / (conv_us * 1e-6) / 1e9
     stage_report["convolve_total"] = {"us": round(conv_us, 2), "alg_bytes": sb["convolve"],
-                                      "GB/s": round(conv_gbs, 1), "frac": round(conv_gbs / peak, 4)}
-    achieved = sb[dom] / (kern[dom] * 1e-6) / 1e9
-    tr = dram_traffic_record()
-    traffic = None
-    if tr.get("csrc_digest") == csrc_digest() and dom in tr.get("kernels", {}):
-        traffic = tr["kernels"][dom].get("bytes_per_launch")
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": f"{peak_kind} (burst copy)"}
+                                      "GB/s": round(conv_gbs, 1), "frac": round(conv_gbs / peak_gbs, 4)}
+    sc_us = kern["raster_scatter"] + stages["prep_binning"]
+    sc_gbs = sb["raster_scatter"] / (sc_us * 1e-6) / 1e9
+    stage_report["scatter_total"] = {"us": round(sc_us, 2), "alg_bytes": sb["raster_scatter"],
+                                     "GB/s": round(sc_gbs, 1), "frac": round(sc_gbs / peak_gbs, 4),
+                                     "what": "grid clear + rasterize/scatter, against depo read + grid write"}
+    traffic = cnt["kernels"].get(kname[dom], {}).get("dram_bytes_per_launch") if valid else None
+    if dom == "raster_scatter":
+        insts = cnt["kernels"].get(kname[dom], {}).get("warp_instructions_per_launch") if valid else None
+        ach = insts / (kern[dom] * 1e-6) if insts else None
+        roofline = {"bound": "alu", "kernel": kname[dom], "achieved": ach, "peak": issue_peak,
+                    "unit": "warp-inst/s", "frac": round(ach / issue_peak, 4) if ach else None, "traffic": traffic,
+                    "peak_source": f"issue rate: {N_SMS} SMs x {ISSUE_PER_SM_CLK} warp-inst/clk x {sm_mhz_max:.0f} MHz "
+                                   f"(max SM clock, {peak_kind}); instructions per launch from the committed ncu profile"}
+    else:
+        achieved = sb[dom] / (kern[dom] * 1e-6) / 1e9
+        roofline = {"bound": "hbm", "kernel": kname[dom], "achieved": round(achieved, 1), "peak": peak_gbs,
+                    "unit": "GB/s", "frac": round(achieved / peak_gbs, 4), "traffic": traffic,
+                    "peak_source": f"{peak_kind} (burst copy)"}
 
     # ---- end to end through the public API with host buffers ---------------------------
     e2e = None

@@ -25,8 +25,8 @@ namespace wct {
 
 namespace {
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return add2(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return sub2(a, b); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
@@ -131,10 +131,8 @@ struct DftOdd {
                 const int kk = k <= H ? k : R - k;         // cos symmetric, sin antisymmetric
                 const float cs = OddTab<R>::c(kk);
                 const float sn = k <= H ? OddTab<R>::s(kk) : -OddTab<R>::s(kk);
-                a.x = fmaf(t[n - 1].x, cs, a.x);
-                a.y = fmaf(t[n - 1].y, cs, a.y);
-                b.x = fmaf(u[n - 1].x, sn, b.x);
-                b.y = fmaf(u[n - 1].y, sn, b.y);
+                a = fma2(t[n - 1], make_float2(cs, cs), a);
+                b = fma2(u[n - 1], make_float2(sn, sn), b);
             }
             const float2 ib = mul_si<INV>(b);
             out[m] = cadd(a, ib);
@@ -601,10 +599,12 @@ k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, in
     }
     const int f = f0 + tid;
     const bool live = tid < nf;
-    float2 r[KW], acc[KW];
+    // taps as packed pairs: acc += (xr, xr) * (rr, ri) + (-xi, xi) * (ri, rr)
+    float2 r[KW], rs[KW], acc[KW];
 #pragma unroll
     for (int k = 0; k < KW; ++k) {
         r[k] = live ? Rt[(size_t)k * Fs + f] : make_float2(0.f, 0.f);
+        rs[k] = make_float2(r[k].y, r[k].x);
         acc[k] = make_float2(0.f, 0.f);
     }
     bool ok = true;
@@ -625,11 +625,11 @@ k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, in
                     if (in_g == kGroupRows - 1 || idx == n_rows - 1)
                         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[gs])) : "memory");
                 }
+                const float2 x1 = make_float2(x.x, x.x), x2 = make_float2(-x.y, x.y);
 #pragma unroll
                 for (int k = 0; k < KW; ++k) {
                     const int sl = (u + 1 + k) % KW;
-                    acc[sl].x = fmaf(x.x, r[k].x, fmaf(-x.y, r[k].y, acc[sl].x));
-                    acc[sl].y = fmaf(x.x, r[k].y, fmaf(x.y, r[k].x, acc[sl].y));
+                    acc[sl] = fma2(x2, rs[k], fma2(x1, r[k], acc[sl]));
                 }
                 const int done = (u + 1) % KW;
                 if (m >= 2 * KC && live) T[(size_t)(w0 + m - 2 * KC) * Fs + f] = acc[done];

@@ -112,7 +112,7 @@ __device__ __forceinline__ float fold_fluct(const Item &f, const float *wt, cons
             if (l >= l0 && l < l1) {
                 const float w = wa * wp[f.j_base + sb + l];
                 const float m = q * w;
-                const float v = fmaf(sqrtf(m * (1.f - w)), z[l], m);
+                const float v = fmaf(sfu_sqrt(m * (1.f - w)), z[l], m);
                 acc += fmaxf(v, 0.f);
             }
         }
@@ -139,9 +139,9 @@ __device__ __forceinline__ uint32_t counter_c3(const PlaneParams &pp, uint32_t e
 // ------------------------------------------------------------------------------------------
 constexpr int kChunkThreads = 256;
 constexpr int kChunk = 64;
-constexpr int kItemCap = 7168;     // items cached per pass (a wider single depo is recomputed)
+constexpr int kItemCap = 6144;     // items cached per pass (a wider single depo is recomputed)
 constexpr int kWCap = 2048;        // >= 128 + 512, the weights of the largest window
-constexpr int kBoxCap = 8192;      // wires x ticks accumulated in shared memory
+constexpr int kBoxCap = 6144;      // wires x ticks accumulated in shared memory
 
 struct ChunkSmem {
     DepoDesc d[kChunk];
@@ -157,6 +157,7 @@ struct ChunkSmem {
     float w[kWCap];
     float val[kItemCap];
     float box[kBoxCap];
+    uint8_t slot[kItemCap];   // depo of each cached item (chunk-relative)
 };
 
 // largest j in [lo, hi) with off[j] <= k (off non-decreasing, off[lo] <= k)
@@ -287,14 +288,17 @@ __device__ __forceinline__ void raster_chunk(ChunkSmem &S, const float *__restri
                 const float *wt = S.w + (S.w_off[j] - w_base);
                 const float *wp = wt + d.nt;
                 v = pp.fluctuate ? fold_fluct(f, wt, wp, d.q, (uint32_t)(c0 + j), pp, c3) : fold_plain(f, wt, wp, d.q);
-                if (k < kItemCap) S.val[k] = v;   // a single very wide depo may exceed the cache
+                if (k < kItemCap) {   // a single very wide depo may exceed the cache
+                    S.val[k] = v;
+                    S.slot[k] = (uint8_t)j;
+                }
             }
             if (pp.fluctuate) segmented_add(j, v, S.sum);
         }
         __syncthreads();
         // (4) rescale and accumulate (box in shared memory, or the grid directly)
         for (int k = tid; k < n_items; k += kChunkThreads) {
-            const int j = find_slot(S.item_off, s, e, i_base + k);
+            const int j = k < kItemCap ? (int)S.slot[k] : find_slot(S.item_off, s, e, i_base + k);
             const DepoDesc &d = S.d[j];
             const Item f = make_item(i_base + k - S.item_off[j], S.nw[j], S.wl[j], d, pp.n_imp);
             if (f.wire < 0 || f.wire >= pp.n_wires || f.tick < 0 || f.tick >= pp.n_ticks) continue;
@@ -400,7 +404,7 @@ k_rasterize_patches(int64_t n, const DepoDesc *__restrict__ desc, const int64_t 
                 const float w = wt[a] * wp[j];
                 const float m = q * w;
                 const float z = bin_normal(pp, (uint32_t)di, d.lo_t + a, d.lo_p + j, c3);
-                const float v = fmaxf(fmaf(sqrtf(m * (1.f - w)), z, m), 0.f);
+                const float v = fmaxf(fmaf(sfu_sqrt(m * (1.f - w)), z, m), 0.f);
                 out[b] = v;
                 part += v;
             }

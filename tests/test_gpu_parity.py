@@ -293,5 +293,5 @@ def test_single_depo_wider_than_item_cache():
     sim.sync()
     ref = oracle.rasterize(d, pl, df)
     items = ref.desc[:, 3] * ref.desc[:, 4]
-    assert int(items.max()) > 7168
+    assert int(items.max()) > 6144
     assert max_rel_bin(to_np(grid), oracle.scatter(ref, pl)) <= BIN_TOL
