@@ -599,43 +599,54 @@ k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, in
     }
     const int f = f0 + tid;
     const bool live = tid < nf;
-    // taps as packed pairs: acc += (xr, xr) * (rr, ri) + (-xi, xi) * (ri, rr)
-    float2 r[KW], rs[KW], acc[KW];
+    // Pull form in blocks of kOutBlock outputs: the window holds input rows b .. b+kOutBlock+19,
+    // output b+j = sum_k win[j + 20 - k] * Rt[k]; each input row is read from the ring once.
+    constexpr int kOutBlock = 8;
+    constexpr int kWin = kOutBlock + 2 * KC;
+    float2 r[KW];
 #pragma unroll
-    for (int k = 0; k < KW; ++k) {
-        r[k] = live ? Rt[(size_t)k * Fs + f] : make_float2(0.f, 0.f);
-        rs[k] = make_float2(r[k].y, r[k].x);
-        acc[k] = make_float2(0.f, 0.f);
-    }
+    for (int k = 0; k < KW; ++k) r[k] = live ? Rt[(size_t)k * Fs + f] : make_float2(0.f, 0.f);
     bool ok = true;
-    for (int mb = 0; mb < n_in; mb += KW) {
-#pragma unroll
-        for (int u = 0; u < KW; ++u) {
-            const int m = mb + u;
-            if (m < n_in) {
-                float2 x = make_float2(0.f, 0.f);
-                if (m >= m_lo && m < m_hi) {
-                    const int idx = m - m_lo;
-                    const int g = idx / kGroupRows, in_g = idx - g * kGroupRows, gs = g % kRingGroups;
-                    if (in_g == 0 && ok && !mbar_wait(&full[gs], (g / kRingGroups) & 1)) {
-                        set_status(status, ST_ETIMEOUT);
-                        ok = false;
-                    }
-                    if (ok && live) x = ring[gs * kGroupRows + in_g][tid];
-                    if (in_g == kGroupRows - 1 || idx == n_rows - 1)
-                        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[gs])) : "memory");
-                }
-                const float2 x1 = make_float2(x.x, x.x), x2 = make_float2(-x.y, x.y);
-#pragma unroll
-                for (int k = 0; k < KW; ++k) {
-                    const int sl = (u + 1 + k) % KW;
-                    acc[sl] = fma2(x2, rs[k], fma2(x1, r[k], acc[sl]));
-                }
-                const int done = (u + 1) % KW;
-                if (m >= 2 * KC && live) T[(size_t)(w0 + m - 2 * KC) * Fs + f] = acc[done];
-                acc[done] = make_float2(0.f, 0.f);
+    auto load_row = [&](int m) -> float2 {
+        float2 x = make_float2(0.f, 0.f);
+        if (m >= m_lo && m < m_hi) {
+            const int idx = m - m_lo;
+            const int g = idx / kGroupRows, in_g = idx - g * kGroupRows, gs = g % kRingGroups;
+            if (in_g == 0 && ok && !mbar_wait(&full[gs], (g / kRingGroups) & 1)) {
+                set_status(status, ST_ETIMEOUT);
+                ok = false;
             }
+            if (ok && live) x = ring[gs * kGroupRows + in_g][tid];
+            if (in_g == kGroupRows - 1 || idx == n_rows - 1)
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[gs])) : "memory");
         }
+        return x;
+    };
+    float2 win[kWin];
+#pragma unroll
+    for (int t = 0; t < 2 * KC; ++t) win[t] = load_row(t);
+    const int n_out = w1 - w0;
+    for (int b = 0; b < n_out; b += kOutBlock) {
+#pragma unroll
+        for (int t = 0; t < kOutBlock; ++t) win[2 * KC + t] = load_row(b + 2 * KC + t);
+#pragma unroll
+        for (int j = 0; j < kOutBlock; ++j) {
+            float re = 0.f, im = 0.f, re2 = 0.f, im2 = 0.f;
+#pragma unroll
+            for (int k = 0; k < KW; ++k) {
+                const float2 x = win[j + 2 * KC - k];
+                if (k & 1) {
+                    re2 = fmaf(x.x, r[k].x, fmaf(-x.y, r[k].y, re2));
+                    im2 = fmaf(x.x, r[k].y, fmaf(x.y, r[k].x, im2));
+                } else {
+                    re = fmaf(x.x, r[k].x, fmaf(-x.y, r[k].y, re));
+                    im = fmaf(x.x, r[k].y, fmaf(x.y, r[k].x, im));
+                }
+            }
+            if (live && b + j < n_out) T[(size_t)(w0 + b + j) * Fs + f] = make_float2(re + re2, im + im2);
+        }
+#pragma unroll
+        for (int t = 0; t < 2 * KC; ++t) win[t] = win[t + kOutBlock];
     }
     if (!ok && tid == 0) {
         // after a timeout, wait (bounded) for the last group this CTA issued before leaving
