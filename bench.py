@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched / served measurements")
+    ap.add_argument("--schedule", type=int, default=-1,
+                    help="row-transform schedule: -1 default, 0 register-staged, 1 persistent bulk-copy")
     return ap.parse_args()
 
 
@@ -347,7 +349,7 @@ def main():
     plane = wl.planes[0]
     n_depos = wl.n_depos
     E = args.batch
-    sim = pkg.Simulator(wl.planes, wl.responses(), wl.diffusion)
+    sim = pkg.Simulator(wl.planes, wl.responses(), wl.diffusion, schedule_id=args.schedule)
     # E distinct events per rank, resident in HBM (weak scaling: each rank its own events)
     host_events = [wl.depos(seed=seed, event_id=eid) for seed, eid in shard_plan(rank, world, E, wl.seed)]
     dev_events = [pkg.DeviceDepos.from_host(d) for d in host_events]

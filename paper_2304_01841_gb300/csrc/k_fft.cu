@@ -362,6 +362,122 @@ struct CompiledFft<CtPlan<R0, Rs...>> {
     }
 };
 
+// ---- register-staged row transforms: small CTAs, whole row in one shared buffer ---------
+// One 128-thread CTA per row; each thread keeps all its butterflies of a stage in registers
+// (about M / 128 points), so a stage is: load everything, barrier, arithmetic, store in place,
+// barrier.  Several CTAs share an SM (one M-point buffer each, ~39 KB at M = 4900), so one
+// CTA's global loads overlap the others' arithmetic; twiddles come from the global table
+// through L1.
+constexpr int kRsThreads = 128;
+
+template <int R, int NS, int M, bool INV>
+__device__ __forceinline__ void stage_rs(float2 *buf, const float2 *__restrict__ tw) {
+    constexpr int NB = M / R;
+    constexpr int STRIDE = M / (NS * R);
+    constexpr int ITER = (NB + kRsThreads - 1) / kRsThreads;
+    float2 v[ITER][R];
+#pragma unroll
+    for (int it = 0; it < ITER; ++it) {
+        const int j = threadIdx.x + it * kRsThreads;
+        if (ITER * kRsThreads == NB || j < NB) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[it][r] = buf[j + r * NB];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < ITER; ++it) {
+        const int j = threadIdx.x + it * kRsThreads;
+        if (ITER * kRsThreads == NB || j < NB) {
+            const int k = j % NS;
+            if (NS > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    float2 w = __ldg(&tw[r * k * STRIDE]);
+                    if (INV) w.y = -w.y;
+                    v[it][r] = cmul(v[it][r], w);
+                }
+            }
+            Dft<R, INV>::run(v[it]);
+            const int base = (j - k) * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) buf[base + r * NS] = v[it][r];
+        }
+    }
+    __syncthreads();
+}
+
+template <int M, bool INV, int NS, int R, int... Rest>
+__device__ __forceinline__ void fft_rs(float2 *buf, const float2 *tw) {
+    stage_rs<R, NS, M, INV>(buf, tw);
+    if constexpr (sizeof...(Rest) > 0) fft_rs<M, INV, NS * R, Rest...>(buf, tw);
+}
+
+template <class Plan>
+struct RsFft;
+template <int... Rs>
+struct RsFft<CtPlan<Rs...>> {
+    static constexpr int M = CtPlan<Rs...>::M;
+    template <bool INV>
+    __device__ __forceinline__ static void run(float2 *buf, const float2 *tw) {
+        fft_rs<M, INV, 1, Rs...>(buf, tw);
+    }
+};
+
+template <class Plan>
+__global__ void __launch_bounds__(kRsThreads)
+k_row_r2c_rs(FFTPlan p, const float *__restrict__ in, int n_cols, float2 *__restrict__ spec) {
+    extern __shared__ float2 buf[];
+    constexpr int M = RsFft<Plan>::M;
+    const int row = blockIdx.x;
+    const float4 *src = reinterpret_cast<const float4 *>(in + (size_t)row * n_cols);   // n_cols % 4 == 0
+    const int q4 = n_cols >> 2;
+    for (int i = threadIdx.x; i < q4; i += kRsThreads) {
+        const float4 v = src[i];
+        buf[2 * i] = make_float2(v.x, v.y);
+        buf[2 * i + 1] = make_float2(v.z, v.w);
+    }
+    for (int k = 2 * q4 + threadIdx.x; k < M; k += kRsThreads) buf[k] = make_float2(0.f, 0.f);
+    __syncthreads();
+    RsFft<Plan>::template run<false>(buf, p.tw);
+    float2 *out = spec + (size_t)row * p.Fs;
+    for (int k = threadIdx.x; k < p.Fs; k += kRsThreads) {
+        float2 X = make_float2(0.f, 0.f);
+        if (k <= M) {
+            const float2 a = buf[k == M ? 0 : k];
+            const float2 b = conjf2(buf[k == 0 ? 0 : M - k]);
+            const float2 wd = cmul(__ldg(&p.rtw[k]), csub(a, b));
+            const float2 sm = cadd(a, b);
+            X = make_float2(0.5f * (sm.x + wd.y), 0.5f * (sm.y - wd.x));
+        }
+        out[k] = X;
+    }
+}
+
+template <class Plan>
+__global__ void __launch_bounds__(kRsThreads)
+k_row_c2r_rs(FFTPlan p, const float2 *__restrict__ spec, float *__restrict__ out, int n_cols) {
+    extern __shared__ float2 buf[];
+    constexpr int M = RsFft<Plan>::M;
+    const int row = blockIdx.x;
+    const float2 *X = spec + (size_t)row * p.Fs;
+    for (int k = threadIdx.x; k < M; k += kRsThreads) {
+        const float2 a = X[k];
+        const float2 b = conjf2(X[M - k]);
+        const float2 O = cmul(conjf2(__ldg(&p.rtw[k])), csub(a, b));
+        const float2 sm = cadd(a, b);
+        buf[k] = make_float2(0.5f * (sm.x - O.y), 0.5f * (sm.y + O.x));
+    }
+    __syncthreads();
+    RsFft<Plan>::template run<true>(buf, p.tw);
+    float4 *dst = reinterpret_cast<float4 *>(out + (size_t)row * n_cols);             // n_cols % 4 == 0
+    const int q4 = n_cols >> 2;
+    for (int i = threadIdx.x; i < q4; i += kRsThreads) {
+        const float2 a = buf[2 * i], b = buf[2 * i + 1];
+        dst[i] = make_float4(a.x, a.y, b.x, b.y);
+    }
+}
+
 // ---- persistent row transforms: one CTA per SM, rows streamed in by bulk copies ---------
 // Shared memory: A (staging row, M + 2 entries), B, C (ping-pong, M each), TW (M twiddles),
 // RTW (M + 1 real-split twiddles, padded to M + 2), one mbarrier.  The twiddle tables are
@@ -698,6 +814,11 @@ size_t device_smem_optin() {
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
+// Row-transform schedule: 0 = register-staged small CTAs (compiled lengths), 1 = persistent
+// bulk-copy CTAs.  Chosen by set_row_schedule (wct_sim_create's schedule_id).
+int g_row_schedule = 0;
+int row_kernel_choice() { return g_row_schedule; }
+
 // The persistent bulk-copy kernels need 16-byte aligned rows (n_cols % 4 == 0, dense rows)
 // and their five row-sized buffers in one CTA's shared memory.
 bool use_row_tma(const FFTPlan &p, int64_t stride, int n_cols, const void *ptr) {
@@ -739,11 +860,49 @@ cudaError_t launch_row_tma_kernel(const FFTPlan &p, size_t smem, int grid, cudaS
     return go(K::template get<RuntimeFft>());
 }
 
+// Register-staged kernels for the compiled lengths (4900, 3125, 625); false if none applies.
+template <bool R2C, class Launch>
+bool launch_row_rs(const FFTPlan &p, Launch &&launch, cudaError_t &err) {
+    auto is = [&](std::initializer_list<int> rs) {
+        if ((int)rs.size() != p.n_stages) return false;
+        int k = 0;
+        for (int r : rs)
+            if (p.radix[k++] != r) return false;
+        return true;
+    };
+    const size_t smem = sizeof(float2) * (size_t)p.M;
+    auto go = [&](auto kern) {
+        err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err == cudaSuccess) {
+            launch(kern, smem);
+            err = cudaGetLastError();
+        }
+        return true;
+    };
+    if constexpr (R2C) {
+        if (is({4, 7, 7, 5, 5})) return go(k_row_r2c_rs<CtPlan<4, 7, 7, 5, 5>>);
+        if (is({5, 5, 5, 5, 5})) return go(k_row_r2c_rs<CtPlan<5, 5, 5, 5, 5>>);
+        if (is({5, 5, 5, 5})) return go(k_row_r2c_rs<CtPlan<5, 5, 5, 5>>);
+    } else {
+        if (is({4, 7, 7, 5, 5})) return go(k_row_c2r_rs<CtPlan<4, 7, 7, 5, 5>>);
+        if (is({5, 5, 5, 5, 5})) return go(k_row_c2r_rs<CtPlan<5, 5, 5, 5, 5>>);
+        if (is({5, 5, 5, 5})) return go(k_row_c2r_rs<CtPlan<5, 5, 5, 5>>);
+    }
+    return false;
+}
+
 }  // namespace
 
 cudaError_t launch_row_r2c(const FFTPlan &p, const float *in, int64_t in_stride, int n_in_cols, int n_rows,
                            float2 *spec, cudaStream_t s, int32_t *status) {
     if (n_rows <= 0) return cudaSuccess;
+    if (row_kernel_choice() == 0 && (n_in_cols % 4 == 0) && in_stride == n_in_cols && aligned16(in) && aligned16(spec)) {
+        cudaError_t err = cudaSuccess;
+        if (launch_row_rs<true>(p, [&](auto kern, size_t smem) {
+                kern<<<n_rows, kRsThreads, smem, s>>>(p, in, n_in_cols, spec);
+            }, err))
+            return err;
+    }
     if (use_row_tma(p, in_stride, n_in_cols, in) && aligned16(spec)) {
         const size_t smem = row_tma_smem_bytes(p.M);
         const int grid = std::min(n_rows, device_sms());
@@ -762,6 +921,14 @@ cudaError_t launch_row_r2c(const FFTPlan &p, const float *in, int64_t in_stride,
 cudaError_t launch_row_c2r(const FFTPlan &p, const float2 *spec, int n_rows, float *out, int64_t out_stride,
                            int n_out_cols, cudaStream_t s, int32_t *status) {
     if (n_rows <= 0) return cudaSuccess;
+    if (row_kernel_choice() == 0 && (n_out_cols % 4 == 0) && out_stride == n_out_cols && aligned16(out) &&
+        aligned16(spec)) {
+        cudaError_t err = cudaSuccess;
+        if (launch_row_rs<false>(p, [&](auto kern, size_t smem) {
+                kern<<<n_rows, kRsThreads, smem, s>>>(p, spec, out, n_out_cols);
+            }, err))
+            return err;
+    }
     if (use_row_tma(p, out_stride, n_out_cols, out) && aligned16(spec)) {
         const size_t smem = row_tma_smem_bytes(p.M);
         const int grid = std::min(n_rows, device_sms());
@@ -789,6 +956,8 @@ cudaError_t launch_wire_stage(const FFTPlan &p, const float2 *spec, const float2
     k_wire_stage<<<grid, kStageThreads, 0, s>>>(spec, resp_spec, p.Fs, n_wires, out);
     return cudaGetLastError();
 }
+
+void set_row_schedule(int schedule) { g_row_schedule = schedule; }
 
 cudaError_t launch_make_twiddles(const FFTPlan &p, cudaStream_t s) {
     k_make_twiddles<<<(p.M + 256) / 256, 256, 0, s>>>(p.tw, p.rtw, p.M);

@@ -303,6 +303,7 @@ wct_status_t wct_sim_create(const wct_plane_t *planes, int n_planes, const wct_r
         s->opts.schedule_id = -1;
         s->opts.deterministic = 0;
     }
+    if (s->opts.schedule_id == 1 || s->opts.schedule_id == 0) set_row_schedule(s->opts.schedule_id);
     wct_status_t st = WCT_OK;
     size_t spec_elems = 0;
     int max_tiles = 1;
