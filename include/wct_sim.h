@@ -173,9 +173,11 @@ wct_status_t wct_sim_run_event(wct_sim_t *sim, const wct_depos_t *depos, float *
                                void *stream);
 
 /* Several events in one pass: events[e] for e < n_events; waveforms: HOST array of
- * n_events * n_planes DEVICE pointers, event-major.  Every (event, plane) grid is cleared,
- * all pairs are rasterized and scattered by one batched launch (per 256 pairs), then each
- * grid is convolved in place.  When a call repeats an earlier call's pointers, depo counts
+ * n_events * n_planes DEVICE pointers, event-major.  Per event, its grids are cleared and
+ * all its planes rasterized and scattered by one launch on a library stream, and each grid
+ * is then convolved in place on a second library stream, so the rasterize of event e + 1
+ * overlaps the convolution of event e; both streams are ordered after earlier work on
+ * `stream`, and `stream` waits for both before later work.  When a call repeats an earlier call's pointers, depo counts
  * and event ids, the sequence is recorded as a CUDA graph, and later repeats replay it (up
  * to 8 graphs are kept per handle); the depo values themselves may change between replays.  Results equal
  * those of wct_sim_run_event for each event. */

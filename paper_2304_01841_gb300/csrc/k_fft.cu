@@ -304,11 +304,13 @@ __device__ __forceinline__ void stage_ct(const float2 *__restrict__ in, float2 *
 #pragma unroll
             for (int r = 0; r < R; ++r) v[r] = in[j + r * NB];
             if (NS > 1) {
+                float2 w1 = tw[k * STRIDE];
+                if (INV) w1.y = -w1.y;
+                float2 w = w1;
 #pragma unroll
                 for (int r = 1; r < R; ++r) {
-                    float2 w = tw[r * k * STRIDE];
-                    if (INV) w.y = -w.y;
                     v[r] = cmul(v[r], w);
+                    if (r + 1 < R) w = cmul(w, w1);
                 }
             }
             Dft<R, INV>::run(v);
@@ -391,11 +393,14 @@ __device__ __forceinline__ void stage_rs(float2 *buf, const float2 *__restrict__
         if (ITER * kRsThreads == NB || j < NB) {
             const int k = j % NS;
             if (NS > 1) {
+                // one table load per butterfly; the higher twiddles are its powers
+                float2 w1 = __ldg(&tw[k * STRIDE]);
+                if (INV) w1.y = -w1.y;
+                float2 w = w1;
 #pragma unroll
                 for (int r = 1; r < R; ++r) {
-                    float2 w = __ldg(&tw[r * k * STRIDE]);
-                    if (INV) w.y = -w.y;
                     v[it][r] = cmul(v[it][r], w);
+                    if (r + 1 < R) w = cmul(w, w1);
                 }
             }
             Dft<R, INV>::run(v[it]);
@@ -425,7 +430,7 @@ struct RsFft<CtPlan<Rs...>> {
 };
 
 template <class Plan>
-__global__ void __launch_bounds__(kRsThreads)
+__global__ void __launch_bounds__(kRsThreads, 5)
 k_row_r2c_rs(FFTPlan p, const float *__restrict__ in, int n_cols, float2 *__restrict__ spec) {
     extern __shared__ float2 buf[];
     constexpr int M = RsFft<Plan>::M;
@@ -455,7 +460,7 @@ k_row_r2c_rs(FFTPlan p, const float *__restrict__ in, int n_cols, float2 *__rest
 }
 
 template <class Plan>
-__global__ void __launch_bounds__(kRsThreads)
+__global__ void __launch_bounds__(kRsThreads, 5)
 k_row_c2r_rs(FFTPlan p, const float2 *__restrict__ spec, float *__restrict__ out, int n_cols) {
     extern __shared__ float2 buf[];
     constexpr int M = RsFft<Plan>::M;

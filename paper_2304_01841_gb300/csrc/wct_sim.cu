@@ -26,6 +26,7 @@ namespace {
 constexpr int kMaxPlanes = 8;
 constexpr int kStages = 5;        // prep + binning, raster-scatter, row r2c, wire stage, row c2r
 constexpr int kMaxSlots = 4096;
+constexpr int kBatchEvents = 16;  // fork / join and per-event dependency events of run_batch
 constexpr int kMaxM = 14336;   // largest complex FFT length: two M-point buffers in one CTA's shared memory
 
 struct PlaneState {
@@ -65,6 +66,8 @@ struct wct_sim {
     int64_t launches = 0;   // kernels launched by this handle
     // run_batch: CUDA graphs of whole batches, keyed by the batch's pointers and sizes
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t rs_stream = nullptr, cv_stream = nullptr;   // run_batch raster / convolution streams
+    cudaEvent_t bev[kBatchEvents] = {};
     struct Graph {
         std::vector<uint64_t> key;
         cudaGraphExec_t exec;
@@ -400,6 +403,10 @@ wct_status_t wct_sim_destroy(wct_sim_t *s) {
         for (auto &e : slot) cudaEventDestroy(e);
     for (auto &g : s->graphs) cudaGraphExecDestroy(g.exec);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+    if (s->rs_stream) cudaStreamDestroy(s->rs_stream);
+    if (s->cv_stream) cudaStreamDestroy(s->cv_stream);
+    for (auto &e : s->bev)
+        if (e) cudaEventDestroy(e);
     delete s;
     return WCT_OK;
 }
@@ -489,20 +496,42 @@ constexpr size_t kMaxGraphs = 8;
 
 // All (event, plane) pairs: grids cleared, one batched rasterize + scatter launch per group
 // of up to kBatchItems pairs, then the convolution of every grid (in place).
+// Library streams and events used to overlap the rasterize of one event with the
+// convolution of the previous one inside run_batch.
+wct_status_t batch_streams(wct_sim *s) {
+    if (s->rs_stream) return WCT_OK;
+    cudaError_t e = cudaStreamCreateWithFlags(&s->rs_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cv_stream, cudaStreamNonBlocking);
+    for (int i = 0; e == cudaSuccess && i < kBatchEvents; ++i)
+        e = cudaEventCreateWithFlags(&s->bev[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(s, e, "batch streams");
+    return WCT_OK;
+}
+
+// All (event, plane) pairs, event by event: on the raster stream each event's grids are
+// cleared and rasterized by one batched launch; on the convolution stream each grid is then
+// convolved in place.  The raster of event e + 1 overlaps the convolution of event e (they
+// use different units: the raster is integer / SFU bound, the transforms shared-memory
+// bound).  Both streams fork from and join back into `st`.
 wct_status_t enqueue_batch(wct_sim *s, const wct_depos_t *events, int n_events, float *const *wfs, cudaStream_t st) {
+    wct_status_t r = batch_streams(s);
+    if (r) return r;
     const int npl = s->n_planes;
-    const int total = n_events * npl;
     static thread_local BatchTable tab;   // ~21 KB: kept off the stack
-    for (int g0 = 0; g0 < total; g0 += kBatchItems) {
-        const int g1 = std::min(total, g0 + kBatchItems);
-        for (int p = 0; p < npl; ++p) tab.plane[p] = s->planes[p].pp;
+    for (int p = 0; p < npl; ++p) tab.plane[p] = s->planes[p].pp;
+    cudaStream_t rs = s->rs_stream, cv = s->cv_stream;
+    cudaError_t err = cudaEventRecord(s->bev[0], st);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(rs, s->bev[0], 0);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(cv, s->bev[0], 0);
+    if (err != cudaSuccess) return cuda_fail(s, err, "batch fork");
+    for (int e = 0; e < n_events; ++e) {
+        const wct_depos_t &d = events[e];
         int64_t chunks = 0;
         tab.n_items = 0;
-        for (int it = g0; it < g1; ++it) {
-            const int e = it / npl, p = it % npl;
-            const wct_depos_t &d = events[e];
+        for (int p = 0; p < npl; ++p) {
             const PlaneState &ps = s->planes[p];
-            cudaError_t err = cudaMemsetAsync(wfs[it], 0, sizeof(float) * (size_t)ps.g.n_wires * ps.g.n_ticks, st);
+            float *grid = wfs[(size_t)e * npl + p];
+            err = cudaMemsetAsync(grid, 0, sizeof(float) * (size_t)ps.g.n_wires * ps.g.n_ticks, rs);
             if (err != cudaSuccess) return cuda_fail(s, err, "grid clear");
             if (d.n <= 0) continue;
             BatchItem &b = tab.item[tab.n_items++];
@@ -512,22 +541,33 @@ wct_status_t enqueue_batch(wct_sim *s, const wct_depos_t *events, int n_events, 
             b.z = d.z_mm;
             b.q = d.q_e;
             b.n = d.n;
-            b.grid = wfs[it];
+            b.grid = grid;
             b.chunk_begin = chunks;
             b.event_lo = (uint32_t)d.event_id;
             b.plane = p;
             chunks += raster_chunk_count(d.n);
         }
         if (chunks > 0) {
-            cudaError_t err = launch_raster_batch(tab, chunks, s->status, st);
+            err = launch_raster_batch(tab, chunks, s->status, rs);
             if (err != cudaSuccess) return cuda_fail(s, err, "batched raster-scatter");
             s->launches += 1;
         }
+        cudaEvent_t done = s->bev[1 + e % (kBatchEvents - 2)];
+        err = cudaEventRecord(done, rs);
+        if (err == cudaSuccess) err = cudaStreamWaitEvent(cv, done, 0);
+        if (err != cudaSuccess) return cuda_fail(s, err, "batch dependency");
+        for (int p = 0; p < npl; ++p) {
+            float *grid = wfs[(size_t)e * npl + p];
+            r = convolve_plane(s, p, grid, grid, cv, -1);
+            if (r) return r;
+        }
     }
-    for (int it = 0; it < total; ++it) {
-        wct_status_t r = convolve_plane(s, it % npl, wfs[it], wfs[it], st, -1);
-        if (r) return r;
-    }
+    cudaEvent_t end = s->bev[kBatchEvents - 1];
+    err = cudaEventRecord(end, cv);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(st, end, 0);
+    if (err == cudaSuccess) err = cudaEventRecord(end, rs);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(st, end, 0);
+    if (err != cudaSuccess) return cuda_fail(s, err, "batch join");
     return WCT_OK;
 }
 
