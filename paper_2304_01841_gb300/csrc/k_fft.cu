@@ -821,7 +821,7 @@ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 
 
 // Row-transform schedule: 0 = register-staged small CTAs (compiled lengths), 1 = persistent
 // bulk-copy CTAs.  Chosen by set_row_schedule (wct_sim_create's schedule_id).
-int g_row_schedule = 0;
+int g_row_schedule = 1;
 int row_kernel_choice() { return g_row_schedule; }
 
 // The persistent bulk-copy kernels need 16-byte aligned rows (n_cols % 4 == 0, dense rows)

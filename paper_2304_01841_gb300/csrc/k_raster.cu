@@ -332,6 +332,200 @@ __device__ __forceinline__ void raster_chunk(ChunkSmem &S, const float *__restri
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// Warp-level variant: each warp owns kWarpDepos consecutive depos and runs the same steps with
+// warp-synchronous code only (no CTA barriers, so a warp never waits for a slower one), with
+// its own weights / item cache / accumulation box in shared memory.
+// ------------------------------------------------------------------------------------------
+constexpr int kWarpDepos = 8;
+constexpr int kWarpsPerCta = 4;
+constexpr int kWItemCap = 512;
+constexpr int kWWCap = 640;        // >= 128 + 512, the weights of the largest window
+constexpr int kWBoxCap = 320;
+
+struct WarpSmem {
+    DepoDesc d[kWarpDepos];
+    int item_off[kWarpDepos + 1];
+    int w_off[kWarpDepos + 1];
+    int wl[kWarpDepos];
+    int nw[kWarpDepos];
+    float nrm_t[kWarpDepos];
+    float nrm_p[kWarpDepos];
+    float sum[kWarpDepos];
+    int pass_end, use_box, box_w0, box_t0, box_nw, box_nt;
+    float w[kWWCap];
+    float val[kWItemCap];
+    float box[kWBoxCap];
+    uint8_t slot[kWItemCap];
+};
+
+__device__ __forceinline__ void raster_warp(WarpSmem &S, const float *__restrict__ t0, const float *__restrict__ x,
+                                            const float *__restrict__ y, const float *__restrict__ z,
+                                            const float *__restrict__ q, int64_t n, const PlaneParams &pp,
+                                            uint32_t event_lo, float *__restrict__ grid, int32_t *status,
+                                            int64_t chunk) {
+    const int lane = threadIdx.x & 31;
+    const int64_t c0 = chunk * kWarpDepos;
+    if (c0 >= n) return;
+    const int cn = (int)((n - c0) < kWarpDepos ? (n - c0) : kWarpDepos);
+    const uint32_t c3 = counter_c3(pp, event_lo);
+    if (lane < cn) {
+        const int64_t i = c0 + lane;
+        DepoDesc d;
+        if (!depo_window(t0[i], x[i], y[i], z[i], q[i], pp, d)) set_status(status, ST_EINVAL);
+        S.d[lane] = d;
+        int wl = 0, nw = 0;
+        if (d.nt > 0) {
+            wl = floor_div(d.lo_p, pp.n_imp);
+            nw = floor_div(d.lo_p + d.np - 1, pp.n_imp) - wl + 1;
+        }
+        S.wl[lane] = wl;
+        S.nw[lane] = nw;
+        S.nrm_t[lane] = d.inv_t == 0.f ? 1.f : 1.f / (erff(((float)d.nt - d.mu_t) * d.inv_t) - erff(-d.mu_t * d.inv_t));
+        S.nrm_p[lane] = d.inv_p == 0.f ? 1.f : 1.f / (erff(((float)d.np - d.mu_p) * d.inv_p) - erff(-d.mu_p * d.inv_p));
+        S.sum[lane] = 0.f;
+    }
+    __syncwarp();
+    for (int s = 0; s < cn;) {
+        if (lane == 0) {
+            int it = 0, ww = 0, e = s;
+            int w0 = INT_MAX, w1 = INT_MIN, t0b = INT_MAX, t1b = INT_MIN;
+            for (; e < cn; ++e) {
+                const DepoDesc &d = S.d[e];
+                const int ni = (int)d.nt * S.nw[e], nwt = (int)d.nt + (int)d.np;
+                if (e > s && (it + ni > kWItemCap || ww + nwt > kWWCap)) break;
+                S.item_off[e] = it;
+                S.w_off[e] = ww;
+                it += ni;
+                ww += nwt;
+                if (d.nt > 0) {
+                    const int a0 = max(S.wl[e], 0), a1 = min(S.wl[e] + S.nw[e] - 1, pp.n_wires - 1);
+                    const int b0 = max(d.lo_t, 0), b1 = min(d.lo_t + (int)d.nt - 1, pp.n_ticks - 1);
+                    if (a0 <= a1 && b0 <= b1) {
+                        w0 = min(w0, a0); w1 = max(w1, a1);
+                        t0b = min(t0b, b0); t1b = max(t1b, b1);
+                    }
+                }
+            }
+            S.item_off[e] = it;
+            S.w_off[e] = ww;
+            S.pass_end = e;
+            const bool any = w0 <= w1;
+            const int64_t area = any ? (int64_t)(w1 - w0 + 1) * (t1b - t0b + 1) : 0;
+            S.use_box = any && area <= kWBoxCap;
+            S.box_w0 = w0;
+            S.box_t0 = t0b;
+            S.box_nw = any ? w1 - w0 + 1 : 0;
+            S.box_nt = any ? t1b - t0b + 1 : 0;
+        }
+        __syncwarp();
+        const int e = S.pass_end;
+        const int n_items = S.item_off[e] - S.item_off[s];
+        const int i_base = S.item_off[s];
+        const int n_w = S.w_off[e] - S.w_off[s];
+        const int w_base = S.w_off[s];
+        const bool use_box = S.use_box;
+        const int bnt = S.box_nt, bw0 = S.box_w0, bt0 = S.box_t0;
+        if (use_box)
+            for (int k = lane; k < S.box_nw * bnt; k += 32) S.box[k] = 0.f;
+        for (int k = lane; k < n_w; k += 32) {
+            const int j = find_slot(S.w_off, s, e, w_base + k);
+            const DepoDesc &d = S.d[j];
+            const int r = w_base + k - S.w_off[j];
+            float w;
+            if (r < d.nt) {
+                w = d.inv_t == 0.f ? 1.f
+                                   : (erff(((float)(r + 1) - d.mu_t) * d.inv_t) - erff(((float)r - d.mu_t) * d.inv_t)) *
+                                         S.nrm_t[j];
+            } else {
+                const int rr = r - d.nt;
+                w = d.inv_p == 0.f ? 1.f
+                                   : (erff(((float)(rr + 1) - d.mu_p) * d.inv_p) - erff(((float)rr - d.mu_p) * d.inv_p)) *
+                                         S.nrm_p[j];
+            }
+            S.w[k] = w;
+        }
+        __syncwarp();
+        for (int base = 0; base < n_items; base += 32) {
+            const int k = base + lane;
+            int j = -1;
+            float v = 0.f;
+            if (k < n_items) {
+                j = find_slot(S.item_off, s, e, i_base + k);
+                const DepoDesc &d = S.d[j];
+                const Item f = make_item(i_base + k - S.item_off[j], S.nw[j], S.wl[j], d, pp.n_imp);
+                const float *wt = S.w + (S.w_off[j] - w_base);
+                const float *wp = wt + d.nt;
+                v = pp.fluctuate ? fold_fluct(f, wt, wp, d.q, (uint32_t)(c0 + j), pp, c3) : fold_plain(f, wt, wp, d.q);
+                if (k < kWItemCap) {
+                    S.val[k] = v;
+                    S.slot[k] = (uint8_t)j;
+                }
+            }
+            if (pp.fluctuate) segmented_add(j, v, S.sum);
+        }
+        __syncwarp();
+        for (int k = lane; k < n_items; k += 32) {
+            const int j = k < kWItemCap ? (int)S.slot[k] : find_slot(S.item_off, s, e, i_base + k);
+            const DepoDesc &d = S.d[j];
+            const Item f = make_item(i_base + k - S.item_off[j], S.nw[j], S.wl[j], d, pp.n_imp);
+            if (f.wire < 0 || f.wire >= pp.n_wires || f.tick < 0 || f.tick >= pp.n_ticks) continue;
+            const float *wt = S.w + (S.w_off[j] - w_base);
+            float v;
+            if (k < kWItemCap) v = S.val[k];
+            else v = pp.fluctuate ? fold_fluct(f, wt, wt + d.nt, d.q, (uint32_t)(c0 + j), pp, c3)
+                                  : fold_plain(f, wt, wt + d.nt, d.q);
+            if (pp.fluctuate) {
+                const float sm = S.sum[j];
+                if (sm > 0.f) v *= d.q / sm;
+                else v = fold_plain(f, wt, wt + d.nt, d.q);
+            }
+            if (use_box) atomicAdd(&S.box[(f.wire - bw0) * bnt + (f.tick - bt0)], v);
+            else atomicAdd(&grid[(int64_t)f.wire * pp.n_ticks + f.tick], v);
+        }
+        __syncwarp();
+        if (use_box) {
+            const int area = S.box_nw * bnt;
+            for (int k = lane; k < area; k += 32) {
+                const float v = S.box[k];
+                if (v != 0.f) {
+                    const int r = k / bnt;
+                    atomicAdd(&grid[(int64_t)(bw0 + r) * pp.n_ticks + bt0 + (k - r * bnt)], v);
+                }
+            }
+        }
+        __syncwarp();
+        s = e;
+    }
+}
+
+__global__ void __launch_bounds__(kWarpsPerCta * 32)
+k_raster_warps(const float *__restrict__ t0, const float *__restrict__ x, const float *__restrict__ y,
+               const float *__restrict__ z, const float *__restrict__ q, int64_t n, PlaneParams pp,
+               uint32_t event_lo, float *__restrict__ grid, int32_t *status) {
+    __shared__ WarpSmem S[kWarpsPerCta];
+    const int warp = threadIdx.x >> 5;
+    raster_warp(S[warp], t0, x, y, z, q, n, pp, event_lo, grid, status, (int64_t)blockIdx.x * kWarpsPerCta + warp);
+}
+
+// Batched: warp-chunk c of the whole launch belongs to the (event, plane) pair whose chunk
+// range (in warp-chunks) holds c.
+__global__ void __launch_bounds__(kWarpsPerCta * 32)
+k_raster_batch_warps(const BatchTable tab, int32_t *status) {
+    __shared__ WarpSmem S[kWarpsPerCta];
+    const int warp = threadIdx.x >> 5;
+    const int64_t c = (int64_t)blockIdx.x * kWarpsPerCta + warp;
+    int lo = 0, hi = tab.n_items;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (tab.item[mid].chunk_begin <= c) lo = mid;
+        else hi = mid;
+    }
+    const BatchItem &it = tab.item[lo];
+    raster_warp(S[warp], it.t0, it.x, it.y, it.z, it.q, it.n, tab.plane[it.plane], it.event_lo, it.grid, status,
+                c - it.chunk_begin);
+}
+
 __global__ void __launch_bounds__(kChunkThreads)
 k_raster_chunks(const float *__restrict__ t0, const float *__restrict__ x, const float *__restrict__ y,
                 const float *__restrict__ z, const float *__restrict__ q, int64_t n, PlaneParams pp,
@@ -508,10 +702,21 @@ constexpr int kTileW = 32, kTileT = 256;
 int tile_wires() { return kTileW; }
 int tile_ticks() { return kTileT; }
 
-int64_t raster_chunk_count(int64_t n) { return (n + kChunk - 1) / kChunk; }
+// Raster schedule: 0 = warp-level chunks (default), 1 = CTA-level chunks.
+int g_raster_schedule = 0;
+void set_raster_schedule(int schedule) { g_raster_schedule = schedule; }
+
+int64_t raster_chunk_count(int64_t n) {
+    return g_raster_schedule == 1 ? (n + kChunk - 1) / kChunk : (n + kWarpDepos - 1) / kWarpDepos;
+}
 
 cudaError_t launch_raster_batch(const BatchTable &tab, int64_t total_chunks, int32_t *status, cudaStream_t s) {
     if (total_chunks <= 0) return cudaSuccess;
+    if (g_raster_schedule != 1) {
+        const int64_t blocks = (total_chunks + kWarpsPerCta - 1) / kWarpsPerCta;
+        k_raster_batch_warps<<<(unsigned)blocks, kWarpsPerCta * 32, 0, s>>>(tab, status);
+        return cudaGetLastError();
+    }
     const size_t smem = sizeof(ChunkSmem);
     cudaError_t e = cudaFuncSetAttribute(k_raster_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -522,6 +727,13 @@ cudaError_t launch_raster_batch(const BatchTable &tab, int64_t total_chunks, int
 cudaError_t launch_raster_chunks(const wct_depos_t &d, const PlaneParams &pp, uint32_t event_lo, float *grid,
                                  int32_t *status, cudaStream_t s) {
     if (d.n <= 0) return cudaSuccess;
+    if (g_raster_schedule != 1) {
+        const int64_t chunks = (d.n + kWarpDepos - 1) / kWarpDepos;
+        const int64_t blocks = (chunks + kWarpsPerCta - 1) / kWarpsPerCta;
+        k_raster_warps<<<(unsigned)blocks, kWarpsPerCta * 32, 0, s>>>(d.t0_us, d.x_mm, d.y_mm, d.z_mm, d.q_e, d.n, pp,
+                                                                      event_lo, grid, status);
+        return cudaGetLastError();
+    }
     const size_t smem = sizeof(ChunkSmem);
     cudaError_t e = cudaFuncSetAttribute(k_raster_chunks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

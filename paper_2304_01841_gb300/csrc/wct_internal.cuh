@@ -78,6 +78,7 @@ cudaError_t launch_raster_chunks(const wct_depos_t &d, const PlaneParams &pp, ui
                                  int32_t *status, cudaStream_t s);
 cudaError_t launch_raster_batch(const BatchTable &tab, int64_t total_chunks, int32_t *status, cudaStream_t s);
 int64_t raster_chunk_count(int64_t n);
+void set_raster_schedule(int schedule);   // 0 warp-level chunks, 1 CTA-level chunks
 cudaError_t launch_rasterize_patches(int64_t n, const DepoDesc *desc, const int64_t *offsets, const PlaneParams &pp,
                                      uint32_t event_lo, float *patches, int64_t *patch_desc, cudaStream_t s);
 cudaError_t launch_bin_patches(int64_t n, const int64_t *patch_desc, const PlaneParams &pp, int32_t *tile_count,
