@@ -531,8 +531,7 @@ __device__ __forceinline__ bool row_tma_wait(uint64_t *bar, uint32_t parity, int
 template <class FFT>
 __global__ void __launch_bounds__(kRowThreads, 1)
 k_row_r2c_tma(FFTPlan p, const float *__restrict__ in, int n_rows, int n_cols, float2 *__restrict__ spec,
-              int32_t *status, int32_t *row_counter) {
-    __shared__ int s_next;
+              int32_t *status) {
     extern __shared__ float4 sm4[];
     const int M = p.M;
     const RowSmem L(sm4, M);
@@ -549,19 +548,15 @@ k_row_r2c_tma(FFTPlan p, const float *__restrict__ in, int n_rows, int n_cols, f
         bulk_g2s(A, in + (size_t)row * n_cols, bytes, bar);
     }
     uint32_t parity = 0;
-    while (row < n_rows) {
+    for (; row < n_rows; row += gridDim.x) {
         if (!row_tma_wait(bar, parity, status)) return;
         parity ^= 1u;
         FFT::template range<false>(A, B, C, p, TW, 0, 1);    // A -> B, ends with a CTA barrier
-        if (threadIdx.x == 0) {
-            // rows after the first are handed out dynamically (or strided without a counter)
-            const int next = row_counter ? (int)gridDim.x + atomicAdd(row_counter, 1) : row + (int)gridDim.x;
-            s_next = next;
-            if (next < n_rows) {
-                fence_proxy_async_smem();
-                mbar_arrive_expect_tx(bar, bytes);
-                bulk_g2s(A, in + (size_t)next * n_cols, bytes, bar);
-            }
+        const int next = row + gridDim.x;
+        if (threadIdx.x == 0 && next < n_rows) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(bar, bytes);
+            bulk_g2s(A, in + (size_t)next * n_cols, bytes, bar);
         }
         const float2 *Z = FFT::template range<false>(B, B, C, p, TW, 1, p.n_stages);
         float2 *out = spec + (size_t)row * p.Fs;
@@ -577,15 +572,13 @@ k_row_r2c_tma(FFTPlan p, const float *__restrict__ in, int n_rows, int n_cols, f
             out[k] = X;
         }
         __syncthreads();
-        row = s_next;
     }
 }
 
 template <class FFT>
 __global__ void __launch_bounds__(kRowThreads, 1)
 k_row_c2r_tma(FFTPlan p, const float2 *__restrict__ spec, int n_rows, float *__restrict__ out, int n_cols,
-              int32_t *status, int32_t *row_counter) {
-    __shared__ int s_next;
+              int32_t *status) {
     extern __shared__ float4 sm4[];
     const int M = p.M;
     const RowSmem L(sm4, M);
@@ -600,7 +593,7 @@ k_row_c2r_tma(FFTPlan p, const float2 *__restrict__ spec, int n_rows, float *__r
         bulk_g2s(A, spec + (size_t)row * p.Fs, bytes, bar);
     }
     uint32_t parity = 0;
-    while (row < n_rows) {
+    for (; row < n_rows; row += gridDim.x) {
         if (!row_tma_wait(bar, parity, status)) return;
         parity ^= 1u;
         // Z[k] = E + i O, E = (X[k] + conj X[M-k]) / 2, O = exp(2 pi i k / P)(X[k] - conj X[M-k]) / 2
@@ -612,20 +605,16 @@ k_row_c2r_tma(FFTPlan p, const float2 *__restrict__ spec, int n_rows, float *__r
             B[k] = make_float2(0.5f * (sm.x - O.y), 0.5f * (sm.y + O.x));
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            const int next = row_counter ? (int)gridDim.x + atomicAdd(row_counter, 1) : row + (int)gridDim.x;
-            s_next = next;
-            if (next < n_rows) {
-                fence_proxy_async_smem();
-                mbar_arrive_expect_tx(bar, bytes);
-                bulk_g2s(A, spec + (size_t)next * p.Fs, bytes, bar);
-            }
+        const int next = row + gridDim.x;
+        if (threadIdx.x == 0 && next < n_rows) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(bar, bytes);
+            bulk_g2s(A, spec + (size_t)next * p.Fs, bytes, bar);
         }
         const float2 *z = FFT::template range<true>(B, B, C, p, TW, 0, p.n_stages);
         float *dst = out + (size_t)row * n_cols;
         for (int n2 = threadIdx.x; 2 * n2 < n_cols; n2 += blockDim.x) reinterpret_cast<float2 *>(dst)[n2] = z[n2];
         __syncthreads();
-        row = s_next;
     }
 }
 
@@ -910,7 +899,7 @@ bool launch_row_rs(const FFTPlan &p, Launch &&launch, cudaError_t &err) {
 }  // namespace
 
 cudaError_t launch_row_r2c(const FFTPlan &p, const float *in, int64_t in_stride, int n_in_cols, int n_rows,
-                           float2 *spec, cudaStream_t s, int32_t *status, int32_t *row_counter) {
+                           float2 *spec, cudaStream_t s, int32_t *status) {
     if (n_rows <= 0) return cudaSuccess;
     if (row_kernel_choice() == 0 && (n_in_cols % 4 == 0) && in_stride == n_in_cols && aligned16(in) && aligned16(spec)) {
         cudaError_t err = cudaSuccess;
@@ -923,7 +912,7 @@ cudaError_t launch_row_r2c(const FFTPlan &p, const float *in, int64_t in_stride,
         const size_t smem = row_tma_smem_bytes(p.M);
         const int grid = std::min(n_rows, device_sms());
         return launch_row_tma_kernel(p, smem, grid, s, [&](auto kern) {
-            kern<<<grid, kRowThreads, smem, s>>>(p, in, n_rows, n_in_cols, spec, status, row_counter);
+            kern<<<grid, kRowThreads, smem, s>>>(p, in, n_rows, n_in_cols, spec, status);
         }, R2CKernels{});
     }
     const int T = pick_threads(p.M);
@@ -935,7 +924,7 @@ cudaError_t launch_row_r2c(const FFTPlan &p, const float *in, int64_t in_stride,
 }
 
 cudaError_t launch_row_c2r(const FFTPlan &p, const float2 *spec, int n_rows, float *out, int64_t out_stride,
-                           int n_out_cols, cudaStream_t s, int32_t *status, int32_t *row_counter) {
+                           int n_out_cols, cudaStream_t s, int32_t *status) {
     if (n_rows <= 0) return cudaSuccess;
     if (row_kernel_choice() == 0 && (n_out_cols % 4 == 0) && out_stride == n_out_cols && aligned16(out) &&
         aligned16(spec)) {
@@ -949,7 +938,7 @@ cudaError_t launch_row_c2r(const FFTPlan &p, const float2 *spec, int n_rows, flo
         const size_t smem = row_tma_smem_bytes(p.M);
         const int grid = std::min(n_rows, device_sms());
         return launch_row_tma_kernel(p, smem, grid, s, [&](auto kern) {
-            kern<<<grid, kRowThreads, smem, s>>>(p, spec, n_rows, out, n_out_cols, status, row_counter);
+            kern<<<grid, kRowThreads, smem, s>>>(p, spec, n_rows, out, n_out_cols, status);
         }, C2RKernels{});
     }
     const int T = pick_threads(p.M);

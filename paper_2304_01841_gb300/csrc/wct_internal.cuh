@@ -90,14 +90,12 @@ cudaError_t launch_tile_scatter_patches(const int64_t *patch_desc, const float *
                                         const int32_t *tile_list, int64_t list_cap, const PlaneParams &pp, float *grid,
                                         cudaStream_t s);
 
-// row_counter (optional, device int zeroed by the caller): rows after each CTA's first are
-// handed out dynamically by the persistent kernels.
 cudaError_t launch_row_r2c(const FFTPlan &p, const float *in, int64_t in_stride, int n_in_cols, int n_rows,
-                           float2 *spec, cudaStream_t s, int32_t *status = nullptr, int32_t *row_counter = nullptr);
+                           float2 *spec, cudaStream_t s, int32_t *status = nullptr);
 cudaError_t launch_wire_stage(const FFTPlan &p, const float2 *spec, const float2 *resp_spec, int n_wires,
                               float2 *out, cudaStream_t s, int32_t *status = nullptr);
 cudaError_t launch_row_c2r(const FFTPlan &p, const float2 *spec, int n_rows, float *out, int64_t out_stride,
-                           int n_out_cols, cudaStream_t s, int32_t *status = nullptr, int32_t *row_counter = nullptr);
+                           int n_out_cols, cudaStream_t s, int32_t *status = nullptr);
 cudaError_t launch_scale_spectrum(float2 *spec, int64_t n, float scale, cudaStream_t s);
 cudaError_t launch_make_twiddles(const FFTPlan &p, cudaStream_t s);
 void set_row_schedule(int schedule);   // 0 register-staged row kernels, 1 persistent bulk-copy kernels

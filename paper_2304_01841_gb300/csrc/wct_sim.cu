@@ -55,7 +55,6 @@ struct wct_sim {
     int32_t *tile_list = nullptr;
     int64_t list_cap = 0;
     int32_t *status = nullptr;
-    int32_t *row_ctr = nullptr;   // [2]: dynamic row counters of the forward / inverse row kernels
     size_t bytes = 0;
     std::vector<void *> allocs;
     std::string err;
@@ -257,14 +256,13 @@ wct_status_t raster_scatter(wct_sim *s, int plane, const wct_depos_t *d, float *
 wct_status_t convolve_plane(wct_sim *s, int plane, const float *grid, float *wf, cudaStream_t st, int slot) {
     const PlaneState &ps = s->planes[plane];
     const int nw = ps.g.n_wires, nt = ps.g.n_ticks;
-    cudaError_t e = cudaMemsetAsync(s->row_ctr, 0, 2 * sizeof(int32_t), st);
-    if (e == cudaSuccess) e = launch_row_r2c(ps.fft, grid, nt, nt, nw, s->spec, st, s->status, s->row_ctr);
+    cudaError_t e = launch_row_r2c(ps.fft, grid, nt, nt, nw, s->spec, st, s->status);
     if (e != cudaSuccess) return cuda_fail(s, e, "row r2c");
     mark(s, slot, 3, st);
     e = launch_wire_stage(ps.fft, s->spec, ps.resp_spec, nw, s->spec2, st, s->status);
     if (e != cudaSuccess) return cuda_fail(s, e, "wire stage");
     mark(s, slot, 4, st);
-    e = launch_row_c2r(ps.fft, s->spec2, nw, wf, nt, nt, st, s->status, s->row_ctr + 1);
+    e = launch_row_c2r(ps.fft, s->spec2, nw, wf, nt, nt, st, s->status);
     if (e != cudaSuccess) return cuda_fail(s, e, "row c2r");
     s->launches += 3;
     mark(s, slot, 5, st);
@@ -364,7 +362,6 @@ wct_status_t wct_sim_create(const wct_plane_t *planes, int n_planes, const wct_r
     if (st == WCT_OK) st = dev_alloc(s, (void **)&s->tile_cursor, sizeof(int32_t) * (max_tiles + 1));
     if (st == WCT_OK) st = dev_alloc(s, (void **)&s->scan32, sizeof(int32_t) * scan_tmp_elems(max_tiles + 1));
     if (st == WCT_OK) st = dev_alloc(s, (void **)&s->status, sizeof(int32_t));
-    if (st == WCT_OK) st = dev_alloc(s, (void **)&s->row_ctr, 2 * sizeof(int32_t));
     if (st == WCT_OK) {
         cudaError_t e = cudaMemset(s->status, 0, sizeof(int32_t));
         if (e != cudaSuccess) st = cuda_fail(s, e, "status init");
@@ -508,12 +505,8 @@ constexpr size_t kMaxGraphs = 8;
 // convolution of the previous one inside run_batch.
 wct_status_t batch_streams(wct_sim *s) {
     if (s->rs_stream) return WCT_OK;
-    // the convolution stream gets the higher priority, so its CTAs go first whenever SMs free
-    // up and the rasterize CTAs fill the remaining room
-    int lo = 0, hi = 0;
-    cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
-    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->rs_stream, cudaStreamNonBlocking, lo);
-    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->cv_stream, cudaStreamNonBlocking, hi);
+    cudaError_t e = cudaStreamCreateWithFlags(&s->rs_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cv_stream, cudaStreamNonBlocking);
     for (int i = 0; e == cudaSuccess && i < kBatchEvents; ++i)
         e = cudaEventCreateWithFlags(&s->bev[i], cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_fail(s, e, "batch streams");
