@@ -505,8 +505,12 @@ constexpr size_t kMaxGraphs = 8;
 // convolution of the previous one inside run_batch.
 wct_status_t batch_streams(wct_sim *s) {
     if (s->rs_stream) return WCT_OK;
-    cudaError_t e = cudaStreamCreateWithFlags(&s->rs_stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cv_stream, cudaStreamNonBlocking);
+    // the convolution stream gets the higher priority, so its CTAs go first whenever SMs free
+    // up and the rasterize CTAs fill the remaining room
+    int lo = 0, hi = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->rs_stream, cudaStreamNonBlocking, lo);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->cv_stream, cudaStreamNonBlocking, hi);
     for (int i = 0; e == cudaSuccess && i < kBatchEvents; ++i)
         e = cudaEventCreateWithFlags(&s->bev[i], cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_fail(s, e, "batch streams");
