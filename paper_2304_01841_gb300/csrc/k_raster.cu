@@ -64,7 +64,9 @@ struct Item {
 
 __device__ __forceinline__ Item make_item(int it, int nw, int wl, const DepoDesc &d, int n_imp) {
     Item f;
-    f.a = it / nw;
+    // it / nw without an integer division: the quotient (it + 1/2) / nw is at most 128 and at
+    // least 1/(2 nw) >= 1e-3 away from an integer, far beyond the ~3e-5 error of the SFU divide
+    f.a = (int)__fdividef((float)it + 0.5f, (float)nw);
     f.wire = wl + (it - f.a * nw);
     f.tick = d.lo_t + f.a;
     const int first = f.wire * n_imp;                     // absolute impact of sub-bin 0
