@@ -95,8 +95,8 @@ __device__ __forceinline__ void axis_window(double mu, double s, double nsigma, 
 //   t_d = x / v, arrival = t0 + t_d, sigma_L,T = sqrt(2 D_L,T t_d)
 //   mu_t = (arrival - t_window0) / tick, s_t = (sigma_L / v) / tick
 //   mu_p = (z cos a + y sin a - origin) / (pitch / n_imp), s_p = sigma_T / (pitch / n_imp)
-__device__ __forceinline__ bool depo_window(double T0, double X, double Y, double Z, double Q, const PlaneParams &pp,
-                                            DepoDesc &d) {
+__device__ __forceinline__ bool depo_window_f64(double T0, double X, double Y, double Z, double Q,
+                                                const PlaneParams &pp, DepoDesc &d) {
     d.mu_t = d.mu_p = d.inv_t = d.inv_p = 0.f;
     d.q = 0.f;
     d.lo_t = d.lo_p = 0;
@@ -159,6 +159,71 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
     unsigned long long d;
     asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
     return bits_f2(d);
+}
+
+// The same window, decided cheaply.  FP64 division and square root are slow on this part,
+// so: mu comes from multiplications by host-computed FP64 reciprocals (within ~1e-12 bin of
+// the divided value), sigma from an FP32 square root (relative error < 2^-21).  Each window
+// edge floor(mu -+ n sigma) is accepted when the interval of +-eps around it (eps bounds both
+// errors generously) holds no integer, and the point-charge test when sigma is not within
+// 1e-5 (relative) of its threshold; otherwise depo_window_f64 decides, exactly as before.
+// mu_t/mu_p relative to the window and the erf scales only feed FP32 weights.
+__device__ __forceinline__ bool fast_edge(double a, double eps, long long &f) {
+    const double lo = floor(a - eps), hi = floor(a + eps);
+    f = (long long)lo;
+    return lo == hi;
+}
+
+__device__ __forceinline__ bool depo_window(double T0, double X, double Y, double Z, double Q, const PlaneParams &pp,
+                                            DepoDesc &d) {
+    const bool ok = isfinite(T0) && isfinite(X) && isfinite(Y) && isfinite(Z) && isfinite(Q) && X >= 0.0 && Q >= 0.0;
+    if (!ok) return depo_window_f64(T0, X, Y, Z, Q, pp, d);
+    const double mu_t = fma(X, pp.inv_vtick, (T0 - pp.tw0) * pp.inv_tick);
+    const double p = fma(Z, pp.cos_a, Y * pp.sin_a);
+    const double mu_p = (p - pp.origin) * pp.inv_dp;
+    const float sx = sqrtf((float)X);
+    const float s_t = sx * pp.kt, s_p = sx * pp.kp;
+    const float ns = (float)pp.nsigma;
+    const double big = 1099511627776.0;
+    if (!(fabs(mu_t) < 0.5 * big && fabs(mu_p) < 0.5 * big && s_t < 1e30f && s_p < 1e30f))
+        return depo_window_f64(T0, X, Y, Z, Q, pp, d);
+    long long lo_t, hi_t, lo_p, hi_p;
+    bool sure = true;
+    // point-charge threshold: sigma < 1e-6 bin
+    const bool dt = s_t < 1e-6f, dp = s_p < 1e-6f;
+    sure &= fabsf(s_t - 1e-6f) > 1e-11f && fabsf(s_p - 1e-6f) > 1e-11f;
+    const double et = 1e-9 * (1.0 + fabs(mu_t)) + 4e-6 * (double)(ns * s_t);
+    const double ep = 1e-9 * (1.0 + fabs(mu_p)) + 4e-6 * (double)(ns * s_p);
+    if (dt) sure &= fast_edge(mu_t, et, lo_t), hi_t = lo_t;
+    else {
+        sure &= fast_edge(mu_t - (double)(ns * s_t), et, lo_t);
+        sure &= fast_edge(mu_t + (double)(ns * s_t), et, hi_t);
+    }
+    if (dp) sure &= fast_edge(mu_p, ep, lo_p), hi_p = lo_p;
+    else {
+        sure &= fast_edge(mu_p - (double)(ns * s_p), ep, lo_p);
+        sure &= fast_edge(mu_p + (double)(ns * s_p), ep, hi_p);
+    }
+    if (!sure) return depo_window_f64(T0, X, Y, Z, Q, pp, d);
+    const long long n_t = hi_t - lo_t + 1, n_p = hi_p - lo_p + 1;
+    const long long lim = 1LL << 30;
+    d.mu_t = d.mu_p = d.inv_t = d.inv_p = 0.f;
+    d.q = 0.f;
+    d.lo_t = d.lo_p = 0;
+    d.nt = d.np = 0;
+    if (n_t > WCT_MAX_WINDOW_TICKS || n_p > WCT_MAX_WINDOW_IMPACTS || lo_t < -lim || lo_t > lim || lo_p < -lim ||
+        lo_p > lim)
+        return false;
+    d.lo_t = (int32_t)lo_t;
+    d.lo_p = (int32_t)lo_p;
+    d.nt = (int16_t)n_t;
+    d.np = (int16_t)n_p;
+    d.mu_t = (float)(mu_t - (double)lo_t);
+    d.mu_p = (float)(mu_p - (double)lo_p);
+    d.inv_t = dt ? 0.f : 0.70710678118654752f / s_t;
+    d.inv_p = dp ? 0.f : 0.70710678118654752f / s_p;
+    d.q = (float)Q;
+    return true;
 }
 
 __device__ __forceinline__ float warp_sum(float v) {

@@ -26,6 +26,8 @@ static_assert(sizeof(DepoDesc) == 32, "DepoDesc must stay 32 bytes");
 struct PlaneParams {
     double pitch, origin, cos_a, sin_a, tick, tw0, dp;   // dp = pitch / n_imp
     double DL, DT, v, nsigma;                            // DL, DT in mm^2/us
+    double inv_tick, inv_vtick, inv_dp;                  // 1/tick, 1/(v tick), 1/dp
+    float kt, kp;                                        // sigma_t = kt sqrt(x), sigma_p = kp sqrt(x)
     int32_t n_imp, n_wires, n_ticks, plane_index;
     int32_t fluctuate;
     uint32_t key0, key1;

@@ -331,6 +331,12 @@ wct_status_t wct_sim_create(const wct_plane_t *planes, int n_planes, const wct_r
         pp.DT = df.DT_cm2_s * 1.0e-4;
         pp.v = df.v_drift_mm_us;
         pp.nsigma = df.nsigma;
+        pp.inv_tick = 1.0 / g.tick_us;
+        pp.inv_vtick = 1.0 / (df.v_drift_mm_us * g.tick_us);
+        pp.inv_dp = 1.0 / pp.dp;
+        // sigma_t = sqrt(2 D_L x / v) / v / tick, sigma_p = sqrt(2 D_T x / v) / dp
+        pp.kt = (float)(std::sqrt(2.0 * pp.DL / df.v_drift_mm_us) / (df.v_drift_mm_us * g.tick_us));
+        pp.kp = (float)(std::sqrt(2.0 * pp.DT / df.v_drift_mm_us) / pp.dp);
         pp.n_imp = g.n_impact_per_pitch;
         pp.n_wires = g.n_wires;
         pp.n_ticks = g.n_ticks;

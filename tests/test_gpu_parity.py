@@ -295,3 +295,32 @@ def test_single_depo_wider_than_item_cache():
     items = ref.desc[:, 3] * ref.desc[:, 4]
     assert int(items.max()) > 6144
     assert max_rel_bin(to_np(grid), oracle.scatter(ref, pl)) <= BIN_TOL
+
+
+def test_windows_with_time_offsets_angles_and_edges():
+    # windows are decided by a cheap path with an exact fallback near bin edges: exercise
+    # non-zero t0 / window start, an inclined plane, and depos placed on tick / impact edges
+    a = np.radians(-35.7)
+    pl = synth.Plane(300, 3000, wire_angle_rad=a, t_window0_us=12.5, tick_us=0.5, pitch_origin_mm=-450.0)
+    df = synth.Diffusion(fluctuate=True, seed=31)
+    rng = np.random.default_rng(77)
+    n = 20000
+    x = rng.uniform(0, 2000, n)
+    t0 = rng.uniform(0, 300, n)
+    y = rng.uniform(-200, 200, n)
+    z = rng.uniform(-300, 300, n)
+    x[:2000] = np.round(x[:2000] / 0.8) * 0.8          # arrival on tick edges (tick = 0.5 us, v = 1.6)
+    t0[:2000] = np.round(t0[:2000] * 2.0) / 2.0
+    z[2000:4000] = np.round(z[2000:4000] / 0.3) * 0.3
+    y[2000:4000] = 0.0
+    x[4000:4500] = 0.0                                 # point charges
+    d = synth.Depos(t0, x, y, z, rng.lognormal(8.5, 0.3, n))
+    sim = make_sim([pl], [synth.make_response("bipolar")], df)
+    dd = _dev(d)
+    desc, patches = sim.rasterize(0, dd)
+    grid = sim.scatter(0, dd)
+    sim.sync()
+    ref = oracle.rasterize(d, pl, df)
+    assert np.array_equal(to_np(desc), ref.desc)
+    assert max_rel_bin(to_np(patches), ref.values) <= BIN_TOL
+    assert max_rel_bin(to_np(grid), oracle.scatter(ref, pl)) <= BIN_TOL
