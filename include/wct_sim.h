@@ -206,6 +206,13 @@ wct_status_t wct_sim_stage_times(wct_sim_t *sim, float *us, int n);
  * launched.  Host call, no device work. */
 wct_status_t wct_sim_counters(const wct_sim_t *sim, int64_t *out, int n);
 
+/* Failure-detection self-test: launches one kernel whose bounded wait on a shared-memory
+ * barrier can never complete (nothing arrives); after limit_cycles SM clocks it gives up and
+ * records WCT_ETIMEOUT in the handle's status word, exactly as the library's copy-fed kernels
+ * do when a bulk copy never lands.  wct_sim_sync then returns WCT_ETIMEOUT.  The GPU context
+ * stays usable.  (The paper has no counterpart.) */
+wct_status_t wct_sim_selftest_wait(wct_sim_t *sim, int64_t limit_cycles, void *stream);
+
 /* Human-readable description of the last error on this handle ("" if none). */
 const char *wct_sim_last_error(const wct_sim_t *sim);
 

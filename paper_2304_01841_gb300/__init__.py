@@ -174,6 +174,10 @@ class Simulator:
         """wct_sim_sync: wait for the stream and raise on a device-side error."""
         self._check(self._lib.wct_sim_sync(self._h, _stream_handle(stream)))
 
+    def selftest_wait(self, limit_cycles: int = 2_000_000, stream=None):
+        """wct_sim_selftest_wait: a bounded wait that must time out (status WCT_ETIMEOUT)."""
+        self._check(self._lib.wct_sim_selftest_wait(self._h, int(limit_cycles), _stream_handle(stream)))
+
     def set_timing(self, enable: bool = True):
         self._check(self._lib.wct_sim_set_timing(self._h, int(bool(enable))))
 

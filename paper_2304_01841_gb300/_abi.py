@@ -63,6 +63,7 @@ EXPORTS = {
     "wct_sim_set_timing": ([c_vp, ctypes.c_int], ctypes.c_int),
     "wct_sim_stage_times": ([c_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int], ctypes.c_int),
     "wct_sim_counters": ([c_vp, ctypes.POINTER(c_i64), ctypes.c_int], ctypes.c_int),
+    "wct_sim_selftest_wait": ([c_vp, c_i64, c_vp], ctypes.c_int),
     "wct_sim_last_error": ([c_vp], ctypes.c_char_p),
     "wct_philox4x32_10": ([c_vp, c_u64, c_i64, c_vp, c_vp], ctypes.c_int),
     "wct_convolve_static": ([c_vp, c_i32, c_i32, c_vp, c_i32, c_i32, c_vp, c_vp], ctypes.c_int),

@@ -791,6 +791,18 @@ __global__ void k_make_twiddles(float2 *__restrict__ tw, float2 *__restrict__ rt
     }
 }
 
+// Self-test of the bounded wait: one thread waits on an mbarrier whose phase never completes
+// (nothing arrives), gives up after `limit` cycles and records WCT_ETIMEOUT, as the library's
+// kernels do when a copy never lands.
+__global__ void k_wait_selftest(long long limit, int32_t *status) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        if (!mbar_wait(&bar, 0, limit)) set_status(status, ST_ETIMEOUT);
+    }
+}
+
 __global__ void k_scale(float2 *__restrict__ a, int64_t n, float s) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) a[i] = cscale(a[i], s);
@@ -966,6 +978,11 @@ void set_row_schedule(int schedule) { g_row_schedule = schedule; }
 
 cudaError_t launch_make_twiddles(const FFTPlan &p, cudaStream_t s) {
     k_make_twiddles<<<(p.M + 256) / 256, 256, 0, s>>>(p.tw, p.rtw, p.M);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wait_selftest(long long limit, int32_t *status, cudaStream_t s) {
+    k_wait_selftest<<<1, 32, 0, s>>>(limit, status);
     return cudaGetLastError();
 }
 

@@ -100,6 +100,7 @@ cudaError_t launch_row_c2r(const FFTPlan &p, const float2 *spec, int n_rows, flo
                            int n_out_cols, cudaStream_t s, int32_t *status = nullptr);
 cudaError_t launch_scale_spectrum(float2 *spec, int64_t n, float scale, cudaStream_t s);
 cudaError_t launch_make_twiddles(const FFTPlan &p, cudaStream_t s);
+cudaError_t launch_wait_selftest(long long limit, int32_t *status, cudaStream_t s);
 void set_row_schedule(int schedule);   // 0 register-staged row kernels, 1 persistent bulk-copy kernels
 cudaError_t launch_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, int64_t n, uint32_t *out, cudaStream_t s);
 

@@ -739,6 +739,13 @@ wct_status_t wct_sim_counters(const wct_sim_t *s, int64_t *out, int n) {
 
 const char *wct_sim_last_error(const wct_sim_t *s) { return s ? s->err.c_str() : "null handle"; }
 
+wct_status_t wct_sim_selftest_wait(wct_sim_t *s, int64_t limit_cycles, void *stream) {
+    if (!s || limit_cycles < 0) return WCT_EINVAL;
+    cudaError_t e = launch_wait_selftest((long long)limit_cycles, s->status, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "wait self-test");
+    return WCT_OK;
+}
+
 wct_status_t wct_philox4x32_10(const uint32_t *ctr, uint64_t seed, int64_t n, uint32_t *out, void *stream) {
     if (n < 0 || (n > 0 && (!ctr || !out))) return WCT_EINVAL;
     if (((uintptr_t)ctr & 15) || ((uintptr_t)out & 15)) return WCT_EINVAL;

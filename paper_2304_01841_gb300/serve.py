@@ -5,13 +5,16 @@ Requests (one event's depos each, in host memory) arrive at any time.  The sched
 slots run concurrently on the device.  Whenever a slot is free, the scheduler admits the
 oldest pending requests whose device memory (depo arrays + waveforms) fits the remaining HBM
 budget, up to `max_batch` per slot, copies their depos to the device and launches them as one
-batch (one batched rasterize + scatter launch, then the convolutions) on that slot's stream.
+batch (rasterize + scatter and the convolutions, wct_sim_run_batch) on that slot's stream.
 A request that arrives while others are on the GPU is admitted as soon as a slot and memory
 free up.  Latency is submit -> completion observed on the host.
 
 The results of a request do not depend on what it was batched with: the fluctuation stream is
 keyed by (seed, event id, plane, depo index, bin), so each event is the same alone and in a mix
 up to the FP32 summation order of the scatter.
+
+The scheduling logic (admission, budget, FIFO order) is independent of the device: the device
+work goes through a backend object (`CudaBackend` here; tests drive the scheduler with a fake).
 """
 from __future__ import annotations
 
@@ -22,8 +25,6 @@ from dataclasses import dataclass, field
 from typing import Deque, List, Optional, Sequence
 
 import numpy as np
-
-from . import DeviceDepos, Simulator
 
 
 @dataclass
@@ -58,28 +59,66 @@ def pin_depos(d):
     return out
 
 
+class CudaBackend:
+    """Device side of a slot: a simulator handle and a stream."""
+
+    def __init__(self, planes, responses, diffusion, keep_results: bool):
+        import torch
+        from . import Simulator
+        self.torch = torch
+        self.planes = list(planes)
+        self.sim = Simulator(planes, responses, diffusion)
+        self.stream = torch.cuda.Stream()
+        self.keep = keep_results
+        self.dev, self.outs, self.host, self.event = [], [], [], None
+
+    def launch(self, batch: List[Request]):
+        from . import DeviceDepos
+        torch = self.torch
+        with torch.cuda.stream(self.stream):
+            self.dev = []
+            for r in batch:
+                d = r.depos
+                dev = [_host_tensor(torch, a).to("cuda", non_blocking=True) for a in (d.t0, d.x, d.y, d.z, d.q)]
+                self.dev.append(DeviceDepos(*dev, event_id=int(d.event_id)))
+            self.outs = [[torch.empty((p.n_wires, p.n_ticks), dtype=torch.float32, device="cuda")
+                          for p in self.planes] for _ in batch]
+            self.sim.run_batch(self.dev, self.outs, stream=self.stream)
+            if self.keep:
+                self.host = [[o.to("cpu", non_blocking=True) for o in ev] for ev in self.outs]
+            self.event = torch.cuda.Event()
+            self.event.record(self.stream)
+
+    def done(self) -> bool:
+        return self.event is not None and self.event.query()
+
+    def retire(self, batch: List[Request]):
+        self.sim.sync(stream=self.stream)
+        if self.keep:
+            for r, h in zip(batch, self.host):
+                r.waveforms = [x.numpy() for x in h]
+        self.dev, self.outs, self.host, self.event = [], [], [], None
+
+    def close(self):
+        self.sim.close()
+
+
 class _Slot:
-    def __init__(self, sim: Simulator, stream):
-        self.sim = sim
-        self.stream = stream
+    def __init__(self, backend):
+        self.backend = backend
         self.batch: List[Request] = []
-        self.dev: List[DeviceDepos] = []
-        self.outs: List[List] = []
-        self.done_event = None
         self.bytes = 0
 
 
 class EventServer:
     def __init__(self, planes, responses, diffusion, n_slots: int = 4, max_batch: int = 8,
-                 hbm_budget_bytes: int = 16 << 30, keep_results: bool = False):
-        import torch
-        self.torch = torch
+                 hbm_budget_bytes: int = 16 << 30, keep_results: bool = False, backend_factory=None):
         self.planes = list(planes)
-        self.slots = [_Slot(Simulator(planes, responses, diffusion), torch.cuda.Stream()) for _ in range(n_slots)]
+        make = backend_factory or (lambda: CudaBackend(planes, responses, diffusion, keep_results))
+        self.slots = [_Slot(make()) for _ in range(n_slots)]
         self.max_batch = max_batch
         self.budget = int(hbm_budget_bytes)
         self.in_use = 0
-        self.keep = keep_results
         self.pending: Deque[Request] = collections.deque()
         self.lock = threading.Lock()
         self.completed: List[Request] = []
@@ -98,46 +137,21 @@ class EventServer:
         return 20 * int(len(r.depos.t0)) + self.plane_bytes
 
     # -- scheduler ---------------------------------------------------------------------------
-    def _launch(self, slot: _Slot, batch: List[Request]):
-        torch = self.torch
-        slot.batch = batch
-        slot.bytes = sum(self.request_bytes(r) for r in batch)
-        now = time.perf_counter()
-        with torch.cuda.stream(slot.stream):
-            slot.dev = []
-            for r in batch:
-                r.t_admit = now
-                d = r.depos
-                dev = [_host_tensor(torch, a).to("cuda", non_blocking=True) for a in (d.t0, d.x, d.y, d.z, d.q)]
-                slot.dev.append(DeviceDepos(*dev, event_id=int(d.event_id)))
-            slot.outs = [[torch.empty((p.n_wires, p.n_ticks), dtype=torch.float32, device="cuda")
-                          for p in self.planes] for _ in batch]
-            slot.sim.run_batch(slot.dev, slot.outs, stream=slot.stream)
-            if self.keep:
-                slot.host = [[o.to("cpu", non_blocking=True) for o in ev] for ev in slot.outs]
-            slot.done_event = torch.cuda.Event()
-            slot.done_event.record(slot.stream)
-
-    def _retire(self, slot: _Slot):
-        now = time.perf_counter()
-        slot.sim.sync(stream=slot.stream)
-        for i, r in enumerate(slot.batch):
-            r.t_done = now
-            if self.keep:
-                r.waveforms = [h.numpy() for h in slot.host[i]]
-            r.done.set()
-            self.completed.append(r)
-        self.in_use -= slot.bytes
-        slot.batch, slot.dev, slot.outs, slot.done_event, slot.bytes = [], [], [], None, 0
-
     def step(self) -> int:
         """One scheduler pass: retire finished slots, admit pending requests into free slots.
         Returns the number of requests still pending or in flight."""
         for slot in self.slots:
-            if slot.done_event is not None and slot.done_event.query():
-                self._retire(slot)
+            if slot.batch and slot.backend.done():
+                now = time.perf_counter()
+                slot.backend.retire(slot.batch)
+                for r in slot.batch:
+                    r.t_done = now
+                    r.done.set()
+                    self.completed.append(r)
+                self.in_use -= slot.bytes
+                slot.batch, slot.bytes = [], 0
         for slot in self.slots:
-            if slot.done_event is not None:
+            if slot.batch:
                 continue
             batch: List[Request] = []
             need_total = 0
@@ -150,8 +164,12 @@ class EventServer:
                     batch.append(self.pending.popleft())
             if not batch:
                 break
-            self._launch(slot, batch)
-            self.in_use += slot.bytes
+            now = time.perf_counter()
+            for r in batch:
+                r.t_admit = now
+            slot.batch, slot.bytes = batch, need_total
+            self.in_use += need_total
+            slot.backend.launch(batch)
         with self.lock:
             return len(self.pending) + sum(len(s.batch) for s in self.slots)
 
@@ -162,7 +180,7 @@ class EventServer:
     def close(self):
         self.drain()
         for s in self.slots:
-            s.sim.close()
+            s.backend.close()
 
 
 def run_open_loop(server: EventServer, events: Sequence, rate_hz: float, seed: int = 0) -> dict:

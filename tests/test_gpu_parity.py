@@ -324,3 +324,20 @@ def test_windows_with_time_offsets_angles_and_edges():
     assert np.array_equal(to_np(desc), ref.desc)
     assert max_rel_bin(to_np(patches), ref.values) <= BIN_TOL
     assert max_rel_bin(to_np(grid), oracle.scatter(ref, pl)) <= BIN_TOL
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    # a wait that can never complete gives up, reports WCT_ETIMEOUT, and the GPU stays usable
+    import paper_2304_01841_gb300 as g
+    wl = synth.workload("tiny")
+    sim = make_sim(wl.planes, wl.responses(), wl.diffusion)
+    sim.selftest_wait(2_000_000)                     # ~1 ms at 2 GHz
+    with pytest.raises(g.WctError) as ei:
+        sim.sync()
+    assert ei.value.code == 4
+    sim.sync()                                       # status cleared
+    d = wl.depos()
+    wf = sim.run_event(_dev(d))[0]
+    sim.sync()
+    ref = oracle.simulate_plane(d, wl.planes[0], wl.diffusion, wl.responses()[0])[2]
+    assert rel_l2(to_np(wf), ref) <= WAVE_RTOL

@@ -1,0 +1,86 @@
+"""CPU tests of the serving scheduler (admission, HBM budget, continuous batching, FIFO), driven
+with a fake device backend whose batches finish after a set number of scheduler passes."""
+import numpy as np
+
+import synth
+from paper_2304_01841_gb300.serve import EventServer
+
+
+class FakeBackend:
+    log = []
+
+    def __init__(self, passes=2):
+        self.passes = passes
+        self.left = 0
+        self.batch = None
+
+    def launch(self, batch):
+        self.batch = [r.rid for r in batch]
+        self.left = self.passes
+        FakeBackend.log.append(("launch", id(self), tuple(self.batch)))
+
+    def done(self):
+        self.left -= 1
+        return self.left <= 0
+
+    def retire(self, batch):
+        FakeBackend.log.append(("retire", id(self), tuple(r.rid for r in batch)))
+
+    def close(self):
+        pass
+
+
+def _depos(n):
+    return synth.Depos(np.zeros(n), np.ones(n), np.zeros(n), np.zeros(n), np.ones(n))
+
+
+PLANES = [synth.Plane(10, 100)]          # 4 kB of waveform per request
+ONE = 4 * 10 * 100
+
+
+def _server(passes=2, **kw):
+    FakeBackend.log = []
+    return EventServer(PLANES, None, None, backend_factory=lambda: FakeBackend(passes), **kw)
+
+
+def test_fifo_and_batching_limits():
+    srv = _server(n_slots=2, max_batch=3, hbm_budget_bytes=1 << 30)
+    reqs = [srv.submit(_depos(10)) for _ in range(8)]
+    srv.drain()
+    launches = [b for kind, _, b in FakeBackend.log if kind == "launch"]
+    assert all(len(b) <= 3 for b in launches)
+    assert [rid for b in launches for rid in b] == list(range(8))          # FIFO, each once
+    assert sorted(r.rid for r in srv.completed) == list(range(8))
+    assert all(r.done.is_set() for r in reqs)
+
+
+def test_budget_limits_memory_in_flight():
+    need = 20 * 100 + ONE
+    srv = _server(n_slots=4, max_batch=4, hbm_budget_bytes=3 * need)
+    for _ in range(12):
+        srv.submit(_depos(100))
+    peak = 0
+    while srv.step() > 0:
+        peak = max(peak, srv.in_use)
+    assert peak <= 3 * need
+    assert len(srv.completed) == 12
+
+
+def test_oversized_request_runs_alone_when_idle():
+    srv = _server(n_slots=2, max_batch=4, hbm_budget_bytes=1000)   # every request is over budget
+    for _ in range(3):
+        srv.submit(_depos(50))
+    srv.drain()
+    launches = [b for kind, _, b in FakeBackend.log if kind == "launch"]
+    assert launches == [(0,), (1,), (2,)]
+
+
+def test_requests_arriving_later_join_as_slots_free():
+    srv = _server(n_slots=1, max_batch=8, hbm_budget_bytes=1 << 30, passes=3)
+    srv.submit(_depos(10))
+    srv.step()                                  # request 0 launched
+    for _ in range(3):
+        srv.submit(_depos(10))                  # arrive while the slot is busy
+    srv.drain()
+    launches = [b for kind, _, b in FakeBackend.log if kind == "launch"]
+    assert launches[0] == (0,) and launches[1] == (1, 2, 3)
