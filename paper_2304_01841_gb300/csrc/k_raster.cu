@@ -87,59 +87,37 @@ __device__ __forceinline__ float fold_plain(const Item &f, const float *wt, cons
 // counter-based pool: Philox4x32-10 of (depo, tick, wire * G + group, c3) under the key;
 // a call serves a group of four sub-bins, lanes 0/1 from the Box-Muller pair of words 0/1
 // and lanes 2/3 from words 2/3.
-// One Philox group (four sub-bins of a wire) of a fluctuated fold.
-__device__ __forceinline__ float fold_group(const uint4 &x, int g, const Item &f, float wa, const float *wp,
-                                            float q) {
-    const int sb = g << 2;
-    const int l0 = max(f.sub_lo - sb, 0), l1 = min(f.sub_hi - sb, 4);   // lanes [l0, l1)
-    float z[4];
-    if (l0 < 2) {
-        const float2 p = box_muller(x.x, x.y);
-        z[0] = p.x;
-        z[1] = p.y;
-    }
-    if (l1 > 2) {
-        const float2 p = box_muller(x.z, x.w);
-        z[2] = p.x;
-        z[3] = p.y;
-    }
-    float acc = 0.f;
-#pragma unroll
-    for (int l = 0; l < 4; ++l) {
-        if (l >= l0 && l < l1) {
-            const float w = wa * wp[f.j_base + sb + l];
-            const float m = q * w;
-            const float v = fmaf(sfu_sqrt(m * (1.f - w)), z[l], m);
-            acc += fmaxf(v, 0.f);
-        }
-    }
-    return acc;
-}
-
 __device__ __forceinline__ float fold_fluct(const Item &f, const float *wt, const float *wp, float q, uint32_t depo,
                                             const PlaneParams &pp, uint32_t c3) {
     const int G = (pp.n_imp + 3) >> 2;
     const float wa = wt[f.a];
-    const int g0 = f.sub_lo >> 2, g1 = (f.sub_hi - 1) >> 2;
-    const uint32_t cw = (uint32_t)(f.wire * G);
-    if (G <= 3) {
-        // up to three groups per wire (n_imp <= 12): the Philox calls are independent, so they
-        // are issued together and their dependency chains overlap
-        uint4 x[3];
-#pragma unroll
-        for (int u = 0; u < 3; ++u)
-            if (g0 + u <= g1)
-                x[u] = philox4x32_10(make_uint4(depo, (uint32_t)f.tick, cw + (uint32_t)(g0 + u), c3), pp.key0, pp.key1);
-        float acc = 0.f;
-#pragma unroll
-        for (int u = 0; u < 3; ++u)
-            if (g0 + u <= g1) acc += fold_group(x[u], g0 + u, f, wa, wp, q);
-        return acc;
-    }
     float acc = 0.f;
+    const int g0 = f.sub_lo >> 2, g1 = (f.sub_hi - 1) >> 2;
     for (int g = g0; g <= g1; ++g) {
-        const uint4 x = philox4x32_10(make_uint4(depo, (uint32_t)f.tick, cw + (uint32_t)g, c3), pp.key0, pp.key1);
-        acc += fold_group(x, g, f, wa, wp, q);
+        const uint4 x = philox4x32_10(
+            make_uint4(depo, (uint32_t)f.tick, (uint32_t)(f.wire * G + g), c3), pp.key0, pp.key1);
+        const int sb = g << 2;
+        const int l0 = max(f.sub_lo - sb, 0), l1 = min(f.sub_hi - sb, 4);   // lanes [l0, l1)
+        float z[4];
+        if (l0 < 2) {
+            const float2 p = box_muller(x.x, x.y);
+            z[0] = p.x;
+            z[1] = p.y;
+        }
+        if (l1 > 2) {
+            const float2 p = box_muller(x.z, x.w);
+            z[2] = p.x;
+            z[3] = p.y;
+        }
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            if (l >= l0 && l < l1) {
+                const float w = wa * wp[f.j_base + sb + l];
+                const float m = q * w;
+                const float v = fmaf(sfu_sqrt(m * (1.f - w)), z[l], m);
+                acc += fmaxf(v, 0.f);
+            }
+        }
     }
     return acc;
 }
@@ -523,7 +501,7 @@ __device__ __forceinline__ void raster_warp(WarpSmem &S, const float *__restrict
     }
 }
 
-__global__ void __launch_bounds__(kWarpsPerCta * 32, 6)
+__global__ void __launch_bounds__(kWarpsPerCta * 32)
 k_raster_warps(const float *__restrict__ t0, const float *__restrict__ x, const float *__restrict__ y,
                const float *__restrict__ z, const float *__restrict__ q, int64_t n, PlaneParams pp,
                uint32_t event_lo, float *__restrict__ grid, int32_t *status) {
@@ -534,7 +512,7 @@ k_raster_warps(const float *__restrict__ t0, const float *__restrict__ x, const 
 
 // Batched: warp-chunk c of the whole launch belongs to the (event, plane) pair whose chunk
 // range (in warp-chunks) holds c.
-__global__ void __launch_bounds__(kWarpsPerCta * 32, 6)
+__global__ void __launch_bounds__(kWarpsPerCta * 32)
 k_raster_batch_warps(const BatchTable tab, int32_t *status) {
     __shared__ WarpSmem S[kWarpsPerCta];
     const int warp = threadIdx.x >> 5;
