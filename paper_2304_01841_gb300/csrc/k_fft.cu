@@ -283,7 +283,7 @@ k_row_c2r(FFTPlan p, const float2 *__restrict__ spec, float *__restrict__ out, i
     }
 }
 
-constexpr int kRowThreadsCt = 512;
+constexpr int kRowThreadsCt = 1024;
 
 // ---- compile-time radix plans ---------------------------------------------------------
 // For the common lengths the radix sequence is a template parameter: every stage's Ns, stride
@@ -488,7 +488,7 @@ k_row_c2r_rs(FFTPlan p, const float2 *__restrict__ spec, float *__restrict__ out
 // RTW (M + 1 real-split twiddles, padded to M + 2), one mbarrier.  The twiddle tables are
 // loaded once per CTA.  While the transform of row r runs on B / C, the bulk copy of row
 // r + gridDim.x lands in A.
-constexpr int kRowThreads = 512;
+constexpr int kRowThreads = 1024;
 
 size_t row_tma_smem_bytes(int M) { return sizeof(float2) * (5 * (size_t)M + 4) + 16; }
 

@@ -88,14 +88,13 @@ __device__ __forceinline__ float fold_plain(const Item &f, const float *wt, cons
 // a call serves a group of four sub-bins, lanes 0/1 from the Box-Muller pair of words 0/1
 // and lanes 2/3 from words 2/3.
 __device__ __forceinline__ float fold_fluct(const Item &f, const float *wt, const float *wp, float q, uint32_t depo,
-                                            const PlaneParams &pp, uint32_t c3) {
+                                            const PlaneParams &pp, uint32_t c3, const uint32_t (&rk)[20]) {
     const int G = (pp.n_imp + 3) >> 2;
     const float wa = wt[f.a];
     float acc = 0.f;
     const int g0 = f.sub_lo >> 2, g1 = (f.sub_hi - 1) >> 2;
     for (int g = g0; g <= g1; ++g) {
-        const uint4 x = philox4x32_10(
-            make_uint4(depo, (uint32_t)f.tick, (uint32_t)(f.wire * G + g), c3), pp.key0, pp.key1);
+        const uint4 x = philox4x32_10_rk(make_uint4(depo, (uint32_t)f.tick, (uint32_t)(f.wire * G + g), c3), rk);
         const int sb = g << 2;
         const int l0 = max(f.sub_lo - sb, 0), l1 = min(f.sub_hi - sb, 4);   // lanes [l0, l1)
         float z[4];
@@ -191,7 +190,7 @@ __device__ __forceinline__ void raster_chunk(ChunkSmem &S, const float *__restri
                                              const float *__restrict__ y, const float *__restrict__ z,
                                              const float *__restrict__ q, int64_t n, const PlaneParams &pp,
                                              uint32_t event_lo, float *__restrict__ grid, int32_t *status,
-                                             int64_t chunk) {
+                                             int64_t chunk, const uint32_t (&RK)[20]) {
     const int tid = threadIdx.x, lane = tid & 31;
     const int64_t c0 = chunk * kChunk;
     const int cn = (int)((n - c0) < kChunk ? (n - c0) : kChunk);
@@ -289,7 +288,7 @@ __device__ __forceinline__ void raster_chunk(ChunkSmem &S, const float *__restri
                 const Item f = make_item(i_base + k - S.item_off[j], S.nw[j], S.wl[j], d, pp.n_imp);
                 const float *wt = S.w + (S.w_off[j] - w_base);
                 const float *wp = wt + d.nt;
-                v = pp.fluctuate ? fold_fluct(f, wt, wp, d.q, (uint32_t)(c0 + j), pp, c3) : fold_plain(f, wt, wp, d.q);
+                v = pp.fluctuate ? fold_fluct(f, wt, wp, d.q, (uint32_t)(c0 + j), pp, c3, RK) : fold_plain(f, wt, wp, d.q);
                 if (k < kItemCap) {   // a single very wide depo may exceed the cache
                     S.val[k] = v;
                     S.slot[k] = (uint8_t)j;
@@ -307,7 +306,7 @@ __device__ __forceinline__ void raster_chunk(ChunkSmem &S, const float *__restri
             const float *wt = S.w + (S.w_off[j] - w_base);
             float v;
             if (k < kItemCap) v = S.val[k];
-            else v = pp.fluctuate ? fold_fluct(f, wt, wt + d.nt, d.q, (uint32_t)(c0 + j), pp, c3)
+            else v = pp.fluctuate ? fold_fluct(f, wt, wt + d.nt, d.q, (uint32_t)(c0 + j), pp, c3, RK)
                                   : fold_plain(f, wt, wt + d.nt, d.q);
             if (pp.fluctuate) {
                 const float sm = S.sum[j];
@@ -341,7 +340,7 @@ __device__ __forceinline__ void raster_chunk(ChunkSmem &S, const float *__restri
 // ------------------------------------------------------------------------------------------
 constexpr int kWarpDepos = 8;
 constexpr int kWarpsPerCta = 4;
-constexpr int kWItemCap = 512;
+constexpr int kWItemCap = 384;
 constexpr int kWWCap = 640;        // >= 128 + 512, the weights of the largest window
 constexpr int kWBoxCap = 320;
 
@@ -358,6 +357,7 @@ struct WarpSmem {
     float w[kWWCap];
     float val[kWItemCap];
     float box[kWBoxCap];
+    int tgt[kWItemCap];        // box or grid index of each cached item, -1 off the grid
     uint8_t slot[kWItemCap];
 };
 
@@ -365,7 +365,7 @@ __device__ __forceinline__ void raster_warp(WarpSmem &S, const float *__restrict
                                             const float *__restrict__ y, const float *__restrict__ z,
                                             const float *__restrict__ q, int64_t n, const PlaneParams &pp,
                                             uint32_t event_lo, float *__restrict__ grid, int32_t *status,
-                                            int64_t chunk) {
+                                            int64_t chunk, const uint32_t (&RK)[20]) {
     const int lane = threadIdx.x & 31;
     const int64_t c0 = chunk * kWarpDepos;
     if (c0 >= n) return;
@@ -458,25 +458,47 @@ __device__ __forceinline__ void raster_warp(WarpSmem &S, const float *__restrict
                 const Item f = make_item(i_base + k - S.item_off[j], S.nw[j], S.wl[j], d, pp.n_imp);
                 const float *wt = S.w + (S.w_off[j] - w_base);
                 const float *wp = wt + d.nt;
-                v = pp.fluctuate ? fold_fluct(f, wt, wp, d.q, (uint32_t)(c0 + j), pp, c3) : fold_plain(f, wt, wp, d.q);
+                v = pp.fluctuate ? fold_fluct(f, wt, wp, d.q, (uint32_t)(c0 + j), pp, c3, RK) : fold_plain(f, wt, wp, d.q);
                 if (k < kWItemCap) {
                     S.val[k] = v;
                     S.slot[k] = (uint8_t)j;
+                    const bool in = f.wire >= 0 && f.wire < pp.n_wires && f.tick >= 0 && f.tick < pp.n_ticks;
+                    S.tgt[k] = !in ? -1 : (use_box ? (f.wire - bw0) * bnt + (f.tick - bt0) : f.wire * pp.n_ticks + f.tick);
                 }
             }
             if (pp.fluctuate) segmented_add(j, v, S.sum);
         }
         __syncwarp();
-        for (int k = lane; k < n_items; k += 32) {
-            const int j = k < kWItemCap ? (int)S.slot[k] : find_slot(S.item_off, s, e, i_base + k);
+        // cached items: target, depo and value were stored by the pass above
+        const int n_cached = min(n_items, kWItemCap);
+        for (int k = lane; k < n_cached; k += 32) {
+            const int t = S.tgt[k];
+            if (t < 0) continue;
+            const int j = S.slot[k];
+            float v = S.val[k];
+            if (pp.fluctuate) {
+                const float sm = S.sum[j];
+                if (sm > 0.f) {
+                    v *= S.d[j].q / sm;
+                } else {
+                    const DepoDesc &d = S.d[j];
+                    const Item f = make_item(i_base + k - S.item_off[j], S.nw[j], S.wl[j], d, pp.n_imp);
+                    const float *wt = S.w + (S.w_off[j] - w_base);
+                    v = fold_plain(f, wt, wt + d.nt, d.q);
+                }
+            }
+            if (use_box) atomicAdd(&S.box[t], v);
+            else atomicAdd(&grid[t], v);
+        }
+        // items beyond the cache (a single very wide depo) are recomputed
+        for (int k = kWItemCap + lane; k < n_items; k += 32) {
+            const int j = find_slot(S.item_off, s, e, i_base + k);
             const DepoDesc &d = S.d[j];
             const Item f = make_item(i_base + k - S.item_off[j], S.nw[j], S.wl[j], d, pp.n_imp);
             if (f.wire < 0 || f.wire >= pp.n_wires || f.tick < 0 || f.tick >= pp.n_ticks) continue;
             const float *wt = S.w + (S.w_off[j] - w_base);
-            float v;
-            if (k < kWItemCap) v = S.val[k];
-            else v = pp.fluctuate ? fold_fluct(f, wt, wt + d.nt, d.q, (uint32_t)(c0 + j), pp, c3)
-                                  : fold_plain(f, wt, wt + d.nt, d.q);
+            float v = pp.fluctuate ? fold_fluct(f, wt, wt + d.nt, d.q, (uint32_t)(c0 + j), pp, c3, RK)
+                                   : fold_plain(f, wt, wt + d.nt, d.q);
             if (pp.fluctuate) {
                 const float sm = S.sum[j];
                 if (sm > 0.f) v *= d.q / sm;
@@ -507,7 +529,7 @@ k_raster_warps(const float *__restrict__ t0, const float *__restrict__ x, const 
                uint32_t event_lo, float *__restrict__ grid, int32_t *status) {
     __shared__ WarpSmem S[kWarpsPerCta];
     const int warp = threadIdx.x >> 5;
-    raster_warp(S[warp], t0, x, y, z, q, n, pp, event_lo, grid, status, (int64_t)blockIdx.x * kWarpsPerCta + warp);
+    raster_warp(S[warp], t0, x, y, z, q, n, pp, event_lo, grid, status, (int64_t)blockIdx.x * kWarpsPerCta + warp, pp.rk);
 }
 
 // Batched: warp-chunk c of the whole launch belongs to the (event, plane) pair whose chunk
@@ -524,8 +546,9 @@ k_raster_batch_warps(const BatchTable tab, int32_t *status) {
         else hi = mid;
     }
     const BatchItem &it = tab.item[lo];
+    // every plane shares the seed, hence the round keys: take them from plane 0 (static index)
     raster_warp(S[warp], it.t0, it.x, it.y, it.z, it.q, it.n, tab.plane[it.plane], it.event_lo, it.grid, status,
-                c - it.chunk_begin);
+                c - it.chunk_begin, tab.plane[0].rk);
 }
 
 __global__ void __launch_bounds__(kChunkThreads)
@@ -534,7 +557,7 @@ k_raster_chunks(const float *__restrict__ t0, const float *__restrict__ x, const
                 uint32_t event_lo, float *__restrict__ grid, int32_t *status) {
     extern __shared__ float4 smem_raw[];
     ChunkSmem &S = *reinterpret_cast<ChunkSmem *>(smem_raw);
-    raster_chunk(S, t0, x, y, z, q, n, pp, event_lo, grid, status, blockIdx.x);
+    raster_chunk(S, t0, x, y, z, q, n, pp, event_lo, grid, status, blockIdx.x, pp.rk);
 }
 
 // Many (event, plane) pairs in one launch: CTA b takes chunk b - chunk_begin[i] of the pair i
@@ -552,7 +575,7 @@ k_raster_batch(const BatchTable tab, int32_t *status) {
     }
     const BatchItem &it = tab.item[lo];
     raster_chunk(S, it.t0, it.x, it.y, it.z, it.q, it.n, tab.plane[it.plane], it.event_lo, it.grid, status,
-                 b - it.chunk_begin);
+                 b - it.chunk_begin, tab.plane[0].rk);
 }
 
 // ------------------------------------------------------------------------------------------

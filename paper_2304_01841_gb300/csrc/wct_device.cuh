@@ -27,6 +27,20 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
+// The same generator with the ten round keys precomputed (rk[2r], rk[2r+1] = key + r * Weyl),
+// so each round's key is an operand instead of two additions.
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t (&rk)[20]) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ rk[2 * r], lo1, hi0 ^ c.w ^ rk[2 * r + 1], lo0);
+    }
+    return c;
+}
+
 // Two standard normals from two 32-bit words (Box-Muller): u = (x + 1/2) 2^-32 in (0,1),
 // r = sqrt(-2 ln u_a), (r cos 2 pi u_b, r sin 2 pi u_b).  Evaluated with the SFU's
 // approximate lg2 / sqrt / sin / cos instructions (relative errors ~2^-22, absolute sin/cos

@@ -31,6 +31,7 @@ struct PlaneParams {
     int32_t n_imp, n_wires, n_ticks, plane_index;
     int32_t fluctuate;
     uint32_t key0, key1;
+    uint32_t rk[20];                                     // Philox round keys of (key0, key1)
     int32_t tile_w, tile_t, n_tiles_w, n_tiles_t;
 };
 

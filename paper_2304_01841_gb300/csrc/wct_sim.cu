@@ -344,6 +344,10 @@ wct_status_t wct_sim_create(const wct_plane_t *planes, int n_planes, const wct_r
         pp.fluctuate = df.fluctuate ? 1 : 0;
         pp.key0 = (uint32_t)(df.seed & 0xFFFFFFFFu);
         pp.key1 = (uint32_t)(df.seed >> 32);
+        for (int r = 0; r < 10; ++r) {   // round r uses key + r * (0x9E3779B9, 0xBB67AE85), mod 2^32
+            pp.rk[2 * r] = pp.key0 + (uint32_t)r * 0x9E3779B9u;
+            pp.rk[2 * r + 1] = pp.key1 + (uint32_t)r * 0xBB67AE85u;
+        }
         pp.tile_w = tile_wires();
         pp.tile_t = tile_ticks();
         pp.n_tiles_w = (g.n_wires + pp.tile_w - 1) / pp.tile_w;
