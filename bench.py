@@ -126,12 +126,13 @@ N_SMS = 152
 ISSUE_PER_SM_CLK = 4
 
 
-def stage_bytes(plane, n_depos, resp_ticks=200):
-    """Algorithmic bytes per event of each stage (f32 = 4 B, c64 = 8 B; spectrum counted at
-    the unpadded minimum length n_ticks + resp_ticks - 1)."""
+def stage_bytes(plane, n_depos, spec_bins, resp_ticks=200):
+    """Algorithmic bytes per event of each stage (f32 = 4 B, c64 = 8 B).  The spectrum is
+    counted at the bins that carry signal: those below the response spectrum's support (the
+    library's spectrum_bins_used), at most the unpadded half length of n_ticks + 199."""
     nw, nt = plane.n_wires, plane.n_ticks
     grid = 4 * nw * nt
-    spec = 8 * nw * ((nt + resp_ticks - 1) // 2 + 1)
+    spec = 8 * nw * min(spec_bins, (nt + resp_ticks - 1) // 2 + 1)
     return {
         "prep_binning": 20 * n_depos,
         "raster_scatter": 20 * n_depos + grid,
@@ -416,7 +417,7 @@ def main():
     # ---- roofline of the dominant kernel -----------------------------------------------
     peak_gbs, sm_mhz_max, peak_kind = measured_peaks()
     issue_peak = N_SMS * ISSUE_PER_SM_CLK * sm_mhz_max * 1e6          # warp-instructions / s
-    sb = stage_bytes(plane, n_depos)
+    sb = stage_bytes(plane, n_depos, sim.plane_info(0)["spectrum_bins_used"])
     kern = {k: stages[k] for k in ("raster_scatter", "row_r2c", "wire_stage", "row_c2r")}
     dom = max(kern, key=kern.get)
     cnt = kernel_counters()

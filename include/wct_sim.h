@@ -188,8 +188,11 @@ wct_status_t wct_sim_run_batch(wct_sim_t *sim, const wct_depos_t *events, int n_
  * first device-side error since the last sync (WCT_EINVAL for invalid depos). */
 wct_status_t wct_sim_sync(wct_sim_t *sim, void *stream);
 
-/* Per-plane sizes: info[0..7] = {n_wires, n_ticks, fft_length, spectrum_bins,
- * spectrum_row_stride, tile_wires, tile_ticks, n_tiles}.  Host call, no device work. */
+/* Per-plane sizes: info[0..8] = {n_wires, n_ticks, fft_length, spectrum_bins,
+ * spectrum_row_stride, tile_wires, tile_ticks, n_tiles, spectrum_bins_used}; the last is the
+ * response spectrum's support (bins where some response row exceeds 2^-23, FP32 machine
+ * epsilon, times the largest magnitude; rounded up to even): the wire stage and inverse transform treat higher bins as zero.
+ * Host call, no device work. */
 wct_status_t wct_sim_plane_info(const wct_sim_t *sim, int plane, int64_t *info);
 
 /* Stage timing with CUDA events recorded on the caller's stream inside run_event.

@@ -107,10 +107,10 @@ class Simulator:
             pass
 
     def plane_info(self, plane: int) -> dict:
-        info = (ctypes.c_int64 * 8)()
+        info = (ctypes.c_int64 * 9)()
         self._check(self._lib.wct_sim_plane_info(self._h, plane, info))
         keys = ("n_wires", "n_ticks", "fft_length", "spectrum_bins", "spectrum_row_stride", "tile_wires",
-                "tile_ticks", "n_tiles")
+                "tile_ticks", "n_tiles", "spectrum_bins_used")
         return dict(zip(keys, (int(v) for v in info)))
 
     def _grid(self, plane: int, out=None):

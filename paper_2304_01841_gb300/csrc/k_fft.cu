@@ -235,7 +235,7 @@ k_row_r2c(FFTPlan p, const float *__restrict__ in, int64_t in_stride, int n_cols
     const float2 *Z = cta_fft<false>(buf, smem2 + p.M, p);
     // X[k] = (Z[k] + conj Z[M-k]) / 2 - i exp(-2 pi i k / P) (Z[k] - conj Z[M-k]) / 2
     float2 *out = spec + (int64_t)row * p.Fs;
-    for (int k = threadIdx.x; k < p.Fs; k += blockDim.x) {
+    for (int k = threadIdx.x; k < p.Fu; k += blockDim.x) {
         float2 X = make_float2(0.f, 0.f);
         if (k <= M) {
             const float2 a = Z[k == M ? 0 : k];
@@ -257,9 +257,10 @@ k_row_c2r(FFTPlan p, const float2 *__restrict__ spec, float *__restrict__ out, i
     const int row = blockIdx.x;
     const float2 *X = spec + (int64_t)row * p.Fs;
     // E = (X[k] + conj X[M-k]) / 2, O = exp(2 pi i k / P) (X[k] - conj X[M-k]) / 2, Z = E + i O
+    const float2 zero = make_float2(0.f, 0.f);
     for (int k = threadIdx.x; k < M; k += blockDim.x) {
-        const float2 a = X[k];
-        const float2 b = conjf2(X[M - k]);
+        const float2 a = k < p.Fu ? X[k] : zero;
+        const float2 b = M - k < p.Fu ? conjf2(X[M - k]) : zero;
         const float2 O = cmul(conjf2(__ldg(&p.rtw[k])), csub(a, b));
         const float2 s = cadd(a, b);
         buf[k] = make_float2(0.5f * (s.x - O.y), 0.5f * (s.y + O.x));
@@ -446,7 +447,7 @@ k_row_r2c_rs(FFTPlan p, const float *__restrict__ in, int n_cols, float2 *__rest
     __syncthreads();
     RsFft<Plan>::template run<false>(buf, p.tw);
     float2 *out = spec + (size_t)row * p.Fs;
-    for (int k = threadIdx.x; k < p.Fs; k += kRsThreads) {
+    for (int k = threadIdx.x; k < p.Fu; k += kRsThreads) {
         float2 X = make_float2(0.f, 0.f);
         if (k <= M) {
             const float2 a = buf[k == M ? 0 : k];
@@ -466,9 +467,10 @@ k_row_c2r_rs(FFTPlan p, const float2 *__restrict__ spec, float *__restrict__ out
     constexpr int M = RsFft<Plan>::M;
     const int row = blockIdx.x;
     const float2 *X = spec + (size_t)row * p.Fs;
+    const float2 zero = make_float2(0.f, 0.f);
     for (int k = threadIdx.x; k < M; k += kRsThreads) {
-        const float2 a = X[k];
-        const float2 b = conjf2(X[M - k]);
+        const float2 a = k < p.Fu ? X[k] : zero;
+        const float2 b = M - k < p.Fu ? conjf2(X[M - k]) : zero;
         const float2 O = cmul(conjf2(__ldg(&p.rtw[k])), csub(a, b));
         const float2 sm = cadd(a, b);
         buf[k] = make_float2(0.5f * (sm.x - O.y), 0.5f * (sm.y + O.x));
@@ -560,7 +562,7 @@ k_row_r2c_tma(FFTPlan p, const float *__restrict__ in, int n_rows, int n_cols, f
         }
         const float2 *Z = FFT::template range<false>(B, B, C, p, TW, 1, p.n_stages);
         float2 *out = spec + (size_t)row * p.Fs;
-        for (int k = threadIdx.x; k < p.Fs; k += blockDim.x) {
+        for (int k = threadIdx.x; k < p.Fu; k += blockDim.x) {
             float2 X = make_float2(0.f, 0.f);
             if (k <= M) {
                 const float2 a = Z[k == M ? 0 : k];
@@ -584,8 +586,9 @@ k_row_c2r_tma(FFTPlan p, const float2 *__restrict__ spec, int n_rows, float *__r
     const RowSmem L(sm4, M);
     float2 *A = L.A, *B = L.B, *C = L.C, *TW = L.TW, *RTW = L.RTW;
     uint64_t *bar = L.bar;
-    const uint32_t bytes = (uint32_t)p.Fs * 8u;        // Fs <= M + 2
+    const uint32_t bytes = (uint32_t)p.Fu * 8u;        // Fu <= Fs <= M + 2
     row_tma_init(p, TW, RTW, bar);
+    for (int k = p.Fu + threadIdx.x; k < M + 2; k += blockDim.x) A[k] = make_float2(0.f, 0.f);   // kept
     __syncthreads();
     int row = blockIdx.x;
     if (threadIdx.x == 0 && row < n_rows) {
@@ -625,10 +628,10 @@ constexpr int kStageThreads = 128;
 constexpr int kStageRun = 64;                // wires per thread
 
 __global__ void __launch_bounds__(kStageThreads)
-k_wire_stage(const float2 *__restrict__ S, const float2 *__restrict__ Rt, int Fs, int n_wires,
+k_wire_stage(const float2 *__restrict__ S, const float2 *__restrict__ Rt, int Fs, int Fu, int n_wires,
              float2 *__restrict__ T) {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= Fs) return;
+    if (f >= Fu) return;
     const int w0 = blockIdx.y * kStageRun;
     const int w1 = min(w0 + kStageRun, n_wires);
     const int n_in = (w1 - w0) + 2 * KC;
@@ -664,28 +667,28 @@ k_wire_stage(const float2 *__restrict__ S, const float2 *__restrict__ Rt, int Fs
 }
 
 // ---- wire stage fed by bulk copies -------------------------------------------------------
-// CTA = kStageFB consecutive frequencies x a run of kStageWires output wires.  A producer warp
-// streams the input rows' frequency slices (kStageFB complex = 1 KB each) into a ring of
+// CTA = kStageFB consecutive frequencies x a run of wires_per_cta output wires.  A producer
+// warp streams the input rows' frequency slices (kStageFB complex = 1 KB each) into a ring of
 // kRingGroups groups of kGroupRows rows with bulk copies, one mbarrier pair per group; the
-// consumer threads (one per frequency) run the same push-form 21-tap stencil as k_wire_stage,
-// reading each input row once from shared memory.  full[g] completes when a group's copies
+// consumer threads (one per frequency) run the 21-tap stencil in pull form, reading each input
+// row once from shared memory.  full[g] completes when a group's copies
 // landed, empty[g] when every consumer finished reading the group.
 constexpr int kStageFB = 128;
-constexpr int kStageWires = 128;
+constexpr int kStageWiresMax = 128;      // output wires per CTA at most (runtime: 128, 64 or 32)
 constexpr int kGroupRows = 8;
 constexpr int kRingGroups = 4;
 
 __global__ void __launch_bounds__(kStageFB + 32)
-k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, int Fs, int n_wires,
-                 float2 *__restrict__ T, int32_t *status) {
+k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, int Fs, int Fu, int n_wires,
+                 int wires_per_cta, float2 *__restrict__ T, int32_t *status) {
     __shared__ __align__(16) float2 ring[kRingGroups * kGroupRows][kStageFB];
     __shared__ uint64_t full[kRingGroups], empty[kRingGroups];
     const int tid = threadIdx.x;
     const int f0 = blockIdx.x * kStageFB;
-    const int nf = min(kStageFB, Fs - f0);             // even (Fs even, f0 multiple of 128)
+    const int nf = min(kStageFB, Fu - f0);             // even (Fu even, f0 multiple of 128)
     const uint32_t row_bytes = (uint32_t)nf * 8u;
-    const int w0 = blockIdx.y * kStageWires;
-    const int w1 = min(w0 + kStageWires, n_wires);
+    const int w0 = blockIdx.y * wires_per_cta;
+    const int w1 = min(w0 + wires_per_cta, n_wires);
     const int n_in = (w1 - w0) + 2 * KC;               // input rows s = w0 - KC + m
     const int m_lo = max(0, KC - w0);                  // rows inside the plane: [m_lo, m_hi)
     const int m_hi = min(n_in, n_wires - w0 + KC);
@@ -871,7 +874,7 @@ cudaError_t launch_row_tma_kernel(const FFTPlan &p, size_t smem, int grid, cudaS
             if (p.radix[k++] != r) return false;
         return true;
     };
-    if (is({4, 7, 7, 5, 5})) return go(K::template get<CompiledFft<CtPlan<4, 7, 7, 5, 5>>>());
+    if (is({7, 4, 5, 5, 7})) return go(K::template get<CompiledFft<CtPlan<7, 4, 5, 5, 7>>>());
     if (is({5, 5, 5, 5, 5})) return go(K::template get<CompiledFft<CtPlan<5, 5, 5, 5, 5>>>());
     if (is({5, 5, 5, 5})) return go(K::template get<CompiledFft<CtPlan<5, 5, 5, 5>>>());
     return go(K::template get<RuntimeFft>());
@@ -897,11 +900,11 @@ bool launch_row_rs(const FFTPlan &p, Launch &&launch, cudaError_t &err) {
         return true;
     };
     if constexpr (R2C) {
-        if (is({4, 7, 7, 5, 5})) return go(k_row_r2c_rs<CtPlan<4, 7, 7, 5, 5>>);
+        if (is({7, 4, 5, 5, 7})) return go(k_row_r2c_rs<CtPlan<7, 4, 5, 5, 7>>);
         if (is({5, 5, 5, 5, 5})) return go(k_row_r2c_rs<CtPlan<5, 5, 5, 5, 5>>);
         if (is({5, 5, 5, 5})) return go(k_row_r2c_rs<CtPlan<5, 5, 5, 5>>);
     } else {
-        if (is({4, 7, 7, 5, 5})) return go(k_row_c2r_rs<CtPlan<4, 7, 7, 5, 5>>);
+        if (is({7, 4, 5, 5, 7})) return go(k_row_c2r_rs<CtPlan<7, 4, 5, 5, 7>>);
         if (is({5, 5, 5, 5, 5})) return go(k_row_c2r_rs<CtPlan<5, 5, 5, 5, 5>>);
         if (is({5, 5, 5, 5})) return go(k_row_c2r_rs<CtPlan<5, 5, 5, 5>>);
     }
@@ -964,13 +967,18 @@ cudaError_t launch_row_c2r(const FFTPlan &p, const float2 *spec, int n_rows, flo
 cudaError_t launch_wire_stage(const FFTPlan &p, const float2 *spec, const float2 *resp_spec, int n_wires, float2 *out,
                               cudaStream_t s, int32_t *status) {
     if (n_wires <= 0) return cudaSuccess;
-    if (aligned16(spec) && (p.Fs % 2) == 0) {
-        dim3 grid((p.Fs + kStageFB - 1) / kStageFB, (n_wires + kStageWires - 1) / kStageWires);
-        k_wire_stage_tma<<<grid, kStageFB + 32, 0, s>>>(spec, resp_spec, p.Fs, n_wires, out, status);
+    if (aligned16(spec) && (p.Fs % 2) == 0 && (p.Fu % 2) == 0) {
+        // fewer wires per CTA when the frequency blocks alone leave the SMs short of CTAs
+        // (about six resident per SM hide the ring's latency); each CTA re-reads 20 halo rows
+        const int fb = (p.Fu + kStageFB - 1) / kStageFB;
+        int wpc = kStageWiresMax;
+        while (wpc > 32 && (int64_t)fb * ((n_wires + wpc - 1) / wpc) < 6 * 152) wpc /= 2;
+        dim3 grid(fb, (n_wires + wpc - 1) / wpc);
+        k_wire_stage_tma<<<grid, kStageFB + 32, 0, s>>>(spec, resp_spec, p.Fs, p.Fu, n_wires, wpc, out, status);
         return cudaGetLastError();
     }
-    dim3 grid((p.Fs + kStageThreads - 1) / kStageThreads, (n_wires + kStageRun - 1) / kStageRun);
-    k_wire_stage<<<grid, kStageThreads, 0, s>>>(spec, resp_spec, p.Fs, n_wires, out);
+    dim3 grid((p.Fu + kStageThreads - 1) / kStageThreads, (n_wires + kStageRun - 1) / kStageRun);
+    k_wire_stage<<<grid, kStageThreads, 0, s>>>(spec, resp_spec, p.Fs, p.Fu, n_wires, out);
     return cudaGetLastError();
 }
 

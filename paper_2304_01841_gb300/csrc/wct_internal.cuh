@@ -47,6 +47,8 @@ struct FFTPlan {
     int32_t fft_len;      // real length P = 2M
     int32_t F;            // spectrum bins = M + 1
     int32_t Fs;           // spectrum row stride (complex elements), even
+    int32_t Fu;           // spectrum bins carried through the wire stage (even, <= Fs): the
+                          // response spectrum's support; bins above it are treated as zero
     float2 *tw;           // device: exp(-2 pi i k / M), k < M
     float2 *rtw;          // device: exp(-2 pi i k / P), k <= M
 };

@@ -119,6 +119,128 @@ bool smooth7(int64_t m) {
     return m == 1;
 }
 
+// Highest bin f < F whose exact DFT (length P, FP64) of some response row exceeds `thr` in
+// magnitude; scans down from the top and stops at the first such bin (0 if none).
+int response_support_last(const wct_response_t &r, int P, int F, double thr) {
+    std::vector<double> c(P), sn(P);
+    for (int j = 0; j < P; ++j) {
+        const double a = 2.0 * M_PI * (double)j / (double)P;
+        c[j] = std::cos(a);
+        sn[j] = std::sin(a);
+    }
+    const double thr2 = thr * thr;
+    for (int f = F - 1; f > 0; --f)
+        for (int row = 0; row < r.n_wires_resp; ++row) {
+            const float *x = r.host_data + (size_t)row * r.n_ticks_resp;
+            double re = 0.0, im = 0.0;
+            int64_t j = 0;
+            for (int n = 0; n < r.n_ticks_resp; ++n) {
+                re += (double)x[n] * c[j];
+                im -= (double)x[n] * sn[j];
+                j += f;
+                if (j >= P) j -= P;
+            }
+            if (re * re + im * im > thr2) return f;
+        }
+    return 0;
+}
+
+constexpr int kNumRadices = 6;
+
+// Shared-memory wavefronts of one Stockham stage (radix R after stages of product NS) for a
+// length-M transform: each warp handles 32 consecutive butterflies j, reads its R inputs
+// x[j + r M/R] (contiguous), one twiddle tw[(j mod NS) M/(NS R)] and writes its R outputs to
+// (j - j mod NS) R + j mod NS + r NS.  A 64-bit access costs, per bank (32 banks of 4 bytes),
+// one wavefront per distinct word the warp touches there.
+int64_t stage_wavefronts(int M, int R, int NS) {
+    const int NB = M / R, stride = M / (NS * R);
+    int64_t total = 0;
+    int64_t addr[32];
+    auto cost = [&](int n) {
+        int words[32][64];
+        int nw[32] = {0};
+        int worst = 0;
+        for (int l = 0; l < n; ++l)
+            for (int h = 0; h < 2; ++h) {
+                const int64_t w = 2 * addr[l] + h;
+                const int b = (int)(w % 32);
+                bool seen = false;
+                for (int i = 0; i < nw[b]; ++i) seen |= words[b][i] == (int)w;
+                if (!seen) words[b][nw[b]++] = (int)w;
+                worst = std::max(worst, nw[b]);
+            }
+        return (int64_t)worst;
+    };
+    for (int w0 = 0; w0 < NB; w0 += 32) {
+        const int n = std::min(32, NB - w0);
+        for (int rr = 0; rr < R; ++rr) {
+            for (int l = 0; l < n; ++l) addr[l] = w0 + l + (int64_t)rr * NB;
+            total += cost(n);
+        }
+        if (NS > 1) {
+            for (int l = 0; l < n; ++l) addr[l] = (int64_t)((w0 + l) % NS) * stride;
+            total += cost(n);
+        }
+        for (int rr = 0; rr < R; ++rr) {
+            for (int l = 0; l < n; ++l) {
+                const int j = w0 + l, k = j % NS;
+                addr[l] = (int64_t)(j - k) * R + k + (int64_t)rr * NS;
+            }
+            total += cost(n);
+        }
+    }
+    return total;
+}
+
+// Stage order with the fewest shared-memory wavefronts under stage_wavefronts: dynamic
+// programming over the sub-multisets of radices already applied (the next stage's cost
+// depends only on its radix and the product of those before it).
+void order_stages(int M, const int rads[kNumRadices], const int count[kNumRadices], int32_t *out) {
+    int dims[kNumRadices], n_states = 1;
+    for (int i = 0; i < kNumRadices; ++i) {
+        dims[i] = count[i] + 1;
+        n_states *= dims[i];
+    }
+    auto decode = [&](int s, int *c) {
+        for (int i = 0; i < kNumRadices; ++i) {
+            c[i] = s % dims[i];
+            s /= dims[i];
+        }
+    };
+    auto encode = [&](const int *c) {
+        int s = 0;
+        for (int i = kNumRadices - 1; i >= 0; --i) s = s * dims[i] + c[i];
+        return s;
+    };
+    const int64_t inf = INT64_MAX / 4;
+    std::vector<int64_t> best(n_states, inf);
+    std::vector<int> from(n_states, -1), via(n_states, -1);
+    best[0] = 0;
+    for (int s = 0; s < n_states; ++s) {            // states in increasing code: predecessors first
+        if (best[s] >= inf) continue;
+        int c[kNumRadices];
+        decode(s, c);
+        int NS = 1;
+        for (int i = 0; i < kNumRadices; ++i)
+            for (int k = 0; k < c[i]; ++k) NS *= rads[i];
+        for (int i = 0; i < kNumRadices; ++i) {
+            if (c[i] == count[i]) continue;
+            ++c[i];
+            const int t = encode(c);
+            --c[i];
+            const int64_t v = best[s] + stage_wavefronts(M, rads[i], NS);
+            if (v < best[t]) {
+                best[t] = v;
+                from[t] = s;
+                via[t] = rads[i];
+            }
+        }
+    }
+    std::vector<int> seq;
+    for (int s = n_states - 1; s > 0; s = from[s]) seq.push_back(via[s]);
+    for (size_t k = 0; k < seq.size(); ++k) out[k] = seq[seq.size() - 1 - k];
+}
+
 // FFT length: the smallest even P >= n_ticks + n_resp_ticks - 1 with P / 2 7-smooth, so
 // the circular convolution of length P equals the linear one on the kept ticks.
 bool plan_fft(int n_ticks, int kt, FFTPlan &p) {
@@ -130,20 +252,26 @@ bool plan_fft(int n_ticks, int kt, FFTPlan &p) {
     p.fft_len = (int32_t)(2 * M);
     p.F = (int32_t)(M + 1);
     p.Fs = (int32_t)((M + 2) & ~1LL);
+    p.Fu = p.Fs;
+    // radix multiset: largest radices first (fewest stages); their order is chosen below
     int64_t r = M;
+    const int rads[kNumRadices] = {8, 7, 5, 4, 3, 2};
+    int count[kNumRadices] = {0, 0, 0, 0, 0, 0};
     int ns = 0;
-    const int order[] = {8, 4, 7, 5, 3, 2};
-    for (int rad : order) {
+    for (int rad : {8, 4, 7, 5, 3, 2}) {
         while (r % rad == 0) {
-            if (ns >= 12) return false;
-            p.radix[ns++] = rad;
+            if (++ns > 12) return false;
+            for (int i = 0; i < kNumRadices; ++i)
+                if (rads[i] == rad) ++count[i];
             r /= rad;
         }
     }
+    if (r != 1) return false;
+    order_stages((int)M, rads, count, p.radix);
     p.n_stages = ns;
     p.radix_code = 0;
     for (int k = 0; k < ns; ++k) p.radix_code |= (uint64_t)p.radix[k] << (4 * k);
-    return r == 1;
+    return true;
 }
 
 wct_status_t upload_twiddles(wct_sim *s, FFTPlan &p) {
@@ -397,7 +525,30 @@ wct_status_t wct_sim_create(const wct_plane_t *planes, int n_planes, const wct_r
             e = launch_scale_spectrum(ps.resp_spec, (int64_t)KW * ps.fft.Fs, 1.0f / (float)ps.fft.M, 0);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         dev_free(s, d_resp, sizeof(float) * pad.size());
-        if (e != cudaSuccess) st = cuda_fail(s, e, "response spectrum");
+        if (e != cudaSuccess) {
+            st = cuda_fail(s, e, "response spectrum");
+            break;
+        }
+        // Spectral support: the time spectra of the response rows decay fast (smooth field and
+        // shaping functions).  Bins where every row's exact (FP64) spectrum is below FP32
+        // machine epsilon (2^-23) times the largest magnitude are at the level of the rounding
+        // of the FP32 response samples themselves; they are treated as zero, and only the bins
+        // below the support go through the wire stage and the inverse transform.  A response
+        // with full support (e.g. a delta) keeps every bin.
+        std::vector<float2> hs((size_t)KW * ps.fft.Fs);
+        e = cudaMemcpy(hs.data(), ps.resp_spec, sizeof(float2) * hs.size(), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            st = cuda_fail(s, e, "response spectrum support");
+            break;
+        }
+        double gmax = 0.0;   // scale of the threshold from the device spectrum (FP32-accurate)
+        for (int k = 0; k < KW; ++k)
+            for (int f = 0; f < ps.fft.F; ++f) {
+                const float2 v = hs[(size_t)k * ps.fft.Fs + f];
+                gmax = std::max(gmax, std::sqrt((double)v.x * v.x + (double)v.y * v.y));
+            }
+        const int last = response_support_last(r, 2 * ps.fft.M, ps.fft.F, 0x1p-23 * gmax * (double)ps.fft.M);
+        ps.fft.Fu = std::min(ps.fft.Fs, (last + 2) & ~1);
     }
     if (st != WCT_OK) {
         for (void *a : s->allocs)
@@ -703,6 +854,7 @@ wct_status_t wct_sim_plane_info(const wct_sim_t *s, int plane, int64_t *info) {
     info[5] = ps.pp.tile_w;
     info[6] = ps.pp.tile_t;
     info[7] = ps.n_tiles;
+    info[8] = ps.fft.Fu;
     return WCT_OK;
 }
 

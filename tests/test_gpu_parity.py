@@ -114,6 +114,9 @@ def test_convolve_random_grid(shape, kind):
     sim.sync()
     ref = oracle.convolve_fft(g, resp, workers=4)
     assert rel_l2(to_np(out), ref) <= WAVE_RTOL
+    info = sim.plane_info(0)
+    if nt >= 1000:        # smooth responses: the white grid's bins above the support are dropped
+        assert info["spectrum_bins_used"] < 0.6 * info["spectrum_bins"]
 
 
 def test_convolve_small_response_and_in_place():
@@ -137,6 +140,8 @@ def test_convolve_delta_response_is_identity():
     out = sim.convolve(0, torch.from_numpy(g).cuda())
     sim.sync()
     assert np.abs(to_np(out) - g).max() <= 1e-5 * np.abs(g).max()
+    info = sim.plane_info(0)
+    assert info["spectrum_bins_used"] >= info["spectrum_bins"]      # a delta keeps every bin
 
 
 # ------------------------------------------------------------------------------------------
