@@ -491,10 +491,7 @@ wct_status_t wct_sim_create(const wct_plane_t *planes, int n_planes, const wct_r
             break;
         }
         st = upload_twiddles(s, ps.fft);
-        spec_elems = std::max(spec_elems, (size_t)g.n_wires * ps.fft.Fs);
     }
-    if (st == WCT_OK) st = dev_alloc(s, (void **)&s->spec, sizeof(float2) * spec_elems);
-    if (st == WCT_OK) st = dev_alloc(s, (void **)&s->spec2, sizeof(float2) * spec_elems);
     if (st == WCT_OK) st = dev_alloc(s, (void **)&s->tile_count, sizeof(int32_t) * (max_tiles + 1));
     if (st == WCT_OK) st = dev_alloc(s, (void **)&s->tile_off, sizeof(int32_t) * (max_tiles + 1));
     if (st == WCT_OK) st = dev_alloc(s, (void **)&s->tile_cursor, sizeof(int32_t) * (max_tiles + 1));
@@ -548,8 +545,28 @@ wct_status_t wct_sim_create(const wct_plane_t *planes, int n_planes, const wct_r
                 gmax = std::max(gmax, std::sqrt((double)v.x * v.x + (double)v.y * v.y));
             }
         const int last = response_support_last(r, 2 * ps.fft.M, ps.fft.F, 0x1p-23 * gmax * (double)ps.fft.M);
-        ps.fft.Fu = std::min(ps.fft.Fs, (last + 2) & ~1);
+        const int Fu = std::min(ps.fft.Fs, (last + 2) & ~1);
+        if (Fu < ps.fft.Fs) {
+            // the grid spectra and the response spectrum keep only the supported bins: row
+            // stride Fu (even, so rows stay 16-byte aligned)
+            float2 *packed = nullptr;
+            st = dev_alloc(s, (void **)&packed, sizeof(float2) * (size_t)KW * Fu);
+            if (st != WCT_OK) break;
+            e = cudaMemcpy2D(packed, sizeof(float2) * Fu, ps.resp_spec, sizeof(float2) * ps.fft.Fs, sizeof(float2) * Fu,
+                             KW, cudaMemcpyDeviceToDevice);
+            if (e != cudaSuccess) {
+                st = cuda_fail(s, e, "response spectrum support");
+                break;
+            }
+            dev_free(s, ps.resp_spec, sizeof(float2) * (size_t)KW * ps.fft.Fs);
+            ps.resp_spec = packed;
+            ps.fft.Fs = Fu;
+        }
+        ps.fft.Fu = Fu;
+        spec_elems = std::max(spec_elems, (size_t)ps.g.n_wires * ps.fft.Fs);
     }
+    if (st == WCT_OK) st = dev_alloc(s, (void **)&s->spec, sizeof(float2) * spec_elems);
+    if (st == WCT_OK) st = dev_alloc(s, (void **)&s->spec2, sizeof(float2) * spec_elems);
     if (st != WCT_OK) {
         for (void *a : s->allocs)
             if (a) cudaFree(a);
