@@ -621,6 +621,232 @@ k_row_c2r_tma(FFTPlan p, const float2 *__restrict__ spec, int n_rows, float *__r
     }
 }
 
+// ---- paired row transforms: two persistent CTAs per SM -----------------------------------
+// Shared memory per CTA: A and B (M + 2 entries each, ping-pong), TWH (the twiddles
+// exp(-2 pi i k / M) for k <= M/2; the upper half follows from tw[M - k] = conj tw[k]) and
+// one mbarrier: about 96 KB at M = 4900, so two CTAs share an SM and one CTA's barriers and
+// copy waits overlap the other's arithmetic.  The real-split twiddles exp(-i pi k / M) are
+// derived from the same table: tw[k / 2] for even k, tw[(k - 1) / 2] * exp(-i pi / M) for odd
+// k.  The row copy lands in A; the transform runs A -> B -> A ...; for an odd stage count A is
+// free after the last stage, so the next row's copy overlaps the output pass.
+constexpr int kPairThreads = 512;
+
+size_t row_pair_smem_bytes(int M) { return sizeof(float2) * (2 * (size_t)(M + 2) + (size_t)(M / 2 + 2)) + 16; }
+
+struct PairSmem {
+    float2 *A, *B, *TWH;
+    uint64_t *bar;
+    __device__ __forceinline__ PairSmem(float4 *base, int M) {
+        A = reinterpret_cast<float2 *>(base);
+        B = A + M + 2;
+        TWH = B + M + 2;
+        bar = reinterpret_cast<uint64_t *>(TWH + M / 2 + 2);
+    }
+};
+
+template <int M>
+__device__ __forceinline__ float2 tw_half(const float2 *TWH, int idx) {   // exp(-2 pi i idx / M), 0 <= idx < M
+    const bool hi = idx > M / 2;
+    float2 w = TWH[hi ? M - idx : idx];
+    if (hi) w.y = -w.y;
+    return w;
+}
+
+template <int M>
+__device__ __forceinline__ float2 rtw_half(const float2 *TWH, float2 c1, int k) {   // exp(-i pi k / M), 0 <= k <= M
+    const float2 w = tw_half<M>(TWH, k >> 1);
+    return (k & 1) ? cmul(w, c1) : w;
+}
+
+template <int R, int NS, int M, int T, bool INV>
+__device__ __forceinline__ void stage_pair(const float2 *__restrict__ in, float2 *__restrict__ out,
+                                           const float2 *__restrict__ TWH) {
+    constexpr int NB = M / R;
+    constexpr int STRIDE = M / (NS * R);
+    constexpr int ITER = (NB + T - 1) / T;
+#pragma unroll
+    for (int it = 0; it < ITER; ++it) {
+        const int j = threadIdx.x + it * T;
+        if (ITER * T == NB || j < NB) {
+            const int k = j % NS;
+            float2 v[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = in[j + r * NB];
+            if (NS > 1) {
+                float2 w1 = tw_half<M>(TWH, k * STRIDE);
+                if (INV) w1.y = -w1.y;
+                float2 w = w1;
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    v[r] = cmul(v[r], w);
+                    if (r + 1 < R) w = cmul(w, w1);
+                }
+            }
+            Dft<R, INV>::run(v);
+            const int base = (j - k) * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) out[base + r * NS] = v[r];
+        }
+    }
+    __syncthreads();
+}
+
+template <int M, int T, bool INV, int NS, int R, int... Rest>
+struct FftPair {
+    // stages from `in` (A or B) alternating between A and B; returns the buffer with the result
+    __device__ __forceinline__ static float2 *run(float2 *in, float2 *A, float2 *B, const float2 *TWH) {
+        float2 *out = (in == A) ? B : A;
+        stage_pair<R, NS, M, T, INV>(in, out, TWH);
+        if constexpr (sizeof...(Rest) == 0) return out;
+        else return FftPair<M, T, INV, NS * R, Rest...>::run(out, A, B, TWH);
+    }
+};
+
+template <int M>
+__device__ __forceinline__ void pair_init(const FFTPlan &p, float2 *TWH, uint64_t *bar) {
+    for (int k = threadIdx.x; k <= M / 2; k += blockDim.x) TWH[k] = p.tw[k];
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+}
+
+// generic-proxy writes of every thread to A are ordered before the next bulk copy into A
+__device__ __forceinline__ void release_to_copy() {
+    fence_proxy_async_smem();
+    __syncthreads();
+}
+
+template <int... Rs>
+__global__ void __launch_bounds__(kPairThreads, 2)
+k_row_r2c_pair(FFTPlan p, const float *__restrict__ in, int n_rows, int n_cols, float2 *__restrict__ spec,
+               int32_t *status) {
+    constexpr int M = (Rs * ...);
+    constexpr bool kOdd = (sizeof...(Rs) & 1) != 0;     // result in B, A free after the last stage
+    extern __shared__ float4 sm4[];
+    const PairSmem L(sm4, M);
+    float2 *A = L.A, *B = L.B;
+    const float2 *TWH = L.TWH;
+    uint64_t *bar = L.bar;
+    const int half = n_cols >> 1;                      // n_cols % 4 == 0, half <= M
+    const uint32_t bytes = (uint32_t)n_cols * 4u;
+    const float2 c1 = p.rtw[1];
+    pair_init<M>(p, L.TWH, bar);
+    __syncthreads();
+    int row = blockIdx.x;
+    if (threadIdx.x == 0 && row < n_rows) {
+        mbar_arrive_expect_tx(bar, bytes);
+        bulk_g2s(A, in + (size_t)row * n_cols, bytes, bar);
+    }
+    uint32_t parity = 0;
+    for (; row < n_rows; row += gridDim.x) {
+        for (int k = half + threadIdx.x; k < M; k += kPairThreads) A[k] = make_float2(0.f, 0.f);   // zero pad
+        if (!row_tma_wait(bar, parity, status)) return;
+        parity ^= 1u;
+        const float2 *Z = FftPair<M, kPairThreads, false, 1, Rs...>::run(A, A, B, TWH);
+        const int next = row + gridDim.x;
+        if constexpr (kOdd) {
+            release_to_copy();
+            if (threadIdx.x == 0 && next < n_rows) {
+                mbar_arrive_expect_tx(bar, bytes);
+                bulk_g2s(A, in + (size_t)next * n_cols, bytes, bar);
+            }
+        }
+        float2 *out = spec + (size_t)row * p.Fs;
+        for (int k = threadIdx.x; k < p.Fu; k += kPairThreads) {
+            float2 X = make_float2(0.f, 0.f);
+            if (k <= M) {
+                const float2 a = Z[k == M ? 0 : k];
+                const float2 b = conjf2(Z[k == 0 ? 0 : M - k]);
+                const float2 wd = cmul(rtw_half<M>(TWH, c1, k), csub(a, b));
+                const float2 sm = cadd(a, b);
+                X = make_float2(0.5f * (sm.x + wd.y), 0.5f * (sm.y - wd.x));
+            }
+            out[k] = X;
+        }
+        if constexpr (kOdd) {
+            __syncthreads();                           // Z (in B) read before the next row writes B
+        } else {
+            release_to_copy();                         // Z (in A) read before the next copy into A
+            if (threadIdx.x == 0 && next < n_rows) {
+                mbar_arrive_expect_tx(bar, bytes);
+                bulk_g2s(A, in + (size_t)next * n_cols, bytes, bar);
+            }
+        }
+    }
+}
+
+template <int... Rs>
+__global__ void __launch_bounds__(kPairThreads, 2)
+k_row_c2r_pair(FFTPlan p, const float2 *__restrict__ spec, int n_rows, float *__restrict__ out, int n_cols,
+               int32_t *status) {
+    constexpr int M = (Rs * ...);
+    constexpr bool kOdd = (sizeof...(Rs) & 1) != 0;
+    extern __shared__ float4 sm4[];
+    const PairSmem L(sm4, M);
+    float2 *A = L.A, *B = L.B;
+    const float2 *TWH = L.TWH;
+    uint64_t *bar = L.bar;
+    const int Fu = p.Fu;                               // bins >= Fu are zero
+    const uint32_t bytes = (uint32_t)Fu * 8u;          // Fu <= M + 2
+    const float2 c1 = p.rtw[1];
+    pair_init<M>(p, L.TWH, bar);
+    __syncthreads();
+    int row = blockIdx.x;
+    if (threadIdx.x == 0 && row < n_rows) {
+        mbar_arrive_expect_tx(bar, bytes);
+        bulk_g2s(A, spec + (size_t)row * p.Fs, bytes, bar);
+    }
+    uint32_t parity = 0;
+    const float2 zero = make_float2(0.f, 0.f);
+    for (; row < n_rows; row += gridDim.x) {
+        if (!row_tma_wait(bar, parity, status)) return;
+        parity ^= 1u;
+        // Z[k] = E + i O, E = (X[k] + conj X[M-k]) / 2, O = exp(2 pi i k / P)(X[k] - conj X[M-k]) / 2,
+        // in place: one thread forms Z[k] and Z[M-k] from X[k] and X[M-k]; exp(-i pi (M-k) / M)
+        // = -conj exp(-i pi k / M)
+        for (int k = threadIdx.x; 2 * k <= M; k += kPairThreads) {
+            const int k2 = M - k;
+            const float2 xk = k < Fu ? A[k] : zero;
+            const float2 xm = k2 < Fu ? A[k2] : zero;
+            const float2 r = rtw_half<M>(TWH, c1, k);
+            {
+                const float2 a = xk, b = conjf2(xm);
+                const float2 O = cmul(conjf2(r), csub(a, b));
+                const float2 sm = cadd(a, b);
+                A[k] = make_float2(0.5f * (sm.x - O.y), 0.5f * (sm.y + O.x));
+            }
+            if (k > 0 && k2 != k) {
+                const float2 a = xm, b = conjf2(xk);
+                const float2 O = cmul(make_float2(-r.x, -r.y), csub(a, b));   // conj(-conj r) = -r
+                const float2 sm = cadd(a, b);
+                A[k2] = make_float2(0.5f * (sm.x - O.y), 0.5f * (sm.y + O.x));
+            }
+        }
+        __syncthreads();
+        const float2 *z = FftPair<M, kPairThreads, true, 1, Rs...>::run(A, A, B, TWH);
+        const int next = row + gridDim.x;
+        if constexpr (kOdd) {
+            release_to_copy();
+            if (threadIdx.x == 0 && next < n_rows) {
+                mbar_arrive_expect_tx(bar, bytes);
+                bulk_g2s(A, spec + (size_t)next * p.Fs, bytes, bar);
+            }
+        }
+        float *dst = out + (size_t)row * n_cols;
+        for (int n2 = threadIdx.x; 2 * n2 < n_cols; n2 += kPairThreads) reinterpret_cast<float2 *>(dst)[n2] = z[n2];
+        if constexpr (kOdd) {
+            __syncthreads();
+        } else {
+            release_to_copy();
+            if (threadIdx.x == 0 && next < n_rows) {
+                mbar_arrive_expect_tx(bar, bytes);
+                bulk_g2s(A, spec + (size_t)next * p.Fs, bytes, bar);
+            }
+        }
+    }
+}
+
 // ---- wire stage: 21-tap complex stencil across wires per frequency ----------------------
 constexpr int KW = WCT_MAX_RESPONSE_WIRES;   // 21
 constexpr int KC = KW / 2;                   // 10
@@ -832,11 +1058,20 @@ size_t device_smem_optin() {
     return (size_t)n;
 }
 
+size_t device_smem_per_sm() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess)
+        return 0;
+    return (size_t)n;
+}
+
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
 // Row-transform schedule: 0 = register-staged small CTAs (compiled lengths), 1 = persistent
-// bulk-copy CTAs.  Chosen by set_row_schedule (wct_sim_create's schedule_id).
-int g_row_schedule = 1;
+// bulk-copy CTAs, one per SM, 2 = persistent paired CTAs, two per SM (compiled lengths; else
+// 1).  Chosen by set_row_schedule (wct_sim_create's schedule_id).
+int g_row_schedule = 2;
 int row_kernel_choice() { return g_row_schedule; }
 
 // The persistent bulk-copy kernels need 16-byte aligned rows (n_cols % 4 == 0, dense rows)
@@ -911,6 +1146,38 @@ bool launch_row_rs(const FFTPlan &p, Launch &&launch, cudaError_t &err) {
     return false;
 }
 
+// Paired kernels for the compiled lengths (4900, 3125, 625); false if none applies.
+template <bool R2C, class Launch>
+bool launch_row_pair(const FFTPlan &p, Launch &&launch, cudaError_t &err) {
+    auto is = [&](std::initializer_list<int> rs) {
+        if ((int)rs.size() != p.n_stages) return false;
+        int k = 0;
+        for (int r : rs)
+            if (p.radix[k++] != r) return false;
+        return true;
+    };
+    const size_t smem = row_pair_smem_bytes(p.M);
+    if (2 * smem + 2048 > (size_t)device_smem_per_sm() || smem > (size_t)device_smem_optin()) return false;
+    auto go = [&](auto kern) {
+        err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err == cudaSuccess) {
+            launch(kern, smem);
+            err = cudaGetLastError();
+        }
+        return true;
+    };
+    if constexpr (R2C) {
+        if (is({7, 4, 5, 5, 7})) return go(k_row_r2c_pair<7, 4, 5, 5, 7>);
+        if (is({5, 5, 5, 5, 5})) return go(k_row_r2c_pair<5, 5, 5, 5, 5>);
+        if (is({5, 5, 5, 5})) return go(k_row_r2c_pair<5, 5, 5, 5>);
+    } else {
+        if (is({7, 4, 5, 5, 7})) return go(k_row_c2r_pair<7, 4, 5, 5, 7>);
+        if (is({5, 5, 5, 5, 5})) return go(k_row_c2r_pair<5, 5, 5, 5, 5>);
+        if (is({5, 5, 5, 5})) return go(k_row_c2r_pair<5, 5, 5, 5>);
+    }
+    return false;
+}
+
 }  // namespace
 
 cudaError_t launch_row_r2c(const FFTPlan &p, const float *in, int64_t in_stride, int n_in_cols, int n_rows,
@@ -920,6 +1187,14 @@ cudaError_t launch_row_r2c(const FFTPlan &p, const float *in, int64_t in_stride,
         cudaError_t err = cudaSuccess;
         if (launch_row_rs<true>(p, [&](auto kern, size_t smem) {
                 kern<<<n_rows, kRsThreads, smem, s>>>(p, in, n_in_cols, spec);
+            }, err))
+            return err;
+    }
+    if (row_kernel_choice() == 2 && use_row_tma(p, in_stride, n_in_cols, in) && aligned16(spec) && 2 * p.M >= n_in_cols) {
+        cudaError_t err = cudaSuccess;
+        const int grid = std::min(n_rows, 2 * device_sms());
+        if (launch_row_pair<true>(p, [&](auto kern, size_t smem) {
+                kern<<<grid, kPairThreads, smem, s>>>(p, in, n_rows, n_in_cols, spec, status);
             }, err))
             return err;
     }
@@ -946,6 +1221,15 @@ cudaError_t launch_row_c2r(const FFTPlan &p, const float2 *spec, int n_rows, flo
         cudaError_t err = cudaSuccess;
         if (launch_row_rs<false>(p, [&](auto kern, size_t smem) {
                 kern<<<n_rows, kRsThreads, smem, s>>>(p, spec, out, n_out_cols);
+            }, err))
+            return err;
+    }
+    if (row_kernel_choice() == 2 && use_row_tma(p, out_stride, n_out_cols, out) && aligned16(spec) &&
+        2 * p.M >= n_out_cols) {
+        cudaError_t err = cudaSuccess;
+        const int grid = std::min(n_rows, 2 * device_sms());
+        if (launch_row_pair<false>(p, [&](auto kern, size_t smem) {
+                kern<<<grid, kPairThreads, smem, s>>>(p, spec, n_rows, out, n_out_cols, status);
             }, err))
             return err;
     }

@@ -434,10 +434,11 @@ wct_status_t wct_sim_create(const wct_plane_t *planes, int n_planes, const wct_r
         s->opts.schedule_id = -1;
         s->opts.deterministic = 0;
     }
-    // schedule_id: -1 default; otherwise bit 0 = row transforms (0 register-staged, 1 persistent
-    // bulk-copy), bit 1 = rasterize (0 warp-level chunks, 1 CTA-level chunks)
+    // schedule_id: -1 default; otherwise bits 0 and 2 = row transforms (0 register-staged,
+    // 1 persistent bulk-copy, 4 persistent paired), bit 1 = rasterize (0 warp-level chunks,
+    // 1 CTA-level chunks)
     if (s->opts.schedule_id >= 0) {
-        set_row_schedule(s->opts.schedule_id & 1);
+        set_row_schedule((s->opts.schedule_id & 4) ? 2 : (s->opts.schedule_id & 1));
         set_raster_schedule((s->opts.schedule_id >> 1) & 1);
     }
     wct_status_t st = WCT_OK;

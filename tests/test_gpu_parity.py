@@ -119,6 +119,25 @@ def test_convolve_random_grid(shape, kind):
         assert info["spectrum_bins_used"] < 0.6 * info["spectrum_bins"]
 
 
+@pytest.mark.parametrize("nt", [9600, 6000, 1024, 1200])
+def test_convolve_every_row_schedule(nt):
+    # schedule_id 0: register-staged rows, 1: one persistent CTA per SM, 4: two per SM; 700 rows
+    # so every persistent CTA streams several rows.  9600 / 6000 / 1024 ticks have compiled
+    # plans (odd and even stage counts), 1200 the runtime-radix path.
+    pl = synth.Plane(700, nt)
+    resp = synth.make_response("bipolar")
+    g = np.random.default_rng(nt).normal(size=(700, nt)).astype(np.float32)
+    ref = oracle.convolve_fft(g, resp, workers=4)
+    try:
+        for sched in (0, 1, 4):
+            sim = make_sim([pl], [resp], synth.Diffusion(), schedule_id=sched)
+            out = sim.convolve(0, torch.from_numpy(g).cuda())
+            sim.sync()
+            assert rel_l2(to_np(out), ref) <= WAVE_RTOL, sched
+    finally:
+        make_sim([pl], [resp], synth.Diffusion(), schedule_id=4)       # back to the defaults
+
+
 def test_convolve_small_response_and_in_place():
     pl = synth.Plane(64, 500)
     resp = np.random.default_rng(3).normal(size=(5, 37)).astype(np.float32)
