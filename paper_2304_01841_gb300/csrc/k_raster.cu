@@ -341,8 +341,8 @@ __device__ __forceinline__ void raster_chunk(ChunkSmem &S, const float *__restri
 constexpr int kWarpDepos = 8;
 constexpr int kWarpsPerCta = 4;
 constexpr int kWItemCap = 384;
-constexpr int kWWCap = 640;        // >= 128 + 512, the weights of the largest window
-constexpr int kWBoxCap = 320;
+constexpr int kWWCap = 648;        // >= 129 + 513, the bin edges of the largest window
+constexpr int kWBoxCap = 304;
 
 struct WarpSmem {
     DepoDesc d[kWarpDepos];
@@ -354,11 +354,11 @@ struct WarpSmem {
     float nrm_p[kWarpDepos];
     float sum[kWarpDepos];
     int pass_end, use_box, box_w0, box_t0, box_nw, box_nt;
-    float w[kWWCap];
+    float w[kWWCap];           // per depo: nt + 1 tick edges, then np + 1 impact edges
     float val[kWItemCap];
     float box[kWBoxCap];
     int tgt[kWItemCap];        // box or grid index of each cached item, -1 off the grid
-    uint8_t slot[kWItemCap];
+    uint8_t slot[kWWCap];      // depo of each edge, then of each cached item
 };
 
 __device__ __forceinline__ void raster_warp(WarpSmem &S, const float *__restrict__ t0, const float *__restrict__ x,
@@ -383,8 +383,6 @@ __device__ __forceinline__ void raster_warp(WarpSmem &S, const float *__restrict
         }
         S.wl[lane] = wl;
         S.nw[lane] = nw;
-        S.nrm_t[lane] = d.inv_t == 0.f ? 1.f : 1.f / (erff(((float)d.nt - d.mu_t) * d.inv_t) - erff(-d.mu_t * d.inv_t));
-        S.nrm_p[lane] = d.inv_p == 0.f ? 1.f : 1.f / (erff(((float)d.np - d.mu_p) * d.inv_p) - erff(-d.mu_p * d.inv_p));
         S.sum[lane] = 0.f;
     }
     __syncwarp();
@@ -394,7 +392,7 @@ __device__ __forceinline__ void raster_warp(WarpSmem &S, const float *__restrict
             int w0 = INT_MAX, w1 = INT_MIN, t0b = INT_MAX, t1b = INT_MIN;
             for (; e < cn; ++e) {
                 const DepoDesc &d = S.d[e];
-                const int ni = (int)d.nt * S.nw[e], nwt = (int)d.nt + (int)d.np;
+                const int ni = (int)d.nt * S.nw[e], nwt = d.nt > 0 ? (int)d.nt + (int)d.np + 2 : 0;
                 if (e > s && (it + ni > kWItemCap || ww + nwt > kWWCap)) break;
                 S.item_off[e] = it;
                 S.w_off[e] = ww;
@@ -430,22 +428,55 @@ __device__ __forceinline__ void raster_warp(WarpSmem &S, const float *__restrict
         const int bnt = S.box_nt, bw0 = S.box_w0, bt0 = S.box_t0;
         if (use_box)
             for (int k = lane; k < S.box_nw * bnt; k += 32) S.box[k] = 0.f;
+        // depo of every edge (a table instead of a search)
+        for (int j = s; j < e; ++j)
+            for (int k = S.w_off[j] - w_base + lane; k < S.w_off[j + 1] - w_base; k += 32) S.slot[k] = (uint8_t)j;
+        __syncwarp();
+        // bin edges erf((i - mu) * inv), i = 0..n, per axis (a point charge: edges 0, 1)
         for (int k = lane; k < n_w; k += 32) {
-            const int j = find_slot(S.w_off, s, e, w_base + k);
+            const int j = S.slot[k];
             const DepoDesc &d = S.d[j];
             const int r = w_base + k - S.w_off[j];
-            float w;
-            if (r < d.nt) {
-                w = d.inv_t == 0.f ? 1.f
-                                   : (erff(((float)(r + 1) - d.mu_t) * d.inv_t) - erff(((float)r - d.mu_t) * d.inv_t)) *
-                                         S.nrm_t[j];
-            } else {
-                const int rr = r - d.nt;
-                w = d.inv_p == 0.f ? 1.f
-                                   : (erff(((float)(rr + 1) - d.mu_p) * d.inv_p) - erff(((float)rr - d.mu_p) * d.inv_p)) *
-                                         S.nrm_p[j];
+            float E;
+            if (r <= d.nt) E = d.inv_t == 0.f ? (r == 0 ? 0.f : 1.f) : erff(((float)r - d.mu_t) * d.inv_t);
+            else {
+                const int rr = r - d.nt - 1;
+                E = d.inv_p == 0.f ? (rr == 0 ? 0.f : 1.f) : erff(((float)rr - d.mu_p) * d.inv_p);
             }
-            S.w[k] = w;
+            S.w[k] = E;
+        }
+        __syncwarp();
+        if (lane < e - s && S.d[s + lane].nt > 0) {
+            const int j = s + lane;
+            const DepoDesc &d = S.d[j];
+            const float *E = S.w + (S.w_off[j] - w_base);
+            S.nrm_t[j] = 1.f / (E[d.nt] - E[0]);
+            S.nrm_p[j] = 1.f / (E[d.nt + 1 + d.np] - E[d.nt + 1]);
+        }
+        __syncwarp();
+        // weights (E[i + 1] - E[i]) * nrm in place of E[i]: tick weights at [0, nt), impact
+        // weights at [nt + 1, nt + 1 + np) of each depo's block
+        for (int base = 0; base < n_w; base += 32) {
+            const int k = base + lane;
+            float v = 0.f;
+            bool wr = false;
+            if (k < n_w) {
+                const int j = S.slot[k];
+                const int nt = S.d[j].nt;
+                const int r = w_base + k - S.w_off[j];
+                if (r != nt && r != nt + 1 + S.d[j].np) {
+                    v = (S.w[k + 1] - S.w[k]) * (r < nt ? S.nrm_t[j] : S.nrm_p[j]);
+                    wr = true;
+                }
+            }
+            __syncwarp();
+            if (wr) S.w[k] = v;
+            __syncwarp();
+        }
+        // depo of every cached item
+        for (int j = s; j < e; ++j) {
+            const int i1 = min(S.item_off[j + 1] - i_base, kWItemCap);
+            for (int k = S.item_off[j] - i_base + lane; k < i1; k += 32) S.slot[k] = (uint8_t)j;
         }
         __syncwarp();
         for (int base = 0; base < n_items; base += 32) {
@@ -453,15 +484,14 @@ __device__ __forceinline__ void raster_warp(WarpSmem &S, const float *__restrict
             int j = -1;
             float v = 0.f;
             if (k < n_items) {
-                j = find_slot(S.item_off, s, e, i_base + k);
+                j = k < kWItemCap ? S.slot[k] : find_slot(S.item_off, s, e, i_base + k);
                 const DepoDesc &d = S.d[j];
                 const Item f = make_item(i_base + k - S.item_off[j], S.nw[j], S.wl[j], d, pp.n_imp);
                 const float *wt = S.w + (S.w_off[j] - w_base);
-                const float *wp = wt + d.nt;
+                const float *wp = wt + d.nt + 1;
                 v = pp.fluctuate ? fold_fluct(f, wt, wp, d.q, (uint32_t)(c0 + j), pp, c3, RK) : fold_plain(f, wt, wp, d.q);
                 if (k < kWItemCap) {
                     S.val[k] = v;
-                    S.slot[k] = (uint8_t)j;
                     const bool in = f.wire >= 0 && f.wire < pp.n_wires && f.tick >= 0 && f.tick < pp.n_ticks;
                     S.tgt[k] = !in ? -1 : (use_box ? (f.wire - bw0) * bnt + (f.tick - bt0) : f.wire * pp.n_ticks + f.tick);
                 }
@@ -484,7 +514,7 @@ __device__ __forceinline__ void raster_warp(WarpSmem &S, const float *__restrict
                     const DepoDesc &d = S.d[j];
                     const Item f = make_item(i_base + k - S.item_off[j], S.nw[j], S.wl[j], d, pp.n_imp);
                     const float *wt = S.w + (S.w_off[j] - w_base);
-                    v = fold_plain(f, wt, wt + d.nt, d.q);
+                    v = fold_plain(f, wt, wt + d.nt + 1, d.q);
                 }
             }
             if (use_box) atomicAdd(&S.box[t], v);
@@ -497,12 +527,12 @@ __device__ __forceinline__ void raster_warp(WarpSmem &S, const float *__restrict
             const Item f = make_item(i_base + k - S.item_off[j], S.nw[j], S.wl[j], d, pp.n_imp);
             if (f.wire < 0 || f.wire >= pp.n_wires || f.tick < 0 || f.tick >= pp.n_ticks) continue;
             const float *wt = S.w + (S.w_off[j] - w_base);
-            float v = pp.fluctuate ? fold_fluct(f, wt, wt + d.nt, d.q, (uint32_t)(c0 + j), pp, c3, RK)
-                                   : fold_plain(f, wt, wt + d.nt, d.q);
+            float v = pp.fluctuate ? fold_fluct(f, wt, wt + d.nt + 1, d.q, (uint32_t)(c0 + j), pp, c3, RK)
+                                   : fold_plain(f, wt, wt + d.nt + 1, d.q);
             if (pp.fluctuate) {
                 const float sm = S.sum[j];
                 if (sm > 0.f) v *= d.q / sm;
-                else v = fold_plain(f, wt, wt + d.nt, d.q);
+                else v = fold_plain(f, wt, wt + d.nt + 1, d.q);
             }
             if (use_box) atomicAdd(&S.box[(f.wire - bw0) * bnt + (f.tick - bt0)], v);
             else atomicAdd(&grid[(int64_t)f.wire * pp.n_ticks + f.tick], v);
