@@ -422,8 +422,8 @@ def main():
     dom = max(kern, key=kern.get)
     cnt = kernel_counters()
     valid = cnt.get("csrc_digest") == csrc_digest()
-    kname = {"raster_scatter": "k_raster_warps", "row_r2c": "k_row_r2c_tma", "wire_stage": "k_wire_stage_tma",
-             "row_c2r": "k_row_c2r_tma"}
+    kname = {"raster_scatter": "k_raster_warps", "row_r2c": "k_row_r2c_pair", "wire_stage": "k_wire_stage_tma",
+             "row_c2r": "k_row_c2r_pair"}
     stage_report = {}
     for k, us in list(kern.items()) + [("grid_clear", stages["prep_binning"])]:
         if k == "raster_scatter":
