@@ -184,6 +184,33 @@ wct_status_t wct_sim_run_event(wct_sim_t *sim, const wct_depos_t *depos, float *
 wct_status_t wct_sim_run_batch(wct_sim_t *sim, const wct_depos_t *events, int n_events,
                                float *const *waveforms, void *stream);
 
+/*
+ * One event's depos in HOST memory (same fields and units as wct_depos_t).  Pinned
+ * (page-locked) arrays let the uploads overlap device work; pageable arrays work too.
+ */
+typedef struct {
+    const float *t0_us;
+    const float *x_mm;
+    const float *y_mm;
+    const float *z_mm;
+    const float *q_e;
+    int64_t n;
+    uint64_t event_id;
+} wct_host_depos_t;
+
+/* The whole DepoTransform (§2) for n_events events from host memory to host memory.
+ * events: HOST array of n_events host-depo descriptors; waveforms: HOST array of
+ * n_events * n_planes HOST pointers (event-major), each receiving float32 [n_wires][n_ticks]
+ * (pinned memory lets the downloads run at full link speed).  Pipelined on three library
+ * streams with double-buffered device staging owned by the library (2 x the waveforms of
+ * every plane + 2 x the depos of the largest event, counted against the HBM budget): the
+ * upload of event e + 1 and the download of event e - 1 overlap the kernels of event e.
+ * Synchronous: returns when every waveform is in host memory, with the status of
+ * wct_sim_sync (WCT_EINVAL if invalid depos were skipped).  Results equal those of
+ * wct_sim_run_event for each event.  WCT_EINVAL for a NULL or negative argument. */
+wct_status_t wct_sim_run_host(wct_sim_t *sim, const wct_host_depos_t *events, int n_events,
+                              float *const *waveforms);
+
 /* Synchronise `stream` and return (then clear) the device status word: WCT_OK, or the
  * first device-side error since the last sync (WCT_EINVAL for invalid depos). */
 wct_status_t wct_sim_sync(wct_sim_t *sim, void *stream);

@@ -170,6 +170,48 @@ class Simulator:
         self._check(self._lib.wct_sim_run_batch(self._h, evs, len(events), arr, _stream_handle(stream)))
         return wfs
 
+    def run_host(self, events: Sequence, outs: Optional[List[List]] = None) -> List[List]:
+        """wct_sim_run_host: events whose depos are in host memory (objects with t0, x, y, z, q
+        float32 arrays -- numpy arrays or CPU tensors, pinned for overlapped uploads -- and
+        event_id) to waveforms in host memory.  outs: [event][plane] host float32 tensors or
+        arrays [n_wires, n_ticks] (pinned tensors download at full speed); allocated pinned when
+        None.  Synchronous; returns outs."""
+        import torch
+        npl = len(self.planes)
+        if outs is None:
+            outs = [[torch.empty((p.n_wires, p.n_ticks), dtype=torch.float32, pin_memory=True) for p in self.planes]
+                    for _ in events]
+        keep = []
+
+        def host_ptr(a, shape=None):
+            if isinstance(a, torch.Tensor):
+                if a.is_cuda or a.dtype != torch.float32 or not a.is_contiguous():
+                    raise ValueError("host arrays must be contiguous float32 CPU tensors")
+                t = a
+            else:
+                t = np.ascontiguousarray(a, dtype=np.float32)
+                if shape is not None and (t is not a or t.shape != shape or not t.flags.writeable):
+                    raise ValueError("waveform arrays must be writable contiguous float32 [n_wires, n_ticks]")
+            keep.append(t)
+            return t.data_ptr() if isinstance(t, torch.Tensor) else t.ctypes.data
+
+        hev = (_abi.wct_host_depos_t * max(len(events), 1))()
+        for i, e in enumerate(events):
+            ptrs = [host_ptr(getattr(e, k)) for k in ("t0", "x", "y", "z", "q")]
+            n = len(e.t0)
+            hev[i] = _abi.wct_host_depos_t(*ptrs, n, int(e.event_id) & 0xFFFFFFFFFFFFFFFF)
+        wf = []
+        for i in range(len(events)):
+            for p, pl in enumerate(self.planes):
+                o = outs[i][p]
+                if isinstance(o, torch.Tensor) and tuple(o.shape) != (pl.n_wires, pl.n_ticks):
+                    raise ValueError("waveform tensors must be [n_wires, n_ticks]")
+                wf.append(host_ptr(o, (pl.n_wires, pl.n_ticks)))
+        arr = (ctypes.c_void_p * max(len(wf), 1))(*wf)
+        self._check(self._lib.wct_sim_run_host(self._h, hev, len(events), arr))
+        del keep
+        return outs
+
     def sync(self, stream=None):
         """wct_sim_sync: wait for the stream and raise on a device-side error."""
         self._check(self._lib.wct_sim_sync(self._h, _stream_handle(stream)))

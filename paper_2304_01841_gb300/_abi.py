@@ -46,6 +46,11 @@ class wct_depos_t(ctypes.Structure):
                 ("n", c_i64), ("event_id", c_u64)]
 
 
+class wct_host_depos_t(ctypes.Structure):
+    _fields_ = [("t0_us", c_vp), ("x_mm", c_vp), ("y_mm", c_vp), ("z_mm", c_vp), ("q_e", c_vp),
+                ("n", c_i64), ("event_id", c_u64)]
+
+
 EXPORTS = {
     "wct_sim_create": ([ctypes.POINTER(wct_plane_t), ctypes.c_int, ctypes.POINTER(wct_response_t),
                         ctypes.POINTER(wct_diffusion_t), ctypes.POINTER(wct_opts_t), ctypes.POINTER(c_vp)],
@@ -58,6 +63,7 @@ EXPORTS = {
     "wct_sim_run_event": ([c_vp, ctypes.POINTER(wct_depos_t), ctypes.POINTER(c_vp), c_vp], ctypes.c_int),
     "wct_sim_run_batch": ([c_vp, ctypes.POINTER(wct_depos_t), ctypes.c_int, ctypes.POINTER(c_vp), c_vp],
                           ctypes.c_int),
+    "wct_sim_run_host": ([c_vp, ctypes.POINTER(wct_host_depos_t), ctypes.c_int, ctypes.POINTER(c_vp)], ctypes.c_int),
     "wct_sim_sync": ([c_vp, c_vp], ctypes.c_int),
     "wct_sim_plane_info": ([c_vp, ctypes.c_int, ctypes.POINTER(c_i64)], ctypes.c_int),
     "wct_sim_set_timing": ([c_vp, ctypes.c_int], ctypes.c_int),

@@ -76,6 +76,12 @@ struct wct_sim {
     std::vector<Graph> graphs;
     std::vector<std::vector<uint64_t>> seen;   // recent batch keys not (yet) recorded
     int64_t graph_launches = 0;
+    // run_host: upload / compute / download streams, double-buffered device staging
+    cudaStream_t up_stream = nullptr, comp_stream = nullptr, down_stream = nullptr;
+    cudaEvent_t ev_up[2] = {}, ev_comp[2] = {}, ev_down[2] = {};
+    float *h_depo[2] = {};                  // 5 arrays of h_cap floats each
+    int64_t h_cap = 0;
+    float *h_wave[2][kMaxPlanes] = {};
 };
 
 namespace {
@@ -591,6 +597,11 @@ wct_status_t wct_sim_destroy(wct_sim_t *s) {
     if (s->cv_stream) cudaStreamDestroy(s->cv_stream);
     for (auto &e : s->bev)
         if (e) cudaEventDestroy(e);
+    for (cudaStream_t h : {s->up_stream, s->comp_stream, s->down_stream})
+        if (h) cudaStreamDestroy(h);
+    for (int b = 0; b < 2; ++b)
+        for (cudaEvent_t h : {s->ev_up[b], s->ev_comp[b], s->ev_down[b]})
+            if (h) cudaEventDestroy(h);
     delete s;
     return WCT_OK;
 }
@@ -845,6 +856,86 @@ wct_status_t wct_sim_run_batch(wct_sim_t *s, const wct_depos_t *events, int n_ev
     ++s->graph_launches;
     s->launches += recorded;
     return WCT_OK;
+}
+
+wct_status_t wct_sim_run_host(wct_sim_t *s, const wct_host_depos_t *events, int n_events, float *const *wfs) {
+    if (!s || n_events < 0) return WCT_EINVAL;
+    if (n_events == 0) return WCT_OK;
+    if (!events || !wfs) return fail(s, WCT_EINVAL, "events or waveforms is NULL");
+    const int npl = s->n_planes;
+    int64_t max_n = 1;
+    for (int e = 0; e < n_events; ++e) {
+        const wct_host_depos_t &h = events[e];
+        if (h.n < 0 || h.n > ((int64_t)1 << 30)) return fail(s, WCT_EINVAL, "bad depo count");
+        if (h.n > 0 && (!h.t0_us || !h.x_mm || !h.y_mm || !h.z_mm || !h.q_e))
+            return fail(s, WCT_EINVAL, "a depo array pointer is NULL");
+        for (int p = 0; p < npl; ++p)
+            if (!wfs[(size_t)e * npl + p]) return fail(s, WCT_EINVAL, "a waveform pointer is NULL");
+        max_n = std::max(max_n, h.n);
+    }
+    cudaError_t err = cudaSuccess;
+    if (!s->up_stream) {
+        for (cudaStream_t *h : {&s->up_stream, &s->comp_stream, &s->down_stream})
+            if (err == cudaSuccess) err = cudaStreamCreateWithFlags(h, cudaStreamNonBlocking);
+        for (int b = 0; b < 2 && err == cudaSuccess; ++b)
+            for (cudaEvent_t *h : {&s->ev_up[b], &s->ev_comp[b], &s->ev_down[b]})
+                if (err == cudaSuccess) err = cudaEventCreateWithFlags(h, cudaEventDisableTiming);
+        if (err != cudaSuccess) return cuda_fail(s, err, "host pipeline streams");
+    }
+    wct_status_t st = WCT_OK;
+    if (!s->h_wave[0][0]) {
+        for (int b = 0; b < 2 && st == WCT_OK; ++b)
+            for (int p = 0; p < npl && st == WCT_OK; ++p)
+                st = dev_alloc(s, (void **)&s->h_wave[b][p],
+                               sizeof(float) * (size_t)s->planes[p].g.n_wires * s->planes[p].g.n_ticks);
+        if (st) return st;
+    }
+    if (max_n > s->h_cap) {
+        // earlier calls returned only after their streams drained: the old staging is idle
+        for (int b = 0; b < 2; ++b) {
+            dev_free(s, s->h_depo[b], sizeof(float) * 5 * (size_t)s->h_cap);
+            s->h_depo[b] = nullptr;
+        }
+        s->h_cap = 0;
+        for (int b = 0; b < 2 && st == WCT_OK; ++b) st = dev_alloc(s, (void **)&s->h_depo[b], sizeof(float) * 5 * (size_t)max_n);
+        if (st) return st;
+        s->h_cap = max_n;
+    }
+    cudaStream_t up = s->up_stream, comp = s->comp_stream, down = s->down_stream;
+    for (int e = 0; e < n_events && st == WCT_OK && err == cudaSuccess; ++e) {
+        const int b = e & 1;
+        const wct_host_depos_t &h = events[e];
+        float *db = s->h_depo[b];
+        const int64_t cap = s->h_cap;
+        wct_depos_t d{db, db + cap, db + 2 * cap, db + 3 * cap, db + 4 * cap, h.n, h.event_id};
+        // upload once the compute of event e - 2 has released this staging buffer
+        if (e >= 2) err = cudaStreamWaitEvent(up, s->ev_comp[b], 0);
+        const float *src[5] = {h.t0_us, h.x_mm, h.y_mm, h.z_mm, h.q_e};
+        for (int a = 0; a < 5 && err == cudaSuccess && h.n > 0; ++a)
+            err = cudaMemcpyAsync(db + a * cap, src[a], sizeof(float) * (size_t)h.n, cudaMemcpyHostToDevice, up);
+        if (err == cudaSuccess) err = cudaEventRecord(s->ev_up[b], up);
+        // compute once the upload landed and the download of event e - 2 freed the waveforms
+        if (err == cudaSuccess) err = cudaStreamWaitEvent(comp, s->ev_up[b], 0);
+        if (err == cudaSuccess && e >= 2) err = cudaStreamWaitEvent(comp, s->ev_down[b], 0);
+        if (err != cudaSuccess) break;
+        st = wct_sim_run_event(s, &d, s->h_wave[b], comp);
+        if (st) break;
+        err = cudaEventRecord(s->ev_comp[b], comp);
+        if (err == cudaSuccess) err = cudaStreamWaitEvent(down, s->ev_comp[b], 0);
+        for (int p = 0; p < npl && err == cudaSuccess; ++p)
+            err = cudaMemcpyAsync(wfs[(size_t)e * npl + p], s->h_wave[b][p],
+                                  sizeof(float) * (size_t)s->planes[p].g.n_wires * s->planes[p].g.n_ticks,
+                                  cudaMemcpyDeviceToHost, down);
+        if (err == cudaSuccess) err = cudaEventRecord(s->ev_down[b], down);
+    }
+    // drain every stream before returning (also after an error: nothing may still use the staging)
+    for (cudaStream_t h : {up, comp, down}) {
+        const cudaError_t e2 = cudaStreamSynchronize(h);
+        if (err == cudaSuccess) err = e2;
+    }
+    if (st) return st;
+    if (err != cudaSuccess) return cuda_fail(s, err, "host pipeline");
+    return wct_sim_sync(s, comp);
 }
 
 wct_status_t wct_sim_sync(wct_sim_t *s, void *stream) {

@@ -111,3 +111,40 @@ def test_server_respects_hbm_budget():
     assert 0 < peak <= 2 * one
     assert len(srv.completed) == len(evs)
     srv.close()
+
+
+def test_run_host_matches_run_event():
+    # host depos -> host waveforms through the pipelined entry point: pinned tensors and plain
+    # numpy inputs, an empty event, more events than staging buffers, then a larger event that
+    # grows the staging
+    import paper_2304_01841_gb300 as g
+    planes, responses = _small_three_plane()
+    diff = synth.Diffusion(fluctuate=True, seed=11)
+    sim = make_sim(planes, responses, diff)
+    evs = _events(5, seed=7, lo=100, hi=3000, id0=900)
+    evs.append(synth.Depos(*(np.zeros(0, np.float32) for _ in range(5))))
+    evs[-1].event_id = 950
+    pinned = []
+    for i, e in enumerate(evs):
+        if i % 2 == 0:
+            o = type("P", (), {})()
+            for k in ("t0", "x", "y", "z", "q"):
+                setattr(o, k, torch.from_numpy(np.ascontiguousarray(getattr(e, k), dtype=np.float32)).pin_memory())
+            o.event_id = e.event_id
+            pinned.append(o)
+        else:
+            pinned.append(e)
+    outs = sim.run_host(pinned)
+    for e, ev in enumerate(evs):
+        want = [to_np(w) for w in sim.run_event(g.DeviceDepos.from_host(ev))]
+        sim.sync()
+        for p in range(len(planes)):
+            got = outs[e][p].numpy()
+            assert _close(got, want[p], np.abs(want[p]).max()), (e, p)
+    big = _events(1, seed=8, lo=20000, hi=20001, id0=990)
+    out_np = [[np.empty((p.n_wires, p.n_ticks), np.float32) for p in planes]]
+    sim.run_host(big, outs=out_np)
+    want = [to_np(w) for w in sim.run_event(g.DeviceDepos.from_host(big[0]))]
+    sim.sync()
+    for p in range(len(planes)):
+        assert _close(out_np[0][p], want[p], np.abs(want[p]).max())
