@@ -892,6 +892,11 @@ k_wire_stage(const float2 *__restrict__ S, const float2 *__restrict__ Rt, int Fs
     }
 }
 
+// the tile clearing for the fallback wire stage, which does not take it as a side job
+__global__ void __launch_bounds__(256) k_clear_tiles_fft(const ClearJob job) {
+    clear_listed_tiles(job, blockIdx.x, gridDim.x, 256);
+}
+
 // ---- wire stage fed by bulk copies -------------------------------------------------------
 // CTA = kStageFB consecutive frequencies x a run of wires_per_cta output wires.  A producer
 // warp streams the input rows' frequency slices (kStageFB complex = 1 KB each) into a ring of
@@ -906,7 +911,7 @@ constexpr int kRingGroups = 4;
 
 __global__ void __launch_bounds__(kStageFB + 32)
 k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, int Fs, int Fu, int n_wires,
-                 int wires_per_cta, float2 *__restrict__ T, int32_t *status) {
+                 int wires_per_cta, float2 *__restrict__ T, int32_t *status, const ClearJob clear) {
     __shared__ __align__(16) float2 ring[kRingGroups * kGroupRows][kStageFB];
     __shared__ uint64_t full[kRingGroups], empty[kRingGroups];
     const int tid = threadIdx.x;
@@ -947,6 +952,10 @@ k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, in
         }
         return;
     }
+    // side job: clear this CTA's share of the grid tiles listed by the rasterizer (the grid
+    // was read by the forward transform before this launch); consumers only
+    if (clear.grid)
+        clear_listed_tiles(clear, blockIdx.y * gridDim.x + blockIdx.x, gridDim.x * gridDim.y, kStageFB);
     const int f = f0 + tid;
     const bool live = tid < nf;
     // Pull form in blocks of kOutBlock outputs: the window holds input rows b .. b+kOutBlock+19,
@@ -1249,8 +1258,9 @@ cudaError_t launch_row_c2r(const FFTPlan &p, const float2 *spec, int n_rows, flo
 }
 
 cudaError_t launch_wire_stage(const FFTPlan &p, const float2 *spec, const float2 *resp_spec, int n_wires, float2 *out,
-                              cudaStream_t s, int32_t *status) {
+                              cudaStream_t s, int32_t *status, const ClearJob *clear) {
     if (n_wires <= 0) return cudaSuccess;
+    const ClearJob job = clear ? *clear : ClearJob{};
     if (aligned16(spec) && (p.Fs % 2) == 0 && (p.Fu % 2) == 0) {
         // fewer wires per CTA when the frequency blocks alone leave the SMs short of CTAs
         // (about six resident per SM hide the ring's latency); each CTA re-reads 20 halo rows
@@ -1258,12 +1268,17 @@ cudaError_t launch_wire_stage(const FFTPlan &p, const float2 *spec, const float2
         int wpc = kStageWiresMax;
         while (wpc > 32 && (int64_t)fb * ((n_wires + wpc - 1) / wpc) < 6 * 152) wpc /= 2;
         dim3 grid(fb, (n_wires + wpc - 1) / wpc);
-        k_wire_stage_tma<<<grid, kStageFB + 32, 0, s>>>(spec, resp_spec, p.Fs, p.Fu, n_wires, wpc, out, status);
+        k_wire_stage_tma<<<grid, kStageFB + 32, 0, s>>>(spec, resp_spec, p.Fs, p.Fu, n_wires, wpc, out, status, job);
         return cudaGetLastError();
     }
     dim3 grid((p.Fu + kStageThreads - 1) / kStageThreads, (n_wires + kStageRun - 1) / kStageRun);
     k_wire_stage<<<grid, kStageThreads, 0, s>>>(spec, resp_spec, p.Fs, p.Fu, n_wires, out);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && job.grid) {
+        k_clear_tiles_fft<<<job.n_tiles < 2 * 152 ? job.n_tiles : 2 * 152, 256, 0, s>>>(job);
+        e = cudaGetLastError();
+    }
+    return e;
 }
 
 void set_row_schedule(int schedule) { g_row_schedule = schedule; }

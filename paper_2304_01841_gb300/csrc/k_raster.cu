@@ -121,6 +121,25 @@ __device__ __forceinline__ float fold_fluct(const Item &f, const float *wt, cons
     return acc;
 }
 
+// Flag the grid tiles that depo d's window overlaps (clamped to the grid).  flags holds
+// n_tiles flags, then a counter and a done-counter, then the list of flagged tiles: the
+// first depo to flag a tile appends it to the list.
+__device__ __forceinline__ void mark_tiles(uint32_t *flags, const PlaneParams &pp, const DepoDesc &d, int wl, int nw) {
+    if (!flags || d.nt == 0) return;
+    const int a0 = max(wl, 0), a1 = min(wl + nw - 1, pp.n_wires - 1);
+    const int b0 = max(d.lo_t, 0), b1 = min(d.lo_t + (int)d.nt - 1, pp.n_ticks - 1);
+    if (a0 > a1 || b0 > b1) return;
+    const int n_tiles = pp.n_tiles_w * pp.n_tiles_t;
+    for (int tw = a0 / pp.tile_w; tw <= a1 / pp.tile_w; ++tw)
+        for (int tt = b0 / pp.tile_t; tt <= b1 / pp.tile_t; ++tt) {
+            const int t = tw * pp.n_tiles_t + tt;
+            if (flags[t] == 0u && atomicExch(&flags[t], 1u) == 0u) {
+                const uint32_t slot = atomicAdd(&flags[n_tiles], 1u);
+                flags[n_tiles + 2 + slot] = (uint32_t)t;
+            }
+        }
+}
+
 __device__ __forceinline__ uint32_t counter_c3(const PlaneParams &pp, uint32_t event_lo) {
     return ((uint32_t)pp.plane_index << 24) | (event_lo & 0xFFFFFFu);
 }
@@ -190,7 +209,7 @@ __device__ __forceinline__ void raster_chunk(ChunkSmem &S, const float *__restri
                                              const float *__restrict__ y, const float *__restrict__ z,
                                              const float *__restrict__ q, int64_t n, const PlaneParams &pp,
                                              uint32_t event_lo, float *__restrict__ grid, int32_t *status,
-                                             int64_t chunk, const uint32_t (&RK)[20]) {
+                                             int64_t chunk, const uint32_t (&RK)[20], uint32_t *flags) {
     const int tid = threadIdx.x, lane = tid & 31;
     const int64_t c0 = chunk * kChunk;
     const int cn = (int)((n - c0) < kChunk ? (n - c0) : kChunk);
@@ -208,6 +227,7 @@ __device__ __forceinline__ void raster_chunk(ChunkSmem &S, const float *__restri
         }
         S.wl[tid] = wl;
         S.nw[tid] = nw;
+        mark_tiles(flags, pp, d, wl, nw);
         // sum of a window's unnormalised weights telescopes to (erf(x_n) - erf(x_0)) / 2
         S.nrm_t[tid] = d.inv_t == 0.f ? 1.f : 1.f / (erff(((float)d.nt - d.mu_t) * d.inv_t) - erff(-d.mu_t * d.inv_t));
         S.nrm_p[tid] = d.inv_p == 0.f ? 1.f : 1.f / (erff(((float)d.np - d.mu_p) * d.inv_p) - erff(-d.mu_p * d.inv_p));
@@ -365,7 +385,7 @@ __device__ __forceinline__ void raster_warp(WarpSmem &S, const float *__restrict
                                             const float *__restrict__ y, const float *__restrict__ z,
                                             const float *__restrict__ q, int64_t n, const PlaneParams &pp,
                                             uint32_t event_lo, float *__restrict__ grid, int32_t *status,
-                                            int64_t chunk, const uint32_t (&RK)[20]) {
+                                            int64_t chunk, const uint32_t (&RK)[20], uint32_t *flags) {
     const int lane = threadIdx.x & 31;
     const int64_t c0 = chunk * kWarpDepos;
     if (c0 >= n) return;
@@ -383,6 +403,7 @@ __device__ __forceinline__ void raster_warp(WarpSmem &S, const float *__restrict
         }
         S.wl[lane] = wl;
         S.nw[lane] = nw;
+        mark_tiles(flags, pp, d, wl, nw);
         S.sum[lane] = 0.f;
     }
     __syncwarp();
@@ -556,10 +577,11 @@ __device__ __forceinline__ void raster_warp(WarpSmem &S, const float *__restrict
 __global__ void __launch_bounds__(kWarpsPerCta * 32)
 k_raster_warps(const float *__restrict__ t0, const float *__restrict__ x, const float *__restrict__ y,
                const float *__restrict__ z, const float *__restrict__ q, int64_t n, PlaneParams pp,
-               uint32_t event_lo, float *__restrict__ grid, int32_t *status) {
+               uint32_t event_lo, float *__restrict__ grid, int32_t *status, uint32_t *flags) {
     __shared__ WarpSmem S[kWarpsPerCta];
     const int warp = threadIdx.x >> 5;
-    raster_warp(S[warp], t0, x, y, z, q, n, pp, event_lo, grid, status, (int64_t)blockIdx.x * kWarpsPerCta + warp, pp.rk);
+    raster_warp(S[warp], t0, x, y, z, q, n, pp, event_lo, grid, status, (int64_t)blockIdx.x * kWarpsPerCta + warp, pp.rk,
+                flags);
 }
 
 // Batched: warp-chunk c of the whole launch belongs to the (event, plane) pair whose chunk
@@ -578,16 +600,16 @@ k_raster_batch_warps(const BatchTable tab, int32_t *status) {
     const BatchItem &it = tab.item[lo];
     // every plane shares the seed, hence the round keys: take them from plane 0 (static index)
     raster_warp(S[warp], it.t0, it.x, it.y, it.z, it.q, it.n, tab.plane[it.plane], it.event_lo, it.grid, status,
-                c - it.chunk_begin, tab.plane[0].rk);
+                c - it.chunk_begin, tab.plane[0].rk, it.flags);
 }
 
 __global__ void __launch_bounds__(kChunkThreads)
 k_raster_chunks(const float *__restrict__ t0, const float *__restrict__ x, const float *__restrict__ y,
                 const float *__restrict__ z, const float *__restrict__ q, int64_t n, PlaneParams pp,
-                uint32_t event_lo, float *__restrict__ grid, int32_t *status) {
+                uint32_t event_lo, float *__restrict__ grid, int32_t *status, uint32_t *flags) {
     extern __shared__ float4 smem_raw[];
     ChunkSmem &S = *reinterpret_cast<ChunkSmem *>(smem_raw);
-    raster_chunk(S, t0, x, y, z, q, n, pp, event_lo, grid, status, blockIdx.x, pp.rk);
+    raster_chunk(S, t0, x, y, z, q, n, pp, event_lo, grid, status, blockIdx.x, pp.rk, flags);
 }
 
 // Many (event, plane) pairs in one launch: CTA b takes chunk b - chunk_begin[i] of the pair i
@@ -605,7 +627,7 @@ k_raster_batch(const BatchTable tab, int32_t *status) {
     }
     const BatchItem &it = tab.item[lo];
     raster_chunk(S, it.t0, it.x, it.y, it.z, it.q, it.n, tab.plane[it.plane], it.event_lo, it.grid, status,
-                 b - it.chunk_begin, tab.plane[0].rk);
+                 b - it.chunk_begin, tab.plane[0].rk, it.flags);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -780,13 +802,13 @@ cudaError_t launch_raster_batch(const BatchTable &tab, int64_t total_chunks, int
 }
 
 cudaError_t launch_raster_chunks(const wct_depos_t &d, const PlaneParams &pp, uint32_t event_lo, float *grid,
-                                 int32_t *status, cudaStream_t s) {
+                                 int32_t *status, cudaStream_t s, uint32_t *flags) {
     if (d.n <= 0) return cudaSuccess;
     if (g_raster_schedule != 1) {
         const int64_t chunks = (d.n + kWarpDepos - 1) / kWarpDepos;
         const int64_t blocks = (chunks + kWarpsPerCta - 1) / kWarpsPerCta;
         k_raster_warps<<<(unsigned)blocks, kWarpsPerCta * 32, 0, s>>>(d.t0_us, d.x_mm, d.y_mm, d.z_mm, d.q_e, d.n, pp,
-                                                                      event_lo, grid, status);
+                                                                      event_lo, grid, status, flags);
         return cudaGetLastError();
     }
     const size_t smem = sizeof(ChunkSmem);
@@ -794,9 +816,26 @@ cudaError_t launch_raster_chunks(const wct_depos_t &d, const PlaneParams &pp, ui
     if (e != cudaSuccess) return e;
     const int64_t blocks = (d.n + kChunk - 1) / kChunk;
     k_raster_chunks<<<(unsigned)blocks, kChunkThreads, smem, s>>>(d.t0_us, d.x_mm, d.y_mm, d.z_mm, d.q_e, d.n, pp,
-                                                                  event_lo, grid, status);
+                                                                  event_lo, grid, status, flags);
     return cudaGetLastError();
 }
+
+// Size of a plane's flag block: the flags, two counters and the tile list.
+size_t tile_flag_words(const PlaneParams &pp) { return 2 * (size_t)pp.n_tiles_w * pp.n_tiles_t + 2; }
+
+ClearJob clear_job(float *grid, uint32_t *flags, const PlaneParams &pp) {
+    ClearJob j;
+    j.grid = grid;
+    j.flags = flags;
+    j.n_wires = pp.n_wires;
+    j.n_ticks = pp.n_ticks;
+    j.tile_w = pp.tile_w;
+    j.tile_t = pp.tile_t;
+    j.n_tiles_t = pp.n_tiles_t;
+    j.n_tiles = pp.n_tiles_w * pp.n_tiles_t;
+    return j;
+}
+
 
 cudaError_t launch_rasterize_patches(int64_t n, const DepoDesc *desc, const int64_t *offsets, const PlaneParams &pp,
                                      uint32_t event_lo, float *patches, int64_t *patch_desc, cudaStream_t s) {

@@ -58,6 +58,7 @@ struct BatchItem {
     const float *t0, *x, *y, *z, *q;
     int64_t n;
     float *grid;
+    uint32_t *flags;       // touched-tile flags of grid (or null)
     int64_t chunk_begin;   // first CTA of this pair (prefix sum of its chunk counts)
     uint32_t event_lo;
     int32_t plane;
@@ -80,8 +81,61 @@ cudaError_t launch_scan_i64(const int64_t *in, int64_t *out, int64_t n, int64_t 
 int64_t scan_tmp_elems(int64_t n);
 
 cudaError_t launch_raster_chunks(const wct_depos_t &d, const PlaneParams &pp, uint32_t event_lo, float *grid,
-                                 int32_t *status, cudaStream_t s);
+                                 int32_t *status, cudaStream_t s, uint32_t *flags = nullptr);
 cudaError_t launch_raster_batch(const BatchTable &tab, int64_t total_chunks, int32_t *status, cudaStream_t s);
+// Touched-tile flags: the fused rasterizers set flags[tile] = 1 for every tile (tile_w wires x
+// tile_t ticks, pp's tiling) that a depo's window overlaps and list each such tile once
+// (flags: n_tiles flags, a count, a done-counter, the list; tile_flag_words(pp) words, all
+// zero initially).  Clearing zeroes the listed tiles of the grid and resets the flags and
+// the list, restoring an all-zero grid: a side job of the wire stage (ClearJob).
+size_t tile_flag_words(const PlaneParams &pp);
+
+struct ClearJob {
+    float *grid = nullptr;        // null: no job
+    uint32_t *flags = nullptr;
+    int n_wires = 0, n_ticks = 0, tile_w = 0, tile_t = 0, n_tiles_t = 0, n_tiles = 0;
+};
+ClearJob clear_job(float *grid, uint32_t *flags, const PlaneParams &pp);
+
+// The listed tiles of job.grid, CTA `cta` of `n_ctas` taking list entries cta, cta + n_ctas,
+// ...; threads 0 .. threads - 1 (a multiple of 32) take part and meet at named barrier 1.
+// Every CTA of the launch must call it exactly once: thread 0 reads the count for its CTA,
+// and the last CTA to have read it resets the count and the done-counter.
+__device__ __forceinline__ void clear_listed_tiles(const ClearJob &job, unsigned cta, unsigned n_ctas, int threads) {
+    __shared__ uint32_t s_count;
+    const int tid = threadIdx.x;
+    if (tid >= threads) return;
+    uint32_t *flags = job.flags;
+    const int n_tiles = job.n_tiles;
+    if (tid == 0) {
+        s_count = min(*(volatile uint32_t *)&flags[n_tiles], (uint32_t)n_tiles);
+        if (atomicAdd(&flags[n_tiles + 1], 1u) == n_ctas - 1) {   // every CTA has read the count
+            flags[n_tiles] = 0u;
+            flags[n_tiles + 1] = 0u;
+        }
+    }
+    asm volatile("bar.sync 1, %0;" ::"r"(threads) : "memory");
+    const uint32_t count = s_count;
+    const int warp = tid >> 5, lane = tid & 31, n_warps = threads >> 5;
+    const bool vec = (reinterpret_cast<uintptr_t>(job.grid) & 15) == 0 && (job.n_ticks & 3) == 0 && (job.tile_t & 3) == 0;
+    for (uint32_t i = cta; i < count; i += n_ctas) {
+        const int t = (int)flags[n_tiles + 2 + i];
+        if (t < 0 || t >= n_tiles) continue;
+        const int tw = t / job.n_tiles_t, tt = t - tw * job.n_tiles_t;
+        const int w0 = tw * job.tile_w, w1 = min(w0 + job.tile_w, job.n_wires);
+        const int c0 = tt * job.tile_t, width = min(job.tile_t, job.n_ticks - c0);
+        if (vec && (width & 3) == 0) {
+            for (int w = w0 + warp; w < w1; w += n_warps) {
+                float4 *row = reinterpret_cast<float4 *>(job.grid + (size_t)w * job.n_ticks + c0);
+                for (int c = lane; c < (width >> 2); c += 32) row[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        } else {
+            for (int w = w0 + warp; w < w1; w += n_warps)
+                for (int c = lane; c < width; c += 32) job.grid[(size_t)w * job.n_ticks + c0 + c] = 0.f;
+        }
+        if (tid == 0) flags[t] = 0u;
+    }
+}
 int64_t raster_chunk_count(int64_t n);
 void set_raster_schedule(int schedule);   // 0 warp-level chunks, 1 CTA-level chunks
 cudaError_t launch_rasterize_patches(int64_t n, const DepoDesc *desc, const int64_t *offsets, const PlaneParams &pp,
@@ -98,7 +152,7 @@ cudaError_t launch_tile_scatter_patches(const int64_t *patch_desc, const float *
 cudaError_t launch_row_r2c(const FFTPlan &p, const float *in, int64_t in_stride, int n_in_cols, int n_rows,
                            float2 *spec, cudaStream_t s, int32_t *status = nullptr);
 cudaError_t launch_wire_stage(const FFTPlan &p, const float2 *spec, const float2 *resp_spec, int n_wires,
-                              float2 *out, cudaStream_t s, int32_t *status = nullptr);
+                              float2 *out, cudaStream_t s, int32_t *status = nullptr, const ClearJob *clear = nullptr);
 cudaError_t launch_row_c2r(const FFTPlan &p, const float2 *spec, int n_rows, float *out, int64_t out_stride,
                            int n_out_cols, cudaStream_t s, int32_t *status = nullptr);
 cudaError_t launch_scale_spectrum(float2 *spec, int64_t n, float scale, cudaStream_t s);

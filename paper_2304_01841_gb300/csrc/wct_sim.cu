@@ -48,6 +48,14 @@ struct wct_sim {
     wct_opts_t opts{};
     // scratch
     float2 *spec = nullptr, *spec2 = nullptr;
+    // Accumulation grids of run_event / run_batch: two sets of every plane's grid, kept all
+    // zero between uses: the rasterizer flags the tiles it touches, and once the forward
+    // transform has read a grid those tiles are cleared again.
+    float *grids[2] = {};
+    size_t grid_off[kMaxPlanes + 1] = {};
+    uint32_t *tile_flags[2] = {};
+    size_t flag_off[kMaxPlanes + 1] = {};
+    cudaEvent_t gev[2] = {};   // run_batch: a grid set's clearing transforms are done
     DepoDesc *desc = nullptr;
     int64_t *patch_size = nullptr, *patch_off = nullptr, *scan64 = nullptr;
     int64_t depo_cap = 0;
@@ -373,27 +381,44 @@ void mark(wct_sim *s, int slot, int k, cudaStream_t st) {
     if (slot >= 0) cudaEventRecord(s->slots[slot][k], st);
 }
 
-// Fused rasterize + scatter of one plane into `grid` (zeroed first, then accumulated).
-wct_status_t raster_scatter(wct_sim *s, int plane, const wct_depos_t *d, float *grid, cudaStream_t st, int slot) {
+// Restore the all-zero library grids after a failed call (synchronous; best effort).
+void clear_grids(wct_sim *s) {
+    for (int b = 0; b < 2; ++b) {
+        if (s->grids[b]) cudaMemset(s->grids[b], 0, sizeof(float) * s->grid_off[s->n_planes]);
+        if (s->tile_flags[b]) cudaMemset(s->tile_flags[b], 0, sizeof(uint32_t) * s->flag_off[s->n_planes]);
+    }
+    cudaDeviceSynchronize();
+}
+
+// Fused rasterize + scatter of one plane into `grid` (zeroed first unless it is known to be
+// zero, then accumulated).
+wct_status_t raster_scatter(wct_sim *s, int plane, const wct_depos_t *d, float *grid, cudaStream_t st, int slot,
+                            bool clear = true, uint32_t *flags = nullptr) {
     const PlaneState &ps = s->planes[plane];
     const PlaneParams pp = plane_params(s, plane);
-    cudaError_t e = cudaMemsetAsync(grid, 0, sizeof(float) * (size_t)ps.g.n_wires * ps.g.n_ticks, st);
+    cudaError_t e = clear ? cudaMemsetAsync(grid, 0, sizeof(float) * (size_t)ps.g.n_wires * ps.g.n_ticks, st)
+                          : cudaSuccess;
     if (e != cudaSuccess) return cuda_fail(s, e, "grid clear");
     mark(s, slot, 1, st);
-    e = launch_raster_chunks(*d, pp, (uint32_t)d->event_id, grid, s->status, st);
+    e = launch_raster_chunks(*d, pp, (uint32_t)d->event_id, grid, s->status, st, flags);
     if (e != cudaSuccess) return cuda_fail(s, e, "raster-scatter");
     s->launches += d->n > 0 ? 1 : 0;
     mark(s, slot, 2, st);
     return WCT_OK;
 }
 
-wct_status_t convolve_plane(wct_sim *s, int plane, const float *grid, float *wf, cudaStream_t st, int slot) {
+// The convolution of one plane.  clear_grid (== grid, a library grid) with its tile flags:
+// the flagged tiles are zeroed once the forward transform has read the grid.
+wct_status_t convolve_plane(wct_sim *s, int plane, const float *grid, float *wf, cudaStream_t st, int slot,
+                            float *clear_grid = nullptr, uint32_t *flags = nullptr) {
     const PlaneState &ps = s->planes[plane];
     const int nw = ps.g.n_wires, nt = ps.g.n_ticks;
     cudaError_t e = launch_row_r2c(ps.fft, grid, nt, nt, nw, s->spec, st, s->status);
     if (e != cudaSuccess) return cuda_fail(s, e, "row r2c");
     mark(s, slot, 3, st);
-    e = launch_wire_stage(ps.fft, s->spec, ps.resp_spec, nw, s->spec2, st, s->status);
+    // the wire stage clears the grid tiles the rasterizer listed, as a side job
+    const ClearJob job = clear_grid ? clear_job(clear_grid, flags, ps.pp) : ClearJob{};
+    e = launch_wire_stage(ps.fft, s->spec, ps.resp_spec, nw, s->spec2, st, s->status, clear_grid ? &job : nullptr);
     if (e != cudaSuccess) return cuda_fail(s, e, "wire stage");
     mark(s, slot, 4, st);
     e = launch_row_c2r(ps.fft, s->spec2, nw, wf, nt, nt, st, s->status);
@@ -574,6 +599,20 @@ wct_status_t wct_sim_create(const wct_plane_t *planes, int n_planes, const wct_r
     }
     if (st == WCT_OK) st = dev_alloc(s, (void **)&s->spec, sizeof(float2) * spec_elems);
     if (st == WCT_OK) st = dev_alloc(s, (void **)&s->spec2, sizeof(float2) * spec_elems);
+    for (int p = 0; p < n_planes; ++p) {
+        s->grid_off[p + 1] = s->grid_off[p] + (size_t)s->planes[p].g.n_wires * s->planes[p].g.n_ticks;
+        s->flag_off[p + 1] = s->flag_off[p] + tile_flag_words(s->planes[p].pp);
+    }
+    for (int b = 0; b < 2 && st == WCT_OK; ++b) {
+        st = dev_alloc(s, (void **)&s->grids[b], sizeof(float) * s->grid_off[n_planes]);
+        if (st == WCT_OK) st = dev_alloc(s, (void **)&s->tile_flags[b], sizeof(uint32_t) * s->flag_off[n_planes]);
+        if (st == WCT_OK) {
+            cudaError_t e = cudaMemset(s->grids[b], 0, sizeof(float) * s->grid_off[n_planes]);
+            if (e == cudaSuccess) e = cudaMemset(s->tile_flags[b], 0, sizeof(uint32_t) * s->flag_off[n_planes]);
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) st = cuda_fail(s, e, "grid init");
+        }
+    }
     if (st != WCT_OK) {
         for (void *a : s->allocs)
             if (a) cudaFree(a);
@@ -596,6 +635,8 @@ wct_status_t wct_sim_destroy(wct_sim_t *s) {
     if (s->rs_stream) cudaStreamDestroy(s->rs_stream);
     if (s->cv_stream) cudaStreamDestroy(s->cv_stream);
     for (auto &e : s->bev)
+        if (e) cudaEventDestroy(e);
+    for (auto &e : s->gev)
         if (e) cudaEventDestroy(e);
     for (cudaStream_t h : {s->up_stream, s->comp_stream, s->down_stream})
         if (h) cudaStreamDestroy(h);
@@ -674,10 +715,17 @@ wct_status_t wct_sim_run_event(wct_sim_t *s, const wct_depos_t *d, float *const 
     if ((st = ensure_depo_capacity(s, d->n))) return st;
     cudaStream_t cs = (cudaStream_t)stream;
     for (int p = 0; p < s->n_planes; ++p) {
+        // accumulate into the library grid (all zero), which the forward transform clears
+        // again as it reads it; the inverse transform writes the caller's waveform
+        float *grid = s->grids[0] + s->grid_off[p];
+        uint32_t *flags = s->tile_flags[0] + s->flag_off[p];
         const int slot = acquire_slot(s);
         mark(s, slot, 0, cs);
-        if ((st = raster_scatter(s, p, d, wfs[p], cs, slot))) return st;
-        if ((st = convolve_plane(s, p, wfs[p], wfs[p], cs, slot))) return st;
+        if ((st = raster_scatter(s, p, d, grid, cs, slot, false, flags)) ||
+            (st = convolve_plane(s, p, grid, wfs[p], cs, slot, grid, flags))) {
+            clear_grids(s);
+            return st;
+        }
     }
     if (s->timing) ++s->events_timed;
     return WCT_OK;
@@ -703,6 +751,7 @@ wct_status_t batch_streams(wct_sim *s) {
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->cv_stream, cudaStreamNonBlocking, hi);
     for (int i = 0; e == cudaSuccess && i < kBatchEvents; ++i)
         e = cudaEventCreateWithFlags(&s->bev[i], cudaEventDisableTiming);
+    for (int b = 0; e == cudaSuccess && b < 2; ++b) e = cudaEventCreateWithFlags(&s->gev[b], cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_fail(s, e, "batch streams");
     return WCT_OK;
 }
@@ -727,11 +776,13 @@ wct_status_t enqueue_batch(wct_sim *s, const wct_depos_t *events, int n_events, 
         const wct_depos_t &d = events[e];
         int64_t chunks = 0;
         tab.n_items = 0;
+        const int gb = e & 1;   // grid set of this event (all zero once its previous user is done)
+        if (e >= 2) {
+            err = cudaStreamWaitEvent(rs, s->gev[gb], 0);
+            if (err != cudaSuccess) return cuda_fail(s, err, "batch grid dependency");
+        }
         for (int p = 0; p < npl; ++p) {
-            const PlaneState &ps = s->planes[p];
-            float *grid = wfs[(size_t)e * npl + p];
-            err = cudaMemsetAsync(grid, 0, sizeof(float) * (size_t)ps.g.n_wires * ps.g.n_ticks, rs);
-            if (err != cudaSuccess) return cuda_fail(s, err, "grid clear");
+            float *grid = s->grids[gb] + s->grid_off[p];
             if (d.n <= 0) continue;
             BatchItem &b = tab.item[tab.n_items++];
             b.t0 = d.t0_us;
@@ -741,6 +792,7 @@ wct_status_t enqueue_batch(wct_sim *s, const wct_depos_t *events, int n_events, 
             b.q = d.q_e;
             b.n = d.n;
             b.grid = grid;
+            b.flags = s->tile_flags[gb] + s->flag_off[p];
             b.chunk_begin = chunks;
             b.event_lo = (uint32_t)d.event_id;
             b.plane = p;
@@ -756,10 +808,12 @@ wct_status_t enqueue_batch(wct_sim *s, const wct_depos_t *events, int n_events, 
         if (err == cudaSuccess) err = cudaStreamWaitEvent(cv, done, 0);
         if (err != cudaSuccess) return cuda_fail(s, err, "batch dependency");
         for (int p = 0; p < npl; ++p) {
-            float *grid = wfs[(size_t)e * npl + p];
-            r = convolve_plane(s, p, grid, grid, cv, -1);
+            float *grid = s->grids[gb] + s->grid_off[p];
+            r = convolve_plane(s, p, grid, wfs[(size_t)e * npl + p], cv, -1, grid, s->tile_flags[gb] + s->flag_off[p]);
             if (r) return r;
         }
+        err = cudaEventRecord(s->gev[gb], cv);
+        if (err != cudaSuccess) return cuda_fail(s, err, "batch grid dependency");
     }
     cudaEvent_t end = s->bev[kBatchEvents - 1];
     err = cudaEventRecord(end, cv);
@@ -933,8 +987,11 @@ wct_status_t wct_sim_run_host(wct_sim_t *s, const wct_host_depos_t *events, int 
         const cudaError_t e2 = cudaStreamSynchronize(h);
         if (err == cudaSuccess) err = e2;
     }
-    if (st) return st;
-    if (err != cudaSuccess) return cuda_fail(s, err, "host pipeline");
+    if (st) return st;   // run_event restored the grids
+    if (err != cudaSuccess) {
+        clear_grids(s);
+        return cuda_fail(s, err, "host pipeline");
+    }
     return wct_sim_sync(s, comp);
 }
 
@@ -945,6 +1002,15 @@ wct_status_t wct_sim_sync(wct_sim_t *s, void *stream) {
     int32_t code = 0;
     e = cudaMemcpy(&code, s->status, sizeof(int32_t), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemset(s->status, 0, sizeof(int32_t));
+    if (e == cudaSuccess && code != 0) {
+        // a device-side error may have left a grid row uncleared: restore the all-zero grids
+        for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+            if (s->grids[b]) e = cudaMemset(s->grids[b], 0, sizeof(float) * s->grid_off[s->n_planes]);
+            if (e == cudaSuccess && s->tile_flags[b])
+                e = cudaMemset(s->tile_flags[b], 0, sizeof(uint32_t) * s->flag_off[s->n_planes]);
+        }
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    }
     if (e != cudaSuccess) return cuda_fail(s, e, "status read");
     if (code == ST_EINVAL) return fail(s, WCT_EINVAL, "invalid depo(s) skipped (non-finite, x<0, q<0 or window too large)");
     if (code == ST_ETIMEOUT) return fail(s, WCT_ETIMEOUT, "a device-side wait timed out");

@@ -200,6 +200,33 @@ def test_event_three_plane_reduced():
 # ------------------------------------------------------------------------------------------
 # Edge cases
 # ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("schedule", [-1, 6])
+def test_library_grids_return_to_zero(schedule):
+    # run_event accumulates into library grids that are cleared tile by tile after each
+    # forward transform: event A, event B, A again must give A's waveforms both times and B's
+    # as on a fresh handle (schedule 6: CTA-level rasterizer, paired row transforms)
+    wl = synth.workload("tiny")
+    da = wl.depos()
+    lo = [float(da.x.min()), float(da.y.min()), float(da.z.min())]
+    hi = [float(da.x.max()), float(da.y.max()), float(da.z.max())]
+    db = synth.make_isolated_depos(np.random.default_rng(5), 3000, lo, hi)
+    db.event_id = 77
+    try:
+        sim = make_sim(wl.planes, wl.responses(), wl.diffusion, schedule_id=schedule)
+        a1 = [to_np(w) for w in sim.run_event(_dev(da))]
+        b1 = [to_np(w) for w in sim.run_event(_dev(db))]
+        a2 = [to_np(w) for w in sim.run_event(_dev(da))]
+        sim.sync()
+        fresh = make_sim(wl.planes, wl.responses(), wl.diffusion, schedule_id=schedule)
+        b0 = [to_np(w) for w in fresh.run_event(_dev(db))]
+        fresh.sync()
+        for p in range(len(wl.planes)):
+            assert np.abs(a1[p] - a2[p]).max() <= 1e-5 * np.abs(a1[p]).max()
+            assert np.abs(b1[p] - b0[p]).max() <= 1e-5 * np.abs(b0[p]).max()
+    finally:
+        make_sim(wl.planes, wl.responses(), wl.diffusion, schedule_id=4)
+
+
 def test_empty_event_gives_zero_waveforms():
     wl = synth.workload("tiny")
     sim = make_sim(wl.planes, wl.responses(), wl.diffusion)
