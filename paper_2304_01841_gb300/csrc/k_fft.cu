@@ -962,9 +962,13 @@ k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, in
     // output b+j = sum_k win[j + 20 - k] * Rt[k]; each input row is read from the ring once.
     constexpr int kOutBlock = 8;
     constexpr int kWin = kOutBlock + 2 * KC;
-    float2 r[KW];
+    float2 rr[KW], ri[KW];                             // (re, re) and (im, im) of each tap
 #pragma unroll
-    for (int k = 0; k < KW; ++k) r[k] = live ? Rt[(size_t)k * Fs + f] : make_float2(0.f, 0.f);
+    for (int k = 0; k < KW; ++k) {
+        const float2 v = live ? Rt[(size_t)k * Fs + f] : make_float2(0.f, 0.f);
+        rr[k] = make_float2(v.x, v.x);
+        ri[k] = make_float2(v.y, v.y);
+    }
     bool ok = true;
     auto load_row = [&](int m) -> float2 {
         float2 x = make_float2(0.f, 0.f);
@@ -990,19 +994,23 @@ k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, in
         for (int t = 0; t < kOutBlock; ++t) win[2 * KC + t] = load_row(b + 2 * KC + t);
 #pragma unroll
         for (int j = 0; j < kOutBlock; ++j) {
-            float re = 0.f, im = 0.f, re2 = 0.f, im2 = 0.f;
+            // packed pairs: A = sum x * (r.re, r.re), B = sum x * (r.im, r.im), so that
+            // re = A.re - B.im and im = A.im + B.re (two FFMA2 per tap instead of four FFMA)
+            float2 A = make_float2(0.f, 0.f), B = A, A2 = A, B2 = A;
 #pragma unroll
             for (int k = 0; k < KW; ++k) {
                 const float2 x = win[j + 2 * KC - k];
                 if (k & 1) {
-                    re2 = fmaf(x.x, r[k].x, fmaf(-x.y, r[k].y, re2));
-                    im2 = fmaf(x.x, r[k].y, fmaf(x.y, r[k].x, im2));
+                    A2 = fma2(x, rr[k], A2);
+                    B2 = fma2(x, ri[k], B2);
                 } else {
-                    re = fmaf(x.x, r[k].x, fmaf(-x.y, r[k].y, re));
-                    im = fmaf(x.x, r[k].y, fmaf(x.y, r[k].x, im));
+                    A = fma2(x, rr[k], A);
+                    B = fma2(x, ri[k], B);
                 }
             }
-            if (live && b + j < n_out) T[(size_t)(w0 + b + j) * Fs + f] = make_float2(re + re2, im + im2);
+            A = add2(A, A2);
+            B = add2(B, B2);
+            if (live && b + j < n_out) T[(size_t)(w0 + b + j) * Fs + f] = make_float2(A.x - B.y, A.y + B.x);
         }
 #pragma unroll
         for (int t = 0; t < 2 * KC; ++t) win[t] = win[t + kOutBlock];
