@@ -175,68 +175,114 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
     return bits_f2(d);
 }
 
-// The same window, decided cheaply.  FP64 division and square root are slow on this part,
-// so: mu comes from multiplications by host-computed FP64 reciprocals (within ~1e-12 bin of
-// the divided value), sigma from an FP32 square root (relative error < 2^-21).  Each window
-// edge floor(mu -+ n sigma) is accepted when the interval of +-eps around it (eps bounds both
-// errors generously) holds no integer, and the point-charge test when sigma is not within
-// 1e-5 (relative) of its threshold; otherwise depo_window_f64 decides, exactly as before.
-// mu_t/mu_p relative to the window and the erf scales only feed FP32 weights.
-__device__ __forceinline__ bool fast_edge(double a, double eps, long long &f) {
-    const double lo = floor(a - eps), hi = floor(a + eps);
-    f = (long long)lo;
-    return lo == hi;
+// Double-float arithmetic (an unevaluated sum hi + lo of two floats, ~48-bit significand)
+// from error-free transformations: Knuth's TwoSum, Dekker's Fast2Sum and the FMA-based
+// TwoProduct.  Explicitly rounded operations keep the compiler from contracting them.
+struct ffloat {
+    float hi, lo;
+};
+__device__ __forceinline__ ffloat ff_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ ffloat ff_fast_two_sum(float a, float b) {   // |a| >= |b| (or a == 0)
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ffloat ff_two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ ffloat ff_add(ffloat a, ffloat b) {
+    ffloat s = ff_two_sum(a.hi, b.hi);
+    const ffloat t = ff_two_sum(a.lo, b.lo);
+    s = ff_fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+    return ff_fast_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
+}
+__device__ __forceinline__ ffloat ff_mul(ffloat a, ffloat b) {
+    ffloat p = ff_two_prod(a.hi, b.hi);
+    p.lo = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo));
+    return ff_fast_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ ffloat ff_mul_f(float a, ffloat b) {
+    ffloat p = ff_two_prod(a, b.hi);
+    p.lo = __fmaf_rn(a, b.lo, p.lo);
+    return ff_fast_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ ffloat ff_of(const float (&c)[2]) { return {c[0], c[1]}; }
+__device__ __forceinline__ ffloat ff_neg(ffloat a) { return {-a.hi, -a.lo}; }
+
+// floor(v) when v = hi + lo lies more than eps from every integer (|hi| < 2^22); false
+// otherwise.  hi - floor(hi) and floor(hi) + 1 - hi are exact.
+__device__ __forceinline__ bool ff_floor(ffloat v, float eps, int &f) {
+    if (!(fabsf(v.hi) < 4194304.f)) return false;
+    const float fl = floorf(v.hi);
+    const float above = __fadd_rn(__fsub_rn(v.hi, fl), v.lo);
+    const float below = __fsub_rn(__fsub_rn(__fadd_rn(fl, 1.f), v.hi), v.lo);
+    f = (int)fl;
+    return above > eps && below > eps;
 }
 
-__device__ __forceinline__ bool depo_window(double T0, double X, double Y, double Z, double Q, const PlaneParams &pp,
+// The same window, decided cheaply.  FP64 arithmetic is slow on this part, so the fast
+// path is all FP32: mu_t = x / (v tick) + (t0 - tw0) / tick and mu_p = (z cos a + y sin a -
+// origin) / dp in double-float arithmetic with host-computed reciprocals (error ~1e-13 of
+// the operands' magnitude, against ~1e-16 for the FP64 evaluation), sigma from an FP32
+// square root (relative error < 2^-21).  Each window edge floor(mu -+ n sigma) is accepted
+// when it lies farther than eps from every integer, eps = 1e-9 (1 + the magnitudes summed) +
+// 4e-6 n sigma bounding both evaluations' errors generously, and the point-charge test when
+// sigma is not within 1e-5 (relative) of its threshold; otherwise depo_window_f64 decides,
+// exactly as the oracle.  mu_t / mu_p relative to the window and the erf scales only feed
+// FP32 weights.
+__device__ __forceinline__ bool depo_window(float T0, float X, float Y, float Z, float Q, const PlaneParams &pp,
                                             DepoDesc &d) {
-    const bool ok = isfinite(T0) && isfinite(X) && isfinite(Y) && isfinite(Z) && isfinite(Q) && X >= 0.0 && Q >= 0.0;
+    const bool ok = isfinite(T0) && isfinite(X) && isfinite(Y) && isfinite(Z) && isfinite(Q) && X >= 0.f && Q >= 0.f;
     if (!ok) return depo_window_f64(T0, X, Y, Z, Q, pp, d);
-    const double mu_t = fma(X, pp.inv_vtick, (T0 - pp.tw0) * pp.inv_tick);
-    const double p = fma(Z, pp.cos_a, Y * pp.sin_a);
-    const double mu_p = (p - pp.origin) * pp.inv_dp;
-    const float sx = sqrtf((float)X);
+    // mu_t = X * inv_vtick + (T0 - tw0) * inv_tick
+    const ffloat dt0 = ff_add({T0, 0.f}, ff_neg(ff_of(pp.ff[2])));
+    const ffloat mu_t = ff_add(ff_mul_f(X, ff_of(pp.ff[0])), ff_mul(dt0, ff_of(pp.ff[1])));
+    // mu_p = (Z cos a + Y sin a - origin) * inv_dp
+    const ffloat pz = ff_add(ff_mul_f(Z, ff_of(pp.ff[3])), ff_mul_f(Y, ff_of(pp.ff[4])));
+    const ffloat mu_p = ff_mul(ff_add(pz, ff_neg(ff_of(pp.ff[5]))), ff_of(pp.ff[6]));
+    const float sx = sqrtf(X);
     const float s_t = sx * pp.kt, s_p = sx * pp.kp;
     const float ns = (float)pp.nsigma;
-    const double big = 1099511627776.0;
-    if (!(fabs(mu_t) < 0.5 * big && fabs(mu_p) < 0.5 * big && s_t < 1e30f && s_p < 1e30f))
-        return depo_window_f64(T0, X, Y, Z, Q, pp, d);
-    long long lo_t, hi_t, lo_p, hi_p;
+    if (!(s_t < 1e30f && s_p < 1e30f)) return depo_window_f64(T0, X, Y, Z, Q, pp, d);
+    const float mag_t = fabsf(mu_t.hi) + (fabsf(T0) + fabsf(pp.ff[2][0])) * pp.ff[1][0] + X * pp.ff[0][0];
+    const float mag_p = fabsf(mu_p.hi) + (fabsf(pz.hi) + fabsf(pp.ff[5][0])) * pp.ff[6][0];
+    const float et = 1e-9f * (1.f + mag_t) + 4e-6f * (ns * s_t);
+    const float ep = 1e-9f * (1.f + mag_p) + 4e-6f * (ns * s_p);
+    int lo_t, hi_t, lo_p, hi_p;
     bool sure = true;
     // point-charge threshold: sigma < 1e-6 bin
     const bool dt = s_t < 1e-6f, dp = s_p < 1e-6f;
     sure &= fabsf(s_t - 1e-6f) > 1e-11f && fabsf(s_p - 1e-6f) > 1e-11f;
-    const double et = 1e-9 * (1.0 + fabs(mu_t)) + 4e-6 * (double)(ns * s_t);
-    const double ep = 1e-9 * (1.0 + fabs(mu_p)) + 4e-6 * (double)(ns * s_p);
-    if (dt) sure &= fast_edge(mu_t, et, lo_t), hi_t = lo_t;
+    if (dt) sure &= ff_floor(mu_t, et, lo_t), hi_t = lo_t;
     else {
-        sure &= fast_edge(mu_t - (double)(ns * s_t), et, lo_t);
-        sure &= fast_edge(mu_t + (double)(ns * s_t), et, hi_t);
+        sure &= ff_floor(ff_add(mu_t, {-(ns * s_t), 0.f}), et, lo_t);
+        sure &= ff_floor(ff_add(mu_t, {ns * s_t, 0.f}), et, hi_t);
     }
-    if (dp) sure &= fast_edge(mu_p, ep, lo_p), hi_p = lo_p;
+    if (dp) sure &= ff_floor(mu_p, ep, lo_p), hi_p = lo_p;
     else {
-        sure &= fast_edge(mu_p - (double)(ns * s_p), ep, lo_p);
-        sure &= fast_edge(mu_p + (double)(ns * s_p), ep, hi_p);
+        sure &= ff_floor(ff_add(mu_p, {-(ns * s_p), 0.f}), ep, lo_p);
+        sure &= ff_floor(ff_add(mu_p, {ns * s_p, 0.f}), ep, hi_p);
     }
     if (!sure) return depo_window_f64(T0, X, Y, Z, Q, pp, d);
-    const long long n_t = hi_t - lo_t + 1, n_p = hi_p - lo_p + 1;
-    const long long lim = 1LL << 30;
+    const int n_t = hi_t - lo_t + 1, n_p = hi_p - lo_p + 1;
     d.mu_t = d.mu_p = d.inv_t = d.inv_p = 0.f;
     d.q = 0.f;
     d.lo_t = d.lo_p = 0;
     d.nt = d.np = 0;
-    if (n_t > WCT_MAX_WINDOW_TICKS || n_p > WCT_MAX_WINDOW_IMPACTS || lo_t < -lim || lo_t > lim || lo_p < -lim ||
-        lo_p > lim)
-        return false;
-    d.lo_t = (int32_t)lo_t;
-    d.lo_p = (int32_t)lo_p;
+    if (n_t > WCT_MAX_WINDOW_TICKS || n_p > WCT_MAX_WINDOW_IMPACTS) return false;   // |edges| < 2^22 < 2^30
+    d.lo_t = lo_t;
+    d.lo_p = lo_p;
     d.nt = (int16_t)n_t;
     d.np = (int16_t)n_p;
-    d.mu_t = (float)(mu_t - (double)lo_t);
-    d.mu_p = (float)(mu_p - (double)lo_p);
+    d.mu_t = __fadd_rn(__fsub_rn(mu_t.hi, (float)lo_t), mu_t.lo);
+    d.mu_p = __fadd_rn(__fsub_rn(mu_p.hi, (float)lo_p), mu_p.lo);
     d.inv_t = dt ? 0.f : 0.70710678118654752f / s_t;
     d.inv_p = dp ? 0.f : 0.70710678118654752f / s_p;
-    d.q = (float)Q;
+    d.q = Q;
     return true;
 }
 

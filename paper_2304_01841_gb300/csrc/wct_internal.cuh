@@ -27,6 +27,9 @@ struct PlaneParams {
     double pitch, origin, cos_a, sin_a, tick, tw0, dp;   // dp = pitch / n_imp
     double DL, DT, v, nsigma;                            // DL, DT in mm^2/us
     double inv_tick, inv_vtick, inv_dp;                  // 1/tick, 1/(v tick), 1/dp
+    // the same constants as double-floats (hi, lo): inv_vtick, inv_tick, tw0, cos_a, sin_a,
+    // origin, inv_dp; the window's fast path runs on them in FP32
+    float ff[7][2];
     float kt, kp;                                        // sigma_t = kt sqrt(x), sigma_p = kp sqrt(x)
     int32_t n_imp, n_wires, n_ticks, plane_index;
     int32_t fluctuate;

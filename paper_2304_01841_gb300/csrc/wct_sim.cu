@@ -494,6 +494,13 @@ wct_status_t wct_sim_create(const wct_plane_t *planes, int n_planes, const wct_r
         pp.inv_tick = 1.0 / g.tick_us;
         pp.inv_vtick = 1.0 / (df.v_drift_mm_us * g.tick_us);
         pp.inv_dp = 1.0 / pp.dp;
+        {
+            const double c[7] = {pp.inv_vtick, pp.inv_tick, pp.tw0, pp.cos_a, pp.sin_a, pp.origin, pp.inv_dp};
+            for (int k = 0; k < 7; ++k) {
+                pp.ff[k][0] = (float)c[k];
+                pp.ff[k][1] = (float)(c[k] - (double)pp.ff[k][0]);
+            }
+        }
         // sigma_t = sqrt(2 D_L x / v) / v / tick, sigma_p = sqrt(2 D_T x / v) / dp
         pp.kt = (float)(std::sqrt(2.0 * pp.DL / df.v_drift_mm_us) / (df.v_drift_mm_us * g.tick_us));
         pp.kp = (float)(std::sqrt(2.0 * pp.DT / df.v_drift_mm_us) / pp.dp);
