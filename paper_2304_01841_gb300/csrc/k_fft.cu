@@ -1270,11 +1270,28 @@ cudaError_t launch_wire_stage(const FFTPlan &p, const float2 *spec, const float2
     if (n_wires <= 0) return cudaSuccess;
     const ClearJob job = clear ? *clear : ClearJob{};
     if (aligned16(spec) && (p.Fs % 2) == 0 && (p.Fu % 2) == 0) {
-        // fewer wires per CTA when the frequency blocks alone leave the SMs short of CTAs
-        // (about six resident per SM hide the ring's latency); each CTA re-reads 20 halo rows
+        // Output wires per CTA: a CTA's time grows with the rows it streams (wpc + 20 halo),
+        // and the launch takes ceil(CTAs / resident CTAs) waves, so pick the wpc that
+        // minimises waves x (wpc + 20): a last, nearly empty wave costs a full CTA time.
         const int fb = (p.Fu + kStageFB - 1) / kStageFB;
+        static int resident = 0;
+        if (resident == 0) {
+            int per_sm = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wire_stage_tma, kStageFB + 32, 0) != cudaSuccess ||
+                per_sm < 1)
+                per_sm = 1;
+            resident = per_sm * std::max(device_sms(), 1);
+        }
         int wpc = kStageWiresMax;
-        while (wpc > 32 && (int64_t)fb * ((n_wires + wpc - 1) / wpc) < 6 * 152) wpc /= 2;
+        int64_t best = INT64_MAX;
+        for (int c = 16; c <= kStageWiresMax; ++c) {
+            const int64_t ctas = (int64_t)fb * ((n_wires + c - 1) / c);
+            const int64_t cost = (ctas + resident - 1) / resident * (c + 2 * KC);
+            if (cost < best) {
+                best = cost;
+                wpc = c;
+            }
+        }
         dim3 grid(fb, (n_wires + wpc - 1) / wpc);
         k_wire_stage_tma<<<grid, kStageFB + 32, 0, s>>>(spec, resp_spec, p.Fs, p.Fu, n_wires, wpc, out, status, job);
         return cudaGetLastError();
