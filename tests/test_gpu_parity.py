@@ -44,6 +44,16 @@ def test_philox_bit_exact():
         got = g.philox4x32_10(torch.from_numpy(ctr.view(np.int32)).cuda(), seed)
         torch.cuda.synchronize()
         assert np.array_equal(to_np(got).view(np.uint32), want)
+    # the published known-answer vectors, directly
+    import os
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")):
+        if not line.strip() or line.startswith("#"):
+            continue
+        v = [int(t, 16) for t in line.split()]
+        c = np.array([v[0:4]], dtype=np.uint32)
+        got = g.philox4x32_10(torch.from_numpy(c.view(np.int32)).cuda(), v[4] | (v[5] << 32))
+        torch.cuda.synchronize()
+        assert [int(x) for x in to_np(got).view(np.uint32).ravel()] == v[6:10]
 
 
 # ------------------------------------------------------------------------------------------

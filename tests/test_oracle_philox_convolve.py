@@ -6,6 +6,8 @@ tests, by bit-equality with the separately written CUDA generator.  The convolut
 pinned by closed forms (delta response, delta grid), by the literal quadruple loop, by
 linearity and by the absence of circular wrap-around.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -13,6 +15,23 @@ import oracle
 import synth
 
 scipy_stats = pytest.importorskip("scipy.stats")
+
+
+def _kat_vectors():
+    path = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")
+    rows = []
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            v = [int(t, 16) for t in line.split()]
+            rows.append((v[0:4], (v[4], v[5]), v[6:10]))
+    return rows
+
+
+def test_philox_known_answer_vectors():
+    # the published known-answer vectors of Philox4x32-10 (tests/golden, cited there)
+    for ctr, key, want in _kat_vectors():
+        got = oracle.philox4x32_10(np.array([ctr], dtype=np.uint32), key)
+        assert [int(v) for v in np.asarray(got).ravel()] == want
 
 
 def test_philox_words_are_uniform():
