@@ -11,12 +11,14 @@ Parity status of each function (what pins it; see tests/test_oracle_*.py):
                        hand-computed drift / diffusion values, moments of the patch.
   rasterize (no fluct) pinned: patch sums to q, outer-product structure, shift invariance.
   rasterize (fluct)    pinned statistically: per-bin mean / variance of the multinomial,
-                       large-q limit.  The exact Philox stream is pinned only by statistics
-                       and by bit-equality with the independent CUDA implementation (no
-                       published known-answer vectors are available here).
+                       large-q limit; the Philox4x32-10 stream by the published Random123
+                       known-answer vectors (tests/golden).
   scatter              pinned: charge conservation, hand-built folding cases.
   convolve             pinned: delta response = identity, delta grid = placed response,
                        direct quadruple loop, no circular wrap, linearity.
+  impact-resolution    pinned: phase-independent responses reduce to the folded path,
+  scatter / convolve   FFT form = literal loops, a single sub-bin charge places its phase's
+                       response, the impact grid folds to the wire grid.
 """
 from __future__ import annotations
 
@@ -28,7 +30,7 @@ from typing import Optional, Tuple
 
 import numpy as np
 
-from .convolve import convolve_fft, convolve_direct_np  # noqa: F401
+from .convolve import convolve_fft, convolve_direct_np, convolve_impact, convolve_impact_direct  # noqa: F401
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "wct_oracle.c")
@@ -191,3 +193,34 @@ def simulate_plane(depos, plane, diff, resp, plane_index: int = 0):
     grid = scatter(pt, plane)
     wf = convolve_fft(grid, resp)
     return pt, grid, wf
+
+
+def scatter_impact(patches: Patches, plane) -> np.ndarray:
+    """Scatter-add at impact resolution: grid[j, t] over impact sub-bins j (wire j // n_imp,
+    phase j % n_imp) and ticks, (n_wires * n_imp) x n_ticks, FP64; bins outside are dropped.
+    The transverse grid of the paper's scatter-add step (§2 step 2) kept at the resolution of
+    the patches instead of folded onto wires."""
+    n_imp = plane.n_impact_per_pitch
+    ni, nt = plane.n_wires * n_imp, plane.n_ticks
+    grid = np.zeros((ni, nt), dtype=np.float64)
+    desc = patches.desc
+    for k in range(desc.shape[0]):
+        off, lo_t, lo_p, n_t, n_p = (int(v) for v in desc[k])
+        if n_t == 0:
+            continue
+        patch = patches.values[off: off + n_t * n_p].reshape(n_t, n_p)   # [tick][impact]
+        t0, t1 = max(lo_t, 0), min(lo_t + n_t, nt)
+        j0, j1 = max(lo_p, 0), min(lo_p + n_p, ni)
+        if t0 >= t1 or j0 >= j1:
+            continue
+        grid[j0:j1, t0:t1] += patch[t0 - lo_t: t1 - lo_t, j0 - lo_p: j1 - lo_p].T
+    return grid
+
+
+def simulate_plane_impact(depos, plane, diff, resp_impact, plane_index: int = 0):
+    """Whole hot path with per-impact-position responses: (patches, impact grid, waveform).
+    resp_impact[phase][wire offset][tick]."""
+    pt = rasterize(depos, plane, diff, plane_index)
+    g = scatter_impact(pt, plane)
+    wf = convolve_impact(g, resp_impact)
+    return pt, g, wf

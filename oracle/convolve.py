@@ -50,3 +50,46 @@ def convolve_direct_np(grid: np.ndarray, resp: np.ndarray) -> np.ndarray:
                 continue
             out[w_lo:w_hi, tau:] += c * g[w_lo - dw: w_hi - dw, : nt - tau]
     return out
+
+
+# Per-impact-position responses.  The transverse grid is kept at impact resolution: row
+# j = n_imp * w' + phase holds the charge arriving in sub-bin `phase` of wire w', and the
+# response seen on wire w depends on both the wire offset k = w - w' and the phase:
+#     out[w, t] = sum_{w', phase} sum_tau g[n_imp w' + phase, t - tau] * resp[phase][k + kc][tau]
+# (the detector response of §2 step 3 resolved by impact position, as the toolkit's
+# per-impact field responses are).  With the same response for every phase this is the
+# folded convolution of the summed sub-bins.
+
+def convolve_impact(g_imp: np.ndarray, resp_impact: np.ndarray, workers: int = 1) -> np.ndarray:
+    r = np.asarray(resp_impact, dtype=np.float64)
+    n_imp = r.shape[0]
+    g = np.asarray(g_imp, dtype=np.float64)
+    if g.shape[0] % n_imp:
+        raise ValueError("impact grid rows must be a multiple of the phase count")
+    out = None
+    for phase in range(n_imp):
+        part = convolve_fft(g[phase::n_imp], r[phase], workers=workers)
+        out = part if out is None else out + part
+    return out
+
+
+def convolve_impact_direct(g_imp: np.ndarray, resp_impact: np.ndarray) -> np.ndarray:
+    """The same sum as literal loops over charge rows, response rows and ticks (small grids)."""
+    r = np.asarray(resp_impact, dtype=np.float64)
+    n_imp, kw, kt = r.shape
+    kc = kw // 2
+    g = np.asarray(g_imp, dtype=np.float64)
+    ni, nt = g.shape
+    nw = ni // n_imp
+    out = np.zeros((nw, nt))
+    for j in range(ni):
+        wq, phase = divmod(j, n_imp)
+        for row in range(kw):
+            w = wq + row - kc
+            if not 0 <= w < nw:
+                continue
+            for tau in range(min(kt, nt)):
+                c = r[phase, row, tau]
+                if c != 0.0:
+                    out[w, tau:] += c * g[j, : nt - tau]
+    return out

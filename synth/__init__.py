@@ -136,6 +136,41 @@ def make_response(kind: str = "bipolar", n_wires: int = 21, n_ticks: int = 200, 
     return out.astype(np.float32)
 
 
+def make_response_impact(kind: str = "bipolar", n_impact: int = 10, n_wires: int = 21, n_ticks: int = 200,
+                         tick_us: float = 0.5, falloff_wires: float = 2.0, shaping_us: float = 1.0) -> np.ndarray:
+    """Per-impact-position responses, float32 [phase][wire offset][tick].
+
+    A charge in sub-bin `phase` of its wire sits (phase + 1/2) / n_impact - 1/2 pitches from
+    the wire centre, so wire offset k sees it at distance d = k - ((phase + 1/2) / n_impact -
+    1/2) pitches.  The field part is that of make_response with |k| replaced by |d| (centre
+    40 + 4|d|, width 4 + 0.5|d|, amplitude exp(-|d|/falloff)), so the response varies smoothly
+    across the pitch and phases mirror each other (phase p at k equals phase n-1-p at -k);
+    the same CR-RC^2 shaping follows.  Computed in FP64.
+    """
+    if n_wires % 2 != 1:
+        raise ValueError("response wire extent must be odd (centre wire at n_wires//2)")
+    tau = np.arange(n_ticks, dtype=np.float64)
+    s = tau * tick_us / shaping_us
+    h = s * s * np.exp(-s)
+    h /= h.sum()
+    out = np.zeros((n_impact, n_wires, n_ticks), dtype=np.float64)
+    for p in range(n_impact):
+        frac = (p + 0.5) / n_impact - 0.5
+        for r in range(n_wires):
+            d = abs((r - n_wires // 2) - frac)
+            c = 40.0 + 4.0 * d
+            b = 4.0 + 0.5 * d
+            g = np.exp(-0.5 * ((tau - c) / b) ** 2) / (b * math.sqrt(2.0 * math.pi))
+            if kind == "bipolar":
+                fr = -((tau - c) / b) * g
+            elif kind == "unipolar":
+                fr = g
+            else:
+                raise ValueError(kind)
+            out[p, r] = np.convolve(fr * math.exp(-d / falloff_wires), h)[:n_ticks]
+    return out.astype(np.float32)
+
+
 # --------------------------------------------------------------------------------------------
 # Depo generators
 # --------------------------------------------------------------------------------------------
