@@ -184,6 +184,29 @@ wct_status_t wct_sim_run_event(wct_sim_t *sim, const wct_depos_t *depos, float *
 wct_status_t wct_sim_run_batch(wct_sim_t *sim, const wct_depos_t *events, int n_events,
                                float *const *waveforms, void *stream);
 
+/* Per-impact-position responses for one plane: the detector response of §2 step 3 resolved
+ * by where the charge sits inside the wire pitch (the transverse grid kept at the patches'
+ * impact resolution instead of folded onto wires).  responses: n_phases HOST descriptors, one
+ * per impact phase (phase p = sub-bin p of a wire, counted from its low-pitch edge), each
+ * [n_wires_resp][n_ticks_resp] with the wire offset k = w - w' (output wire minus the
+ * charge's wire) at row k + n_wires_resp / 2; n_phases must equal the plane's
+ * n_impact_per_pitch and every phase must share the tick extent of the plane's create-time
+ * response (same transform length).  From then on run_event / run_batch / run_host compute
+ * that plane as
+ *     out[w, t] = sum_{w', p} sum_tau G[n_imp w' + p, t - tau] * R_p[w - w' + kc, tau]
+ * (unfused patches scattered onto n_phases phase grids, each transformed and stenciled with
+ * its phase's response into one summed spectrum, one inverse transform); the patch sizes are
+ * queried on the host, so those calls synchronise the stream, and run_batch runs such events
+ * one after the other.  Library memory: n_phases grids of the plane and the phases' spectra.
+ * responses == NULL switches the plane back to the folded mode.  Synchronous. */
+wct_status_t wct_sim_set_impact_responses(wct_sim_t *sim, int plane, const wct_response_t *responses, int n_phases);
+
+/* The impact-mode convolution alone: phase_grids DEVICE float32 [n_phases][n_wires][n_ticks]
+ * (phase-major), waveform DEVICE [n_wires][n_ticks].  WCT_EINVAL if the plane has no impact
+ * responses. */
+wct_status_t wct_sim_convolve_impact(wct_sim_t *sim, int plane, const float *phase_grids, float *waveform,
+                                     void *stream);
+
 /*
  * One event's depos in HOST memory (same fields and units as wct_depos_t).  Pinned
  * (page-locked) arrays let the uploads overlap device work; pageable arrays work too.

@@ -170,6 +170,31 @@ class Simulator:
         self._check(self._lib.wct_sim_run_batch(self._h, evs, len(events), arr, _stream_handle(stream)))
         return wfs
 
+    def set_impact_responses(self, plane: int, responses: Optional[np.ndarray]):
+        """wct_sim_set_impact_responses: per-impact-position responses [phase][wire][tick] for one
+        plane (None: back to the folded mode)."""
+        if responses is None:
+            self._check(self._lib.wct_sim_set_impact_responses(self._h, plane, None, 0))
+            return
+        r = np.ascontiguousarray(responses, dtype=np.float32)
+        if r.ndim != 3:
+            raise ValueError("impact responses must be [phase][wire][tick]")
+        R = (_abi.wct_response_t * r.shape[0])()
+        for p in range(r.shape[0]):
+            R[p] = _abi.wct_response_t(r.shape[1], r.shape[2], r[p].ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+        self._check(self._lib.wct_sim_set_impact_responses(self._h, plane, R, r.shape[0]))
+
+    def convolve_impact(self, plane: int, phase_grids, out=None, stream=None):
+        """wct_sim_convolve_impact: phase grids [phase][wire][tick] (CUDA float32) -> waveform."""
+        pl = self.planes[plane]
+        if not (phase_grids.is_cuda and phase_grids.is_contiguous() and phase_grids.dim() == 3 and
+                tuple(phase_grids.shape[1:]) == (pl.n_wires, pl.n_ticks)):
+            raise ValueError("phase grids must be a contiguous CUDA float32 [phase, n_wires, n_ticks] tensor")
+        wf = self._grid(plane, out)
+        self._check(self._lib.wct_sim_convolve_impact(self._h, plane, _ptr(phase_grids), _ptr(wf),
+                                                      _stream_handle(stream)))
+        return wf
+
     def run_host(self, events: Sequence, outs: Optional[List[List]] = None) -> List[List]:
         """wct_sim_run_host: events whose depos are in host memory (objects with t0, x, y, z, q
         float32 arrays -- numpy arrays or CPU tensors, pinned for overlapped uploads -- and

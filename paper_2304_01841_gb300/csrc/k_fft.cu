@@ -855,7 +855,7 @@ constexpr int kStageRun = 64;                // wires per thread
 
 __global__ void __launch_bounds__(kStageThreads)
 k_wire_stage(const float2 *__restrict__ S, const float2 *__restrict__ Rt, int Fs, int Fu, int n_wires,
-             float2 *__restrict__ T) {
+             float2 *__restrict__ T, int accumulate) {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= Fu) return;
     const int w0 = blockIdx.y * kStageRun;
@@ -885,7 +885,10 @@ k_wire_stage(const float2 *__restrict__ S, const float2 *__restrict__ Rt, int Fs
                     acc[slot].y = fmaf(x.x, r[k].y, fmaf(x.y, r[k].x, acc[slot].y));
                 }
                 const int done = (u + 1) % KW;
-                if (m >= 2 * KC) T[(int64_t)(w0 + m - 2 * KC) * Fs + f] = acc[done];
+                if (m >= 2 * KC) {
+                    float2 *dst = &T[(int64_t)(w0 + m - 2 * KC) * Fs + f];
+                    *dst = accumulate ? cadd(acc[done], *dst) : acc[done];
+                }
                 acc[done] = make_float2(0.f, 0.f);
             }
         }
@@ -911,7 +914,7 @@ constexpr int kRingGroups = 4;
 
 __global__ void __launch_bounds__(kStageFB + 32)
 k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, int Fs, int Fu, int n_wires,
-                 int wires_per_cta, float2 *__restrict__ T, int32_t *status, const ClearJob clear) {
+                 int wires_per_cta, float2 *__restrict__ T, int32_t *status, const ClearJob clear, int accumulate) {
     __shared__ __align__(16) float2 ring[kRingGroups * kGroupRows][kStageFB];
     __shared__ uint64_t full[kRingGroups], empty[kRingGroups];
     const int tid = threadIdx.x;
@@ -1010,7 +1013,12 @@ k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, in
             }
             A = add2(A, A2);
             B = add2(B, B2);
-            if (live && b + j < n_out) T[(size_t)(w0 + b + j) * Fs + f] = make_float2(A.x - B.y, A.y + B.x);
+            if (live && b + j < n_out) {
+                float2 v = make_float2(A.x - B.y, A.y + B.x);
+                float2 *dst = &T[(size_t)(w0 + b + j) * Fs + f];
+                if (accumulate) v = cadd(v, *dst);
+                *dst = v;
+            }
         }
 #pragma unroll
         for (int t = 0; t < 2 * KC; ++t) win[t] = win[t + kOutBlock];
@@ -1266,7 +1274,7 @@ cudaError_t launch_row_c2r(const FFTPlan &p, const float2 *spec, int n_rows, flo
 }
 
 cudaError_t launch_wire_stage(const FFTPlan &p, const float2 *spec, const float2 *resp_spec, int n_wires, float2 *out,
-                              cudaStream_t s, int32_t *status, const ClearJob *clear) {
+                              cudaStream_t s, int32_t *status, const ClearJob *clear, bool accumulate) {
     if (n_wires <= 0) return cudaSuccess;
     const ClearJob job = clear ? *clear : ClearJob{};
     if (aligned16(spec) && (p.Fs % 2) == 0 && (p.Fu % 2) == 0) {
@@ -1293,11 +1301,12 @@ cudaError_t launch_wire_stage(const FFTPlan &p, const float2 *spec, const float2
             }
         }
         dim3 grid(fb, (n_wires + wpc - 1) / wpc);
-        k_wire_stage_tma<<<grid, kStageFB + 32, 0, s>>>(spec, resp_spec, p.Fs, p.Fu, n_wires, wpc, out, status, job);
+        k_wire_stage_tma<<<grid, kStageFB + 32, 0, s>>>(spec, resp_spec, p.Fs, p.Fu, n_wires, wpc, out, status, job,
+                                                        accumulate ? 1 : 0);
         return cudaGetLastError();
     }
     dim3 grid((p.Fu + kStageThreads - 1) / kStageThreads, (n_wires + kStageRun - 1) / kStageRun);
-    k_wire_stage<<<grid, kStageThreads, 0, s>>>(spec, resp_spec, p.Fs, p.Fu, n_wires, out);
+    k_wire_stage<<<grid, kStageThreads, 0, s>>>(spec, resp_spec, p.Fs, p.Fu, n_wires, out, accumulate ? 1 : 0);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && job.grid) {
         k_clear_tiles_fft<<<job.n_tiles < 2 * 152 ? job.n_tiles : 2 * 152, 256, 0, s>>>(job);

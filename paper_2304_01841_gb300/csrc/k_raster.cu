@@ -820,6 +820,37 @@ cudaError_t launch_raster_chunks(const wct_depos_t &d, const PlaneParams &pp, ui
     return cudaGetLastError();
 }
 
+// Impact-resolution scatter: patch bin (tick lo_t + a, impact lo_p + j) of each depo is added
+// to grid[phase][wire][tick] with wire = impact / n_imp, phase = impact % n_imp (one warp per
+// depo, grid-stride; bins off the grid dropped).  patch_desc rows: off, lo_t, lo_p, nt, np.
+__global__ void __launch_bounds__(256)
+k_scatter_phases(int64_t n, const float *__restrict__ patches, const int64_t *__restrict__ desc, int n_imp,
+                 int n_wires, int n_ticks, float *__restrict__ grids) {
+    const int lane = threadIdx.x & 31;
+    const int64_t n_imp_bins = (int64_t)n_wires * n_imp;
+    for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < n;
+         i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int64_t off = desc[5 * i], lo_t = desc[5 * i + 1], lo_p = desc[5 * i + 2];
+        const int nt = (int)desc[5 * i + 3], np = (int)desc[5 * i + 4];
+        for (int idx = lane; idx < nt * np; idx += 32) {
+            const int a = idx / np;
+            const int64_t tick = lo_t + a, j = lo_p + (idx - a * np);
+            if (tick < 0 || tick >= n_ticks || j < 0 || j >= n_imp_bins) continue;
+            const int64_t w = j / n_imp, phase = j - w * n_imp;
+            atomicAdd(&grids[(phase * n_wires + w) * n_ticks + tick], patches[off + idx]);
+        }
+    }
+}
+
+cudaError_t launch_scatter_phases(int64_t n, const float *patches, const int64_t *desc, int n_imp, int n_wires,
+                                  int n_ticks, float *grids, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int64_t want = (n + 7) / 8;
+    const int blocks = (int)(want < 152 * 16 ? want : 152 * 16);
+    k_scatter_phases<<<blocks, 256, 0, s>>>(n, patches, desc, n_imp, n_wires, n_ticks, grids);
+    return cudaGetLastError();
+}
+
 // Size of a plane's flag block: the flags, two counters and the tile list.
 size_t tile_flag_words(const PlaneParams &pp) { return 2 * (size_t)pp.n_tiles_w * pp.n_tiles_t + 2; }
 

@@ -154,8 +154,13 @@ cudaError_t launch_tile_scatter_patches(const int64_t *patch_desc, const float *
 
 cudaError_t launch_row_r2c(const FFTPlan &p, const float *in, int64_t in_stride, int n_in_cols, int n_rows,
                            float2 *spec, cudaStream_t s, int32_t *status = nullptr);
+// accumulate: out += the stencil instead of out = (the per-phase sum of the impact mode)
 cudaError_t launch_wire_stage(const FFTPlan &p, const float2 *spec, const float2 *resp_spec, int n_wires,
-                              float2 *out, cudaStream_t s, int32_t *status = nullptr, const ClearJob *clear = nullptr);
+                              float2 *out, cudaStream_t s, int32_t *status = nullptr, const ClearJob *clear = nullptr,
+                              bool accumulate = false);
+// Impact-resolution scatter of unfused patches onto n_imp phase grids [phase][wire][tick].
+cudaError_t launch_scatter_phases(int64_t n, const float *patches, const int64_t *desc, int n_imp, int n_wires,
+                                  int n_ticks, float *grids, cudaStream_t s);
 cudaError_t launch_row_c2r(const FFTPlan &p, const float2 *spec, int n_rows, float *out, int64_t out_stride,
                            int n_out_cols, cudaStream_t s, int32_t *status = nullptr);
 cudaError_t launch_scale_spectrum(float2 *spec, int64_t n, float scale, cudaStream_t s);

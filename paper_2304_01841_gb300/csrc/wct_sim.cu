@@ -36,6 +36,14 @@ struct PlaneState {
     float2 *resp_spec = nullptr;   // [WCT_MAX_RESPONSE_WIRES][Fs], scaled by 1/M
     int n_tiles = 0;
     int max_tiles_per_depo = 0;
+    // impact mode (per-impact-position responses): one response spectrum per phase, stride
+    // fft_imp.Fs = fft_imp.Fu (the union of the phases' supports), and n_phases phase grids
+    int n_phases = 0;              // 0: folded mode
+    FFTPlan fft_imp{};
+    float2 *resp_imp = nullptr;    // [n_phases][WCT_MAX_RESPONSE_WIRES][fft_imp.Fs], scaled by 1/M
+    size_t resp_imp_bytes = 0;
+    float *phase_grids = nullptr;  // [n_phases][n_wires][n_ticks]
+    size_t phase_grid_bytes = 0;
 };
 
 }  // namespace
@@ -48,6 +56,12 @@ struct wct_sim {
     wct_opts_t opts{};
     // scratch
     float2 *spec = nullptr, *spec2 = nullptr;
+    size_t spec_elems = 0;          // capacity of spec / spec2 (complex elements)
+    // impact mode: unfused patches and their descriptors
+    float *imp_patches = nullptr;
+    int64_t imp_patch_cap = 0;
+    int64_t *imp_desc = nullptr;
+    int64_t imp_desc_cap = 0;
     // Accumulation grids of run_event / run_batch: two sets of every plane's grid, kept all
     // zero between uses: the rasterizer flags the tiles it touches, and once the forward
     // transform has read a grid those tiles are cleared again.
@@ -428,6 +442,111 @@ wct_status_t convolve_plane(wct_sim *s, int plane, const float *grid, float *wf,
     return WCT_OK;
 }
 
+// Time spectra of one response padded to 21 centred rows (scaled by 1/M), row stride full.Fs,
+// in a new device buffer (KW x full.Fs); host copy in *host for the support computation.
+wct_status_t response_spectrum(wct_sim *s, const FFTPlan &full, const wct_response_t &r, float2 **out,
+                               std::vector<float2> &host) {
+    const int KW = WCT_MAX_RESPONSE_WIRES;
+    const int off = (KW - r.n_wires_resp) / 2;
+    std::vector<float> pad((size_t)KW * r.n_ticks_resp, 0.f);
+    for (int row = 0; row < r.n_wires_resp; ++row)
+        std::memcpy(&pad[(size_t)(row + off) * r.n_ticks_resp], r.host_data + (size_t)row * r.n_ticks_resp,
+                    sizeof(float) * r.n_ticks_resp);
+    float *d_resp = nullptr;
+    *out = nullptr;
+    wct_status_t st = dev_alloc(s, (void **)&d_resp, sizeof(float) * pad.size());
+    if (st == WCT_OK) st = dev_alloc(s, (void **)out, sizeof(float2) * (size_t)KW * full.Fs);
+    if (st != WCT_OK) {
+        dev_free(s, d_resp, sizeof(float) * pad.size());
+        return st;
+    }
+    cudaError_t e = cudaMemcpy(d_resp, pad.data(), sizeof(float) * pad.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_row_r2c(full, d_resp, r.n_ticks_resp, r.n_ticks_resp, KW, *out, 0);
+    if (e == cudaSuccess) e = launch_scale_spectrum(*out, (int64_t)KW * full.Fs, 1.0f / (float)full.M, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    dev_free(s, d_resp, sizeof(float) * pad.size());
+    host.assign((size_t)KW * full.Fs, make_float2(0.f, 0.f));
+    if (e == cudaSuccess) e = cudaMemcpy(host.data(), *out, sizeof(float2) * host.size(), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(s, e, "response spectrum");
+    return WCT_OK;
+}
+
+double spectrum_max(const std::vector<float2> &h, const FFTPlan &full) {
+    double m = 0.0;
+    for (int k = 0; k < WCT_MAX_RESPONSE_WIRES; ++k)
+        for (int f = 0; f < full.F; ++f) {
+            const float2 v = h[(size_t)k * full.Fs + f];
+            m = std::max(m, std::sqrt((double)v.x * v.x + (double)v.y * v.y));
+        }
+    return m;
+}
+
+// Free the impact-mode state of one plane.
+void drop_impact(wct_sim *s, PlaneState &ps) {
+    dev_free(s, ps.resp_imp, ps.resp_imp_bytes);
+    dev_free(s, ps.phase_grids, ps.phase_grid_bytes);
+    ps.resp_imp = nullptr;
+    ps.phase_grids = nullptr;
+    ps.resp_imp_bytes = ps.phase_grid_bytes = 0;
+    ps.n_phases = 0;
+}
+
+// The impact-mode hot path of one plane: unfused patches (sized by a synchronous query),
+// scattered onto the phase grids, each grid transformed and stenciled with its phase's
+// response into one summed spectrum, one inverse transform.
+wct_status_t run_plane_impact(wct_sim *s, int p, const wct_depos_t *d, float *wf, cudaStream_t cs, int slot) {
+    PlaneState &ps = s->planes[p];
+    const int nw = ps.g.n_wires, nt = ps.g.n_ticks;
+    const int64_t n = d->n;
+    wct_status_t st = WCT_OK;
+    if (n > s->imp_desc_cap) {
+        cudaStreamSynchronize(cs);
+        dev_free(s, s->imp_desc, sizeof(int64_t) * 5 * (size_t)s->imp_desc_cap);
+        s->imp_desc = nullptr;
+        s->imp_desc_cap = 0;
+        if ((st = dev_alloc(s, (void **)&s->imp_desc, sizeof(int64_t) * 5 * (size_t)n))) return st;
+        s->imp_desc_cap = n;
+    }
+    mark(s, slot, 0, cs);
+    cudaError_t e = cudaMemsetAsync(ps.phase_grids, 0, ps.phase_grid_bytes, cs);
+    if (e != cudaSuccess) return cuda_fail(s, e, "phase grid clear");
+    mark(s, slot, 1, cs);
+    int64_t total = 0;
+    st = wct_sim_rasterize(s, p, d, s->imp_patches, s->imp_patch_cap, s->imp_desc, &total, cs);
+    if ((st == WCT_OK || st == WCT_EINVAL) && total > s->imp_patch_cap) {
+        // the patch buffer was too small: grow it and rasterize again
+        cudaStreamSynchronize(cs);
+        dev_free(s, s->imp_patches, sizeof(float) * (size_t)s->imp_patch_cap);
+        s->imp_patches = nullptr;
+        s->imp_patch_cap = 0;
+        const int64_t cap = std::max<int64_t>(total, 1 << 20);
+        if ((st = dev_alloc(s, (void **)&s->imp_patches, sizeof(float) * (size_t)cap))) return st;
+        s->imp_patch_cap = cap;
+        st = wct_sim_rasterize(s, p, d, s->imp_patches, s->imp_patch_cap, s->imp_desc, &total, cs);
+    }
+    if (st) return st;
+    e = launch_scatter_phases(n, s->imp_patches, s->imp_desc, ps.n_phases, nw, nt, ps.phase_grids, cs);
+    if (e != cudaSuccess) return cuda_fail(s, e, "phase scatter");
+    s->launches += n > 0 ? 1 : 0;
+    mark(s, slot, 2, cs);
+    const int KW = WCT_MAX_RESPONSE_WIRES;
+    for (int ph = 0; ph < ps.n_phases; ++ph) {
+        e = launch_row_r2c(ps.fft_imp, ps.phase_grids + (size_t)ph * nw * nt, nt, nt, nw, s->spec, cs, s->status);
+        if (e == cudaSuccess)
+            e = launch_wire_stage(ps.fft_imp, s->spec, ps.resp_imp + (size_t)ph * KW * ps.fft_imp.Fs, nw, s->spec2, cs,
+                                  s->status, nullptr, ph > 0);
+        if (e != cudaSuccess) return cuda_fail(s, e, "phase transform");
+        s->launches += 2;
+    }
+    mark(s, slot, 3, cs);
+    mark(s, slot, 4, cs);
+    e = launch_row_c2r(ps.fft_imp, s->spec2, nw, wf, nt, nt, cs, s->status);
+    if (e != cudaSuccess) return cuda_fail(s, e, "row c2r");
+    s->launches += 1;
+    mark(s, slot, 5, cs);
+    return WCT_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -606,6 +725,7 @@ wct_status_t wct_sim_create(const wct_plane_t *planes, int n_planes, const wct_r
     }
     if (st == WCT_OK) st = dev_alloc(s, (void **)&s->spec, sizeof(float2) * spec_elems);
     if (st == WCT_OK) st = dev_alloc(s, (void **)&s->spec2, sizeof(float2) * spec_elems);
+    s->spec_elems = spec_elems;
     for (int p = 0; p < n_planes; ++p) {
         s->grid_off[p + 1] = s->grid_off[p] + (size_t)s->planes[p].g.n_wires * s->planes[p].g.n_ticks;
         s->flag_off[p + 1] = s->flag_off[p] + tile_flag_words(s->planes[p].pp);
@@ -724,6 +844,10 @@ wct_status_t wct_sim_run_event(wct_sim_t *s, const wct_depos_t *d, float *const 
     for (int p = 0; p < s->n_planes; ++p) {
         // accumulate into the library grid (all zero), which the forward transform clears
         // again as it reads it; the inverse transform writes the caller's waveform
+        if (s->planes[p].n_phases > 0) {
+            if ((st = run_plane_impact(s, p, d, wfs[p], cs, acquire_slot(s)))) return st;
+            continue;
+        }
         float *grid = s->grids[0] + s->grid_off[p];
         uint32_t *flags = s->tile_flags[0] + s->flag_off[p];
         const int slot = acquire_slot(s);
@@ -847,6 +971,15 @@ wct_status_t wct_sim_run_batch(wct_sim_t *s, const wct_depos_t *events, int n_ev
     }
     if (n_events == 0) return WCT_OK;
     cudaStream_t cs = (cudaStream_t)stream;
+    for (int p = 0; p < s->n_planes; ++p)
+        if (s->planes[p].n_phases > 0) {
+            // impact mode sizes its patches on the host: events one after the other
+            for (int e = 0; e < n_events; ++e) {
+                const wct_status_t st = wct_sim_run_event(s, &events[e], wfs + (size_t)e * s->n_planes, stream);
+                if (st) return st;
+            }
+            return WCT_OK;
+        }
     // graph key: everything the recorded launches depend on
     std::vector<uint64_t> key;
     key.reserve((size_t)n_events * (7 + s->n_planes) + 1);
@@ -1000,6 +1133,96 @@ wct_status_t wct_sim_run_host(wct_sim_t *s, const wct_host_depos_t *events, int 
         return cuda_fail(s, err, "host pipeline");
     }
     return wct_sim_sync(s, comp);
+}
+
+wct_status_t wct_sim_set_impact_responses(wct_sim_t *s, int plane, const wct_response_t *responses, int n_phases) {
+    wct_status_t st = plane_check(s, plane);
+    if (st) return st;
+    PlaneState &ps = s->planes[plane];
+    cudaDeviceSynchronize();                           // nothing may still use the old state
+    drop_impact(s, ps);
+    if (!responses) return WCT_OK;                     // back to the folded mode
+    if (n_phases != ps.g.n_impact_per_pitch) return fail(s, WCT_EINVAL, "n_phases must equal n_impact_per_pitch");
+    int kt = 0;
+    for (int ph = 0; ph < n_phases; ++ph) {
+        const wct_response_t &r = responses[ph];
+        if (!r.host_data || r.n_wires_resp < 1 || (r.n_wires_resp & 1) == 0 || r.n_wires_resp > WCT_MAX_RESPONSE_WIRES ||
+            r.n_ticks_resp < 1 || r.n_ticks_resp > 65536 || (ph > 0 && r.n_ticks_resp != kt))
+            return fail(s, WCT_EINVAL, "bad impact response (odd wire extent <= 21, equal tick extents)");
+        kt = r.n_ticks_resp;
+    }
+    FFTPlan full{};
+    if (!plan_fft(ps.g.n_ticks, kt, full)) return fail(s, WCT_EINVAL, "no FFT plan for this tick count (too long)");
+    full.tw = ps.fft.tw;                               // same transform length as the plane's
+    full.rtw = ps.fft.rtw;
+    if (full.M != ps.fft.M) return fail(s, WCT_EINVAL, "impact responses need the plane's transform length");
+    // spectra of every phase, the common support, then one packed buffer
+    const int KW = WCT_MAX_RESPONSE_WIRES;
+    std::vector<float2 *> dspec(n_phases, nullptr);
+    std::vector<std::vector<float2>> host(n_phases);
+    double gmax = 0.0;
+    for (int ph = 0; ph < n_phases && st == WCT_OK; ++ph) {
+        st = response_spectrum(s, full, responses[ph], &dspec[ph], host[ph]);
+        if (st == WCT_OK) gmax = std::max(gmax, spectrum_max(host[ph], full));
+    }
+    int last = 0;
+    for (int ph = 0; ph < n_phases && st == WCT_OK; ++ph)
+        last = std::max(last, response_support_last(responses[ph], 2 * full.M, full.F, 0x1p-23 * gmax * (double)full.M));
+    const int Fu = std::min(full.Fs, (last + 2) & ~1);
+    if (st == WCT_OK) {
+        ps.resp_imp_bytes = sizeof(float2) * (size_t)n_phases * KW * Fu;
+        st = dev_alloc(s, (void **)&ps.resp_imp, ps.resp_imp_bytes);
+    }
+    for (int ph = 0; ph < n_phases && st == WCT_OK; ++ph) {
+        const cudaError_t e = cudaMemcpy2D(ps.resp_imp + (size_t)ph * KW * Fu, sizeof(float2) * Fu, dspec[ph],
+                                           sizeof(float2) * full.Fs, sizeof(float2) * Fu, KW, cudaMemcpyDeviceToDevice);
+        if (e != cudaSuccess) st = cuda_fail(s, e, "impact response spectra");
+    }
+    for (int ph = 0; ph < n_phases; ++ph) dev_free(s, dspec[ph], sizeof(float2) * (size_t)KW * full.Fs);
+    ps.fft_imp = full;
+    ps.fft_imp.Fs = ps.fft_imp.Fu = Fu;
+    // spectrum scratch must hold n_wires x Fu
+    const size_t need = (size_t)ps.g.n_wires * Fu;
+    if (st == WCT_OK && need > s->spec_elems) {
+        dev_free(s, s->spec, sizeof(float2) * s->spec_elems);
+        dev_free(s, s->spec2, sizeof(float2) * s->spec_elems);
+        s->spec = s->spec2 = nullptr;
+        s->spec_elems = 0;
+        st = dev_alloc(s, (void **)&s->spec, sizeof(float2) * need);
+        if (st == WCT_OK) st = dev_alloc(s, (void **)&s->spec2, sizeof(float2) * need);
+        if (st == WCT_OK) s->spec_elems = need;
+    }
+    if (st == WCT_OK) {
+        ps.phase_grid_bytes = sizeof(float) * (size_t)n_phases * ps.g.n_wires * ps.g.n_ticks;
+        st = dev_alloc(s, (void **)&ps.phase_grids, ps.phase_grid_bytes);
+    }
+    if (st) {
+        drop_impact(s, ps);
+        return st;
+    }
+    ps.n_phases = n_phases;
+    return WCT_OK;
+}
+
+wct_status_t wct_sim_convolve_impact(wct_sim_t *s, int plane, const float *phase_grids, float *waveform, void *stream) {
+    wct_status_t st = plane_check(s, plane);
+    if (st) return st;
+    PlaneState &ps = s->planes[plane];
+    if (ps.n_phases == 0) return fail(s, WCT_EINVAL, "plane has no impact responses");
+    if (!phase_grids || !waveform) return fail(s, WCT_EINVAL, "phase_grids and waveform are required");
+    cudaStream_t cs = (cudaStream_t)stream;
+    const int nw = ps.g.n_wires, nt = ps.g.n_ticks, KW = WCT_MAX_RESPONSE_WIRES;
+    cudaError_t e = cudaSuccess;
+    for (int ph = 0; ph < ps.n_phases && e == cudaSuccess; ++ph) {
+        e = launch_row_r2c(ps.fft_imp, phase_grids + (size_t)ph * nw * nt, nt, nt, nw, s->spec, cs, s->status);
+        if (e == cudaSuccess)
+            e = launch_wire_stage(ps.fft_imp, s->spec, ps.resp_imp + (size_t)ph * KW * ps.fft_imp.Fs, nw, s->spec2, cs,
+                                  s->status, nullptr, ph > 0);
+    }
+    if (e == cudaSuccess) e = launch_row_c2r(ps.fft_imp, s->spec2, nw, waveform, nt, nt, cs, s->status);
+    if (e != cudaSuccess) return cuda_fail(s, e, "convolve impact");
+    s->launches += 2 * ps.n_phases + 1;
+    return WCT_OK;
 }
 
 wct_status_t wct_sim_sync(wct_sim_t *s, void *stream) {
