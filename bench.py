@@ -290,6 +290,52 @@ def measure_batch(n_events=64, reps=5):
             "depos_per_s_batched": reps * sum(e.n for e in evs) / t_batch}
 
 
+def measure_impact(n_events=4, reps=2):
+    """Impact mode (per-impact-position responses, 10 phases) on the uboone_plane workload:
+    run_event per event (unfused patches, 10 phase grids, 10 transforms + stencils, one inverse
+    transform), CUDA events around reps x n_events events, against the folded mode."""
+    import torch
+    import paper_2304_01841_gb300 as pkg
+    import synth
+    wl = synth.workload(WORKLOAD)
+    pl = wl.planes[0]
+    evs = [pkg.DeviceDepos.from_host(wl.depos(seed=wl.seed + 100 + e, event_id=500 + e)) for e in range(n_events)]
+    sim = pkg.Simulator(wl.planes, wl.responses(), wl.diffusion)
+    out = torch.empty((pl.n_wires, pl.n_ticks), dtype=torch.float32, device="cuda")
+    st = torch.cuda.current_stream()
+
+    def timed():
+        for d in evs[:2]:
+            sim.run_event(d, [out])
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for _ in range(reps):
+            for d in evs:
+                sim.run_event(d, [out])
+        b.record(st)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1000.0 / (reps * n_events)
+
+    t_folded = timed()
+    sim.set_impact_responses(0, synth.make_response_impact(pl.response_kind, n_impact=pl.n_impact_per_pitch))
+    t_impact = timed()
+    sim.set_timing(True)
+    for d in evs:
+        sim.run_event(d, [out])
+    sim.sync()
+    stages = sim.stage_times()
+    sim.set_timing(False)
+    sim.close()
+    n = evs[0].n
+    return {"workload": f"{WORKLOAD}, 10 per-impact-position responses (21 x 200 each)",
+            "events_per_s": 1.0 / t_impact, "depos_per_s": n / t_impact, "ms_per_event": 1e3 * t_impact,
+            "folded_ms_per_event": 1e3 * t_folded,
+            "stages_us": {"patches_rasterize_scatter": round(stages["raster_scatter"] + stages["prep_binning"], 1),
+                          "phase_transforms_and_stencils": round(stages["row_r2c"], 1),
+                          "inverse_transform": round(stages["row_c2r"], 1)}}
+
+
 def measure_serving(n_events=120, loads=(0.5, 0.8, 0.95)):
     """Served: APA-like planes (800/800/960 x 6000), heavy-tailed depo counts (90% 5k-50k,
     10% 1M-3M), open-loop Poisson arrivals at fractions of the measured capacity."""
@@ -513,6 +559,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_extras:
         extras["batch"] = measure_batch()
         extras["serving"] = measure_serving()
+        extras["impact_mode"] = measure_impact()
 
     if rank == 0:
         line = {
