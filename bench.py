@@ -336,6 +336,56 @@ def measure_impact(n_events=4, reps=2):
                           "inverse_transform": round(stages["row_c2r"], 1)}}
 
 
+def measure_scan_free(reps=5):
+    """Unfused rasterize on the uboone_plane event: the prefix-sum version (size query, host
+    synchronisation, packed patches) against the scan-free one (a fixed slot per depo sized for
+    the largest window at the maximum drift), as the paper's OpenMP port does."""
+    import torch
+    import paper_2304_01841_gb300 as pkg
+    import synth
+    wl = synth.workload(WORKLOAD)
+    pl = wl.planes[0]
+    d = wl.depos()
+    dd = pkg.DeviceDepos.from_host(d)
+    sim = pkg.Simulator(wl.planes, wl.responses(), wl.diffusion)
+    slot = pkg.patch_slot_bins(pl, wl.diffusion, float(d.x.max()))
+    desc, patches = sim.rasterize(0, dd)
+    total = patches.numel()
+    desc_f, patches_f = sim.rasterize_fixed(0, dd, slot)
+    st = torch.cuda.current_stream()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for _ in range(reps):
+            fn()
+        b.record(st)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) * 1e3 / reps
+
+    import ctypes
+    total_c = ctypes.c_int64()
+    ds = dd.c_struct()
+    lib, h = sim._lib, sim._h
+
+    def scanned():   # size query + patches, as a caller of the scanned API does it
+        lib.wct_sim_rasterize(h, 0, ctypes.byref(ds), None, 0, desc.data_ptr(), ctypes.byref(total_c), None)
+        lib.wct_sim_rasterize(h, 0, ctypes.byref(ds), patches.data_ptr(), total, desc.data_ptr(),
+                              ctypes.byref(total_c), None)
+
+    def fixed():
+        lib.wct_sim_rasterize_fixed(h, 0, ctypes.byref(ds), patches_f.data_ptr(), slot, desc_f.data_ptr(), None)
+
+    t_scan, t_fixed = timed(scanned), timed(fixed)
+    sim.sync()
+    sim.close()
+    return {"workload": f"{WORKLOAD}, unfused rasterize with fluctuation", "slot_bins": slot,
+            "scanned_us": round(t_scan, 1), "scan_free_us": round(t_fixed, 1),
+            "scanned_patch_bytes": 4 * total, "scan_free_patch_bytes": 4 * d.n * slot}
+
+
 def measure_serving(n_events=120, loads=(0.5, 0.8, 0.95)):
     """Served: APA-like planes (800/800/960 x 6000), heavy-tailed depo counts (90% 5k-50k,
     10% 1M-3M), open-loop Poisson arrivals at fractions of the measured capacity."""
@@ -560,6 +610,7 @@ def main():
         extras["batch"] = measure_batch()
         extras["serving"] = measure_serving()
         extras["impact_mode"] = measure_impact()
+        extras["scan_free_rasterize"] = measure_scan_free()
 
     if rank == 0:
         line = {

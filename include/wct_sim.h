@@ -149,6 +149,16 @@ wct_status_t wct_sim_rasterize(wct_sim_t *sim, int plane, const wct_depos_t *dep
                                int64_t patches_capacity, int64_t *patch_desc, int64_t *total_bins,
                                void *stream);
 
+/* Scan-free variant of wct_sim_rasterize (the paper's OpenMP port, §3.3, drops the prefix sum
+ * for a fixed patch slot per depo at a small memory cost): depo i's patch, row-major
+ * [tick][impact], is written at patches + i * slot_bins and patch_desc row i gets offset
+ * i * slot_bins, so there is no size query and no host synchronisation.  patches: DEVICE
+ * float32 of n * slot_bins; patch_desc: DEVICE int64 [n][5] as for wct_sim_rasterize.
+ * 1 <= slot_bins <= 128 * 512.  A depo whose window holds more than slot_bins bins is skipped
+ * (its descriptor row reads nt = np = 0) and reported as WCT_EINVAL at the next sync. */
+wct_status_t wct_sim_rasterize_fixed(wct_sim_t *sim, int plane, const wct_depos_t *depos, float *patches,
+                                     int64_t slot_bins, int64_t *patch_desc, void *stream);
+
 /*
  * Scatter-add onto the plane grid (§2 step 2).  grid: DEVICE float32 [n_wires][n_ticks],
  * fully overwritten (no need to clear it).  With patches == NULL the patches are computed
@@ -233,6 +243,16 @@ typedef struct {
  * wct_sim_run_event for each event.  WCT_EINVAL for a NULL or negative argument. */
 wct_status_t wct_sim_run_host(wct_sim_t *sim, const wct_host_depos_t *events, int n_events,
                               float *const *waveforms);
+
+/* Drift attenuation by the electron lifetime, the step before the rasterization of §2: every
+ * depo's charge q becomes the surviving charge of Binomial(q, p), p = exp(-t_d / lifetime),
+ * t_d = x / v_drift: its mean q p, or (fluctuate != 0) the normal approximation
+ * max(0, q p + sqrt(q p (1 - p)) z) with z drawn from the Philox stream at counter
+ * (depo index, 0, 0, 0xFF << 24 | event id) under the seed's key, so every plane sees the same
+ * surviving charge.  lifetime_us <= 0 or infinite switches it off (the default).  Applies to
+ * every later call of this handle; synchronises the device; drops recorded batch graphs.
+ * WCT_EINVAL for a NaN lifetime. */
+wct_status_t wct_sim_set_lifetime(wct_sim_t *sim, double lifetime_us, int32_t fluctuate);
 
 /* Synchronise `stream` and return (then clear) the device status word: WCT_OK, or the
  * first device-side error since the last sync (WCT_EINVAL for invalid depos). */

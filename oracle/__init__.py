@@ -16,6 +16,8 @@ Parity status of each function (what pins it; see tests/test_oracle_*.py):
   scatter              pinned: charge conservation, hand-built folding cases.
   convolve             pinned: delta response = identity, delta grid = placed response,
                        direct quadruple loop, no circular wrap, linearity.
+  drift attenuation    pinned: closed form q exp(-t_d / lifetime); fluctuated mean and
+                       variance of the binomial; the same charge for every plane.
   impact-resolution    pinned: phase-independent responses reduce to the folded path,
   scatter / convolve   FFT form = literal loops, a single sub-bin charge places its phase's
                        response, the impact grid folds to the wire grid.
@@ -224,3 +226,35 @@ def simulate_plane_impact(depos, plane, diff, resp_impact, plane_index: int = 0)
     g = scatter_impact(pt, plane)
     wf = convolve_impact(g, resp_impact)
     return pt, g, wf
+
+
+def absorption_normals(seed: int, n: int, event_id: int) -> np.ndarray:
+    """z for the drift attenuation of depos 0..n-1: the first Box-Muller normal of Philox4x32-10
+    at counter (depo, 0, 0, 0xFF << 24 | event id mod 2^24) under the seed's key, in FP64
+    (u = (word + 1/2) 2^-32, z = sqrt(-2 ln u_0) cos(2 pi u_1))."""
+    ctr = np.zeros((n, 4), dtype=np.uint32)
+    ctr[:, 0] = np.arange(n, dtype=np.uint64).astype(np.uint32)
+    ctr[:, 3] = np.uint32((0xFF << 24) | (int(event_id) & 0xFFFFFF))
+    w = philox4x32_10(ctr, (int(seed) & 0xFFFFFFFF, (int(seed) >> 32) & 0xFFFFFFFF)).astype(np.float64)
+    u0 = (w[:, 0] + 0.5) * 2.0 ** -32
+    u1 = (w[:, 1] + 0.5) * 2.0 ** -32
+    return np.sqrt(-2.0 * np.log(u0)) * np.cos(2.0 * np.pi * u1)
+
+
+def drift_depos(depos, diff, lifetime_us: float, fluctuate: bool = False):
+    """The drift step before rasterization: each depo's charge attenuated by the electron
+    lifetime, surviving fraction p = exp(-t_d / lifetime), t_d = x / v.  Without fluctuation the
+    mean q p; with it the normal approximation to Binomial(q, p), max(0, q p + sqrt(q p (1-p)) z)
+    (absorption_normals).  FP64, returned as a copy of the depos with the new charges (float32,
+    the input precision of the later steps)."""
+    import copy
+    x = depos.x.astype(np.float64)
+    q = depos.q.astype(np.float64)
+    p = np.exp(-(x / diff.v_drift_mm_us) / lifetime_us)
+    m = q * p
+    if fluctuate:
+        z = absorption_normals(diff.seed, depos.n, depos.event_id)
+        m = np.maximum(m + np.sqrt(m * (1.0 - p)) * z, 0.0)
+    out = copy.copy(depos)
+    out.q = m.astype(np.float32)
+    return out

@@ -139,6 +139,17 @@ class Simulator:
                                                 _ptr(desc), ctypes.byref(total), sh))
         return desc[: depos.n], patches[: total.value]
 
+    def rasterize_fixed(self, plane: int, depos: DeviceDepos, slot_bins: int, stream=None):
+        """wct_sim_rasterize_fixed: scan-free patches, depo i at offset i * slot_bins; returns
+        (patch_desc [n,5] int64, patches float32 [n * slot_bins])."""
+        torch = _torch()
+        desc = torch.empty((max(depos.n, 1), 5), dtype=torch.int64, device="cuda")
+        patches = torch.empty(max(depos.n * int(slot_bins), 1), dtype=torch.float32, device="cuda")
+        ds = depos.c_struct()
+        self._check(self._lib.wct_sim_rasterize_fixed(self._h, plane, ctypes.byref(ds), _ptr(patches), int(slot_bins),
+                                                      _ptr(desc), _stream_handle(stream)))
+        return desc[: depos.n], patches
+
     def scatter(self, plane: int, depos: DeviceDepos, patches=None, patch_desc=None, out=None, stream=None):
         """wct_sim_scatter: fused (patches None) or from given patches; returns the grid."""
         grid = self._grid(plane, out)
@@ -169,6 +180,10 @@ class Simulator:
         evs = (_abi.wct_depos_t * max(len(events), 1))(*[e.c_struct() for e in events])
         self._check(self._lib.wct_sim_run_batch(self._h, evs, len(events), arr, _stream_handle(stream)))
         return wfs
+
+    def set_lifetime(self, lifetime_us: float, fluctuate: bool = False):
+        """wct_sim_set_lifetime: electron-lifetime attenuation of the drifting charge (<= 0: off)."""
+        self._check(self._lib.wct_sim_set_lifetime(self._h, float(lifetime_us), int(bool(fluctuate))))
 
     def set_impact_responses(self, plane: int, responses: Optional[np.ndarray]):
         """wct_sim_set_impact_responses: per-impact-position responses [phase][wire][tick] for one
@@ -273,3 +288,16 @@ def philox4x32_10(ctr, seed: int, stream=None):
     if rc != 0:
         raise WctError(rc, "wct_philox4x32_10 failed")
     return out
+
+
+def patch_slot_bins(plane, diffusion, x_max_mm: float) -> int:
+    """Bins of the largest window a depo drifting at most x_max_mm can have (the fixed slot of
+    the scan-free rasterize): per axis floor(2 n sigma_max / bin) + 2 bins, with sigma from the
+    drift / diffusion relations of the window (sigma_L,T = sqrt(2 D t_d), t_d = x / v)."""
+    import math
+    td = x_max_mm / diffusion.v_drift_mm_us
+    s_t = math.sqrt(2.0 * diffusion.DL_cm2_s * 1e-4 * td) / diffusion.v_drift_mm_us / plane.tick_us
+    s_p = math.sqrt(2.0 * diffusion.DT_cm2_s * 1e-4 * td) / (plane.pitch_mm / plane.n_impact_per_pitch)
+    nt = int(math.floor(2.0 * diffusion.nsigma * s_t)) + 2
+    n_p = int(math.floor(2.0 * diffusion.nsigma * s_p)) + 2
+    return nt * n_p

@@ -58,6 +58,8 @@ EXPORTS = {
     "wct_sim_destroy": ([c_vp], ctypes.c_int),
     "wct_sim_rasterize": ([c_vp, ctypes.c_int, ctypes.POINTER(wct_depos_t), c_vp, c_i64, c_vp,
                            ctypes.POINTER(c_i64), c_vp], ctypes.c_int),
+    "wct_sim_rasterize_fixed": ([c_vp, ctypes.c_int, ctypes.POINTER(wct_depos_t), c_vp, c_i64, c_vp, c_vp],
+                                ctypes.c_int),
     "wct_sim_scatter": ([c_vp, ctypes.c_int, ctypes.POINTER(wct_depos_t), c_vp, c_vp, c_vp, c_vp], ctypes.c_int),
     "wct_sim_convolve": ([c_vp, ctypes.c_int, c_vp, c_vp, c_vp], ctypes.c_int),
     "wct_sim_run_event": ([c_vp, ctypes.POINTER(wct_depos_t), ctypes.POINTER(c_vp), c_vp], ctypes.c_int),
@@ -66,6 +68,7 @@ EXPORTS = {
     "wct_sim_set_impact_responses": ([c_vp, ctypes.c_int, ctypes.POINTER(wct_response_t), ctypes.c_int], ctypes.c_int),
     "wct_sim_convolve_impact": ([c_vp, ctypes.c_int, c_vp, c_vp, c_vp], ctypes.c_int),
     "wct_sim_run_host": ([c_vp, ctypes.POINTER(wct_host_depos_t), ctypes.c_int, ctypes.POINTER(c_vp)], ctypes.c_int),
+    "wct_sim_set_lifetime": ([c_vp, ctypes.c_double, c_i32], ctypes.c_int),
     "wct_sim_sync": ([c_vp, c_vp], ctypes.c_int),
     "wct_sim_plane_info": ([c_vp, ctypes.c_int, ctypes.POINTER(c_i64)], ctypes.c_int),
     "wct_sim_set_timing": ([c_vp, ctypes.c_int], ctypes.c_int),

@@ -42,12 +42,13 @@ __global__ void __launch_bounds__(kPrepThreads)
 k_prep(const float *__restrict__ t0, const float *__restrict__ x, const float *__restrict__ y,
        const float *__restrict__ z, const float *__restrict__ q, int64_t n, PlaneParams pp,
        DepoDesc *__restrict__ desc, int32_t *__restrict__ tile_count, int64_t *__restrict__ patch_size,
-       int32_t *status) {
+       int32_t *status, uint32_t event_lo) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     DepoDesc d;
     const bool ok = depo_window(t0[i], x[i], y[i], z[i], q[i], pp, d);
     if (!ok) set_status(status, ST_EINVAL);
+    else d.q = drift_absorb(d.q, x[i], (uint32_t)i, event_lo, pp);
     desc[i] = d;
     if (patch_size) patch_size[i] = (int64_t)d.nt * (int64_t)d.np;
     if (tile_count) {
@@ -211,7 +212,8 @@ cudaError_t launch_prep(const wct_depos_t &d, const PlaneParams &pp, DepoDesc *d
                         int64_t *patch_size, int32_t *status, cudaStream_t s) {
     if (d.n <= 0) return cudaSuccess;
     k_prep<<<blocks_for(d.n, kPrepThreads), kPrepThreads, 0, s>>>(d.t0_us, d.x_mm, d.y_mm, d.z_mm, d.q_e, d.n, pp,
-                                                                   desc, tile_count, patch_size, status);
+                                                                   desc, tile_count, patch_size, status,
+                                                                   (uint32_t)d.event_id);
     return cudaGetLastError();
 }
 

@@ -219,6 +219,7 @@ __device__ __forceinline__ void raster_chunk(ChunkSmem &S, const float *__restri
         const int64_t i = c0 + tid;
         DepoDesc d;
         if (!depo_window(t0[i], x[i], y[i], z[i], q[i], pp, d)) set_status(status, ST_EINVAL);
+        else d.q = drift_absorb(d.q, x[i], (uint32_t)i, event_lo, pp);
         S.d[tid] = d;
         int wl = 0, nw = 0;
         if (d.nt > 0) {
@@ -395,6 +396,7 @@ __device__ __forceinline__ void raster_warp(WarpSmem &S, const float *__restrict
         const int64_t i = c0 + lane;
         DepoDesc d;
         if (!depo_window(t0[i], x[i], y[i], z[i], q[i], pp, d)) set_status(status, ST_EINVAL);
+        else d.q = drift_absorb(d.q, x[i], (uint32_t)i, event_lo, pp);
         S.d[lane] = d;
         int wl = 0, nw = 0;
         if (d.nt > 0) {
@@ -647,7 +649,7 @@ __device__ __forceinline__ float bin_normal(const PlaneParams &pp, uint32_t depo
 
 __global__ void __launch_bounds__(kPatchWarps * 32)
 k_rasterize_patches(int64_t n, const DepoDesc *__restrict__ desc, const int64_t *__restrict__ offsets,
-                    PlaneParams pp, uint32_t event_lo, float *__restrict__ patches) {
+                    int64_t slot, PlaneParams pp, uint32_t event_lo, float *__restrict__ patches) {
     __shared__ float wbuf[kPatchWarps][kWBuf];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float *wt = wbuf[warp];
@@ -660,7 +662,7 @@ k_rasterize_patches(int64_t n, const DepoDesc *__restrict__ desc, const int64_t 
         if (nt == 0) continue;
         axis_weights(wt, nt, d.mu_t, d.inv_t, lane);
         axis_weights(wp, np, d.mu_p, d.inv_p, lane);
-        float *out = patches + offsets[di];
+        float *out = patches + (offsets ? offsets[di] : di * slot);
         const int bins = nt * np;
         const float q = d.q;
         if (!pp.fluctuate) {
@@ -690,12 +692,12 @@ k_rasterize_patches(int64_t n, const DepoDesc *__restrict__ desc, const int64_t 
 }
 
 __global__ void k_write_patch_desc(int64_t n, const DepoDesc *__restrict__ desc, const int64_t *__restrict__ offsets,
-                                   int64_t *__restrict__ pd) {
+                                   int64_t slot, int64_t *__restrict__ pd) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const DepoDesc d = desc[i];
     int64_t *e = pd + 5 * i;
-    e[0] = offsets[i];
+    e[0] = offsets ? offsets[i] : i * slot;
     e[1] = d.lo_t;
     e[2] = d.lo_p;
     e[3] = d.nt;
@@ -869,16 +871,37 @@ ClearJob clear_job(float *grid, uint32_t *flags, const PlaneParams &pp) {
 
 
 cudaError_t launch_rasterize_patches(int64_t n, const DepoDesc *desc, const int64_t *offsets, const PlaneParams &pp,
-                                     uint32_t event_lo, float *patches, int64_t *patch_desc, cudaStream_t s) {
+                                     uint32_t event_lo, float *patches, int64_t *patch_desc, cudaStream_t s,
+                                     int64_t slot) {
     if (n <= 0) return cudaSuccess;
     if (patch_desc) {
-        k_write_patch_desc<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, desc, offsets, patch_desc);
+        k_write_patch_desc<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, desc, offsets, slot, patch_desc);
     }
     if (patches) {
         int64_t blocks = (n + kPatchWarps - 1) / kPatchWarps;
         if (blocks > 152 * 16) blocks = 152 * 16;
-        k_rasterize_patches<<<(unsigned)blocks, kPatchWarps * 32, 0, s>>>(n, desc, offsets, pp, event_lo, patches);
+        k_rasterize_patches<<<(unsigned)blocks, kPatchWarps * 32, 0, s>>>(n, desc, offsets, slot, pp, event_lo,
+                                                                          patches);
     }
+    return cudaGetLastError();
+}
+
+// Scan-free slots: a depo whose window holds more than `slot` bins is reported and emptied
+// (nt = np = 0), so neither the patch kernel nor a scatter touches it.
+__global__ void k_fit_slots(int64_t n, DepoDesc *__restrict__ desc, int64_t slot, int32_t *status) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    DepoDesc d = desc[i];
+    if ((int64_t)d.nt * d.np > slot) {
+        set_status(status, ST_EINVAL);
+        d.nt = d.np = 0;
+        desc[i] = d;
+    }
+}
+
+cudaError_t launch_fit_slots(int64_t n, DepoDesc *desc, int64_t slot, int32_t *status, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_fit_slots<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, desc, slot, status);
     return cudaGetLastError();
 }
 

@@ -79,6 +79,22 @@ __device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b) {
     return make_float2(-r * sfu_cos(t), -r * sfu_sin(t));
 }
 
+// Drift attenuation by the electron lifetime (the step before rasterization): the surviving
+// charge is Binomial(q, p) with p = exp(-t_d / lifetime), t_d = x / v; without fluctuation its
+// mean q p, with fluctuation its normal approximation max(0, q p + sqrt(q p (1 - p)) z), z the
+// first Box-Muller normal of Philox(depo, 0, 0, 0xFF << 24 | event) under the seed's key (plane
+// field 0xFF: no bin of any plane uses it, and every plane sees the same surviving charge).
+__device__ __forceinline__ float drift_absorb(float q, float x, uint32_t depo, uint32_t event_lo,
+                                              const PlaneParams &pp) {
+    if (pp.inv_v_lifetime == 0.f) return q;
+    const float p = expf(-x * pp.inv_v_lifetime);
+    const float m = q * p;
+    if (!pp.fluct_absorb) return m;
+    const uint4 w = philox4x32_10_rk(make_uint4(depo, 0u, 0u, (0xFFu << 24) | (event_lo & 0xFFFFFFu)), pp.rk);
+    const float z = box_muller(w.x, w.y).x;
+    return fmaxf(fmaf(sqrtf(m * (1.f - p)), z, m), 0.f);
+}
+
 __device__ __forceinline__ int floor_div(int a, int b) {   // b > 0
     int q = a / b;
     return (a % b != 0 && a < 0) ? q - 1 : q;

@@ -31,6 +31,9 @@ struct PlaneParams {
     // origin, inv_dp; the window's fast path runs on them in FP32
     float ff[7][2];
     float kt, kp;                                        // sigma_t = kt sqrt(x), sigma_p = kp sqrt(x)
+    // drift attenuation: q -> q exp(-x / (v lifetime)) (0: none), optionally fluctuated
+    float inv_v_lifetime;                                // 1 / (v lifetime) in 1/mm
+    int32_t fluct_absorb;
     int32_t n_imp, n_wires, n_ticks, plane_index;
     int32_t fluctuate;
     uint32_t key0, key1;
@@ -142,7 +145,10 @@ __device__ __forceinline__ void clear_listed_tiles(const ClearJob &job, unsigned
 int64_t raster_chunk_count(int64_t n);
 void set_raster_schedule(int schedule);   // 0 warp-level chunks, 1 CTA-level chunks
 cudaError_t launch_rasterize_patches(int64_t n, const DepoDesc *desc, const int64_t *offsets, const PlaneParams &pp,
-                                     uint32_t event_lo, float *patches, int64_t *patch_desc, cudaStream_t s);
+                                     uint32_t event_lo, float *patches, int64_t *patch_desc, cudaStream_t s,
+                                     int64_t slot = 0);
+// offsets == nullptr: depo i's patch at i * slot (the scan-free slots)
+cudaError_t launch_fit_slots(int64_t n, DepoDesc *desc, int64_t slot, int32_t *status, cudaStream_t s);
 cudaError_t launch_bin_patches(int64_t n, const int64_t *patch_desc, const PlaneParams &pp, int32_t *tile_count,
                                int32_t *status, cudaStream_t s);
 cudaError_t launch_fill_patches(int64_t n, const int64_t *patch_desc, const PlaneParams &pp, const int32_t *tile_off,

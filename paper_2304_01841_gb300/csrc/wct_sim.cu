@@ -799,6 +799,26 @@ wct_status_t wct_sim_rasterize(wct_sim_t *s, int plane, const wct_depos_t *d, fl
     return WCT_OK;
 }
 
+wct_status_t wct_sim_rasterize_fixed(wct_sim_t *s, int plane, const wct_depos_t *d, float *patches, int64_t slot_bins,
+                                     int64_t *patch_desc, void *stream) {
+    wct_status_t st = plane_check(s, plane);
+    if (st) return st;
+    if ((st = check_depos(s, d))) return st;
+    if (!patches || !patch_desc) return fail(s, WCT_EINVAL, "patches and patch_desc are required");
+    if (slot_bins < 1 || slot_bins > (int64_t)WCT_MAX_WINDOW_TICKS * WCT_MAX_WINDOW_IMPACTS)
+        return fail(s, WCT_EINVAL, "slot_bins out of range");
+    cudaStream_t cs = (cudaStream_t)stream;
+    if ((st = ensure_depo_capacity(s, d->n))) return st;
+    const PlaneParams pp = plane_params(s, plane);
+    cudaError_t e = launch_prep(*d, pp, s->desc, nullptr, s->patch_size, s->status, cs);
+    if (e == cudaSuccess) e = launch_fit_slots(d->n, s->desc, slot_bins, s->status, cs);
+    if (e == cudaSuccess)
+        e = launch_rasterize_patches(d->n, s->desc, nullptr, pp, (uint32_t)d->event_id, patches, patch_desc, cs, slot_bins);
+    if (e != cudaSuccess) return cuda_fail(s, e, "rasterize fixed");
+    s->launches += d->n > 0 ? 4 : 0;
+    return WCT_OK;
+}
+
 wct_status_t wct_sim_scatter(wct_sim_t *s, int plane, const wct_depos_t *d, const float *patches,
                              const int64_t *patch_desc, float *grid, void *stream) {
     wct_status_t st = plane_check(s, plane);
@@ -1222,6 +1242,22 @@ wct_status_t wct_sim_convolve_impact(wct_sim_t *s, int plane, const float *phase
     if (e == cudaSuccess) e = launch_row_c2r(ps.fft_imp, s->spec2, nw, waveform, nt, nt, cs, s->status);
     if (e != cudaSuccess) return cuda_fail(s, e, "convolve impact");
     s->launches += 2 * ps.n_phases + 1;
+    return WCT_OK;
+}
+
+wct_status_t wct_sim_set_lifetime(wct_sim_t *s, double lifetime_us, int32_t fluctuate) {
+    if (!s) return WCT_EINVAL;
+    if (std::isnan(lifetime_us)) return fail(s, WCT_EINVAL, "lifetime is NaN");
+    const bool on = lifetime_us > 0.0 && std::isfinite(lifetime_us);
+    cudaDeviceSynchronize();                           // launches in flight keep the old value
+    for (int p = 0; p < s->n_planes; ++p) {
+        PlaneParams &pp = s->planes[p].pp;
+        pp.inv_v_lifetime = on ? (float)(1.0 / (pp.v * lifetime_us)) : 0.f;
+        pp.fluct_absorb = on && fluctuate ? 1 : 0;
+    }
+    for (auto &g : s->graphs) cudaGraphExecDestroy(g.exec);   // recorded batches captured the old value
+    s->graphs.clear();
+    s->seen.clear();
     return WCT_OK;
 }
 

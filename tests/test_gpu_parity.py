@@ -237,6 +237,41 @@ def test_library_grids_return_to_zero(schedule):
         make_sim(wl.planes, wl.responses(), wl.diffusion, schedule_id=4)
 
 
+def test_scan_free_fixed_slots_match_the_scanned_patches():
+    # the scan-free rasterize writes the same patches, each at its fixed slot i * slot_bins,
+    # and scattering them gives the same grid; an undersized slot skips and reports depos
+    import paper_2304_01841_gb300 as g
+    wl = synth.workload("uboone_plane")
+    pl = wl.planes[0]
+    d = wl.depos(n_depos=20000)
+    diff = synth.Diffusion(fluctuate=True, seed=21)
+    sim = make_sim([pl], [synth.make_response(pl.response_kind)], diff)
+    dd = _dev(d)
+    slot = g.patch_slot_bins(pl, diff, float(d.x.max()))
+    desc_s, patches_s = sim.rasterize(0, dd)
+    desc_f, patches_f = sim.rasterize_fixed(0, dd, slot)
+    sim.sync()
+    ds, df = to_np(desc_s), to_np(desc_f)
+    assert np.array_equal(ds[:, 1:], df[:, 1:])
+    assert np.array_equal(df[:, 0], np.arange(d.n) * slot)
+    ps, pf = to_np(patches_s), to_np(patches_f)
+    for i in range(0, d.n, 997):
+        nb = int(ds[i, 3] * ds[i, 4])
+        assert np.array_equal(ps[ds[i, 0]: ds[i, 0] + nb], pf[df[i, 0]: df[i, 0] + nb])
+    g_s = to_np(sim.scatter(0, dd, patches_s, desc_s))
+    g_f = to_np(sim.scatter(0, dd, patches_f, desc_f))
+    sim.sync()
+    assert np.abs(g_s - g_f).max() <= 1e-5 * np.abs(g_s).max()
+    small = 40                                          # most windows hold more bins
+    desc_x, _ = sim.rasterize_fixed(0, dd, small)
+    with pytest.raises(g.WctError) as ei:
+        sim.sync()
+    assert ei.value.code == 1
+    dx = to_np(desc_x)
+    over = ds[:, 3] * ds[:, 4] > small
+    assert over.any() and np.all(dx[over, 3] == 0) and np.array_equal(dx[~over, 3:], ds[~over, 3:])
+
+
 def test_empty_event_gives_zero_waveforms():
     wl = synth.workload("tiny")
     sim = make_sim(wl.planes, wl.responses(), wl.diffusion)
@@ -402,3 +437,26 @@ def test_bounded_wait_times_out_and_context_survives():
     sim.sync()
     ref = oracle.simulate_plane(d, wl.planes[0], wl.diffusion, wl.responses()[0])[2]
     assert rel_l2(to_np(wf), ref) <= WAVE_RTOL
+
+
+@pytest.mark.parametrize("fluct", [False, True])
+def test_lifetime_attenuation_matches_oracle(fluct):
+    # the drift step: every depo's charge attenuated (and fluctuated) before the rasterization,
+    # the same surviving charge for every plane; three planes at reduced depo count
+    import paper_2304_01841_gb300 as g
+    wl = synth.workload("three_plane")
+    d = wl.depos(n_depos=30000)
+    diff = synth.Diffusion(fluctuate=True, seed=404)
+    sim = make_sim(wl.planes, wl.responses(), diff)
+    sim.set_lifetime(2000.0, fluctuate=fluct)
+    wfs = sim.run_event(_dev(d))
+    sim.sync()
+    dd = oracle.drift_depos(d, diff, 2000.0, fluctuate=fluct)
+    for p, pl in enumerate(wl.planes):
+        _, grid, wf = oracle.simulate_plane(dd, pl, diff, wl.responses()[p], plane_index=p)
+        assert rel_l2(to_np(wfs[p]), wf) <= WAVE_RTOL, p
+    sim.set_lifetime(0.0)
+    back = sim.run_event(_dev(d))
+    sim.sync()
+    _, _, wf0 = oracle.simulate_plane(d, wl.planes[0], diff, wl.responses()[0], plane_index=0)
+    assert rel_l2(to_np(back[0]), wf0) <= WAVE_RTOL
