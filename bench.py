@@ -386,6 +386,38 @@ def measure_scan_free(reps=5):
             "scanned_patch_bytes": 4 * total, "scan_free_patch_bytes": 4 * d.n * slot}
 
 
+def measure_digitize(reps=20):
+    """Noise + digitisation of one uboone_plane waveform (3456 x 9600): algorithmic bytes 4 B
+    read + 2 B written per bin; CUDA events over reps launches."""
+    import torch
+    import paper_2304_01841_gb300 as pkg
+    import synth
+    wl = synth.workload(WORKLOAD)
+    pl = wl.planes[0]
+    sim = pkg.Simulator(wl.planes, wl.responses(), wl.diffusion)
+    # two waveforms and two outputs used alternately: 400 MB, more than the L2
+    wfs = [torch.randn((pl.n_wires, pl.n_ticks), device="cuda") * 100.0 for _ in range(2)]
+    outs = [torch.empty((pl.n_wires, pl.n_ticks), dtype=torch.int16, device="cuda") for _ in range(2)]
+    st = torch.cuda.current_stream()
+    for k in range(3):
+        sim.digitize(0, wfs[k % 2], 1.0, 900.0, 2.5, out=outs[k % 2], event_id=1)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for k in range(reps):
+        sim.digitize(0, wfs[k % 2], 1.0, 900.0, 2.5, out=outs[k % 2], event_id=k)
+    b.record(st)
+    torch.cuda.synchronize()
+    sim.sync()
+    us = a.elapsed_time(b) * 1e3 / reps
+    sim.close()
+    peak, _, kind = measured_peaks()
+    gbs = 6.0 * pl.n_wires * pl.n_ticks / (us * 1e-6) / 1e9
+    return {"workload": f"{WORKLOAD} waveform, 12-bit codes with white noise", "us": round(us, 2),
+            "alg_bytes": 6 * pl.n_wires * pl.n_ticks, "GB/s": round(gbs, 1), "frac": round(gbs / peak, 4),
+            "peak_source": f"{kind} (burst copy)"}
+
+
 def measure_serving(n_events=120, loads=(0.5, 0.8, 0.95)):
     """Served: APA-like planes (800/800/960 x 6000), heavy-tailed depo counts (90% 5k-50k,
     10% 1M-3M), open-loop Poisson arrivals at fractions of the measured capacity."""
@@ -611,6 +643,7 @@ def main():
         extras["serving"] = measure_serving()
         extras["impact_mode"] = measure_impact()
         extras["scan_free_rasterize"] = measure_scan_free()
+        extras["digitize"] = measure_digitize()
 
     if rank == 0:
         line = {

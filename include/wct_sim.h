@@ -244,6 +244,26 @@ typedef struct {
 wct_status_t wct_sim_run_host(wct_sim_t *sim, const wct_host_depos_t *events, int n_events,
                               float *const *waveforms);
 
+/* Digitiser parameters: gain (ADC counts per waveform unit), baseline (counts), noise_rms
+ * (counts, white Gaussian), bits (1..15), add_noise (0: no noise). */
+typedef struct {
+    double gain;
+    double baseline;
+    double noise_rms;
+    int32_t bits;
+    int32_t add_noise;
+} wct_adc_t;
+
+/* Noise and digitisation, the steps after the convolution of §2: for every bin of a plane's
+ * waveform (DEVICE float32 [n_wires][n_ticks]) the ADC code (DEVICE int16, same shape)
+ *     code = clamp(floor(gain v + baseline + noise_rms z + 1/2), 0, 2^bits - 1)
+ * evaluated in explicitly rounded FP32 in that order (a non-finite value gives 0); z is white
+ * Gaussian noise from the Philox stream under the handle's seed, one call per four consecutive
+ * ticks of a wire at counter (tick / 4, wire, 0, (0x80 | plane) << 24 | event id), Box-Muller
+ * pairs for ticks 4k, 4k+1 and 4k+2, 4k+3.  WCT_EINVAL for bad parameters. */
+wct_status_t wct_sim_digitize(wct_sim_t *sim, int plane, const float *waveform, int16_t *adc,
+                              const wct_adc_t *params, uint64_t event_id, void *stream);
+
 /* Drift attenuation by the electron lifetime, the step before the rasterization of §2: every
  * depo's charge q becomes the surviving charge of Binomial(q, p), p = exp(-t_d / lifetime),
  * t_d = x / v_drift: its mean q p, or (fluctuate != 0) the normal approximation

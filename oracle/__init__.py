@@ -16,6 +16,8 @@ Parity status of each function (what pins it; see tests/test_oracle_*.py):
   scatter              pinned: charge conservation, hand-built folding cases.
   convolve             pinned: delta response = identity, delta grid = placed response,
                        direct quadruple loop, no circular wrap, linearity.
+  digitise             pinned: noise-free codes against exact rounding of hand values,
+                       clamping, the noise's normality and its keying.
   drift attenuation    pinned: closed form q exp(-t_d / lifetime); fluctuated mean and
                        variance of the binomial; the same charge for every plane.
   impact-resolution    pinned: phase-independent responses reduce to the folded path,
@@ -258,3 +260,42 @@ def drift_depos(depos, diff, lifetime_us: float, fluctuate: bool = False):
     out = copy.copy(depos)
     out.q = m.astype(np.float32)
     return out
+
+
+def noise_normals(seed: int, n_wires: int, n_ticks: int, plane_index: int, event_id: int) -> np.ndarray:
+    """White-noise z[wire][tick] of the digitiser (FP64): Philox4x32-10 at counter
+    (tick // 4, wire, 0, (0x80 | plane) << 24 | event id mod 2^24) under the seed's key; words
+    (0, 1) and (2, 3) give the Box-Muller pairs of ticks 4k, 4k+1 and 4k+2, 4k+3
+    (u = (word + 1/2) 2^-32, (r cos 2 pi u_1, r sin 2 pi u_1), r = sqrt(-2 ln u_0))."""
+    nq = (n_ticks + 3) // 4
+    w, qd = np.meshgrid(np.arange(n_wires), np.arange(nq), indexing="ij")
+    ctr = np.zeros((n_wires * nq, 4), dtype=np.uint32)
+    ctr[:, 0] = qd.ravel().astype(np.uint32)
+    ctr[:, 1] = w.ravel().astype(np.uint32)
+    ctr[:, 3] = np.uint32(((0x80 | plane_index) << 24) | (int(event_id) & 0xFFFFFF))
+    x = philox4x32_10(ctr, (int(seed) & 0xFFFFFFFF, (int(seed) >> 32) & 0xFFFFFFFF)).astype(np.float64)
+    u = (x + 0.5) * 2.0 ** -32
+    r01 = np.sqrt(-2.0 * np.log(u[:, 0]))
+    r23 = np.sqrt(-2.0 * np.log(u[:, 2]))
+    z = np.stack([r01 * np.cos(2 * np.pi * u[:, 1]), r01 * np.sin(2 * np.pi * u[:, 1]),
+                  r23 * np.cos(2 * np.pi * u[:, 3]), r23 * np.sin(2 * np.pi * u[:, 3])], axis=1)
+    return z.reshape(n_wires, nq * 4)[:, :n_ticks]
+
+
+def digitize(waveform: np.ndarray, gain: float, baseline: float, noise_rms: float, bits: int, add_noise: bool,
+             seed: int, plane_index: int, event_id: int):
+    """ADC codes of a float32 waveform: code = clamp(floor(gain v + baseline + noise_rms z + 1/2),
+    0, 2^bits - 1), the integer decided in FP32 with each operation rounded separately in that
+    order (as the device does), z = noise_normals(...) rounded to FP32.  Returns (codes int16,
+    the FP32 value before rounding)."""
+    f32 = np.float32
+    v = np.asarray(waveform, dtype=np.float32)
+    nw, nt = v.shape
+    z = (noise_normals(seed, nw, nt, plane_index, event_id).astype(np.float32) if add_noise and noise_rms > 0
+         else np.zeros_like(v))
+    with np.errstate(invalid="ignore", over="ignore"):
+        s = (f32(gain) * v + f32(baseline)) + f32(noise_rms) * z
+        code = np.floor(s + f32(0.5))
+        code = np.where(np.isnan(code), f32(0), code)
+        code = np.clip(code, f32(0), f32((1 << bits) - 1))
+    return code.astype(np.int16), s

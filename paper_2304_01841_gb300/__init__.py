@@ -181,6 +181,21 @@ class Simulator:
         self._check(self._lib.wct_sim_run_batch(self._h, evs, len(events), arr, _stream_handle(stream)))
         return wfs
 
+    def digitize(self, plane: int, waveform, gain: float, baseline: float, noise_rms: float, bits: int = 12,
+                 add_noise: bool = True, event_id: int = 0, out=None, stream=None):
+        """wct_sim_digitize: noise + ADC codes (int16 CUDA tensor [n_wires, n_ticks])."""
+        torch = _torch()
+        wf = self._grid(plane, waveform)
+        pl = self.planes[plane]
+        if out is None:
+            out = torch.empty((pl.n_wires, pl.n_ticks), dtype=torch.int16, device="cuda")
+        elif out.shape != (pl.n_wires, pl.n_ticks) or out.dtype != torch.int16 or not out.is_contiguous():
+            raise ValueError("adc output must be contiguous int16 [n_wires, n_ticks]")
+        a = _abi.wct_adc_t(float(gain), float(baseline), float(noise_rms), int(bits), int(bool(add_noise)))
+        self._check(self._lib.wct_sim_digitize(self._h, plane, _ptr(wf), _ptr(out), ctypes.byref(a),
+                                               int(event_id) & 0xFFFFFFFFFFFFFFFF, _stream_handle(stream)))
+        return out
+
     def set_lifetime(self, lifetime_us: float, fluctuate: bool = False):
         """wct_sim_set_lifetime: electron-lifetime attenuation of the drifting charge (<= 0: off)."""
         self._check(self._lib.wct_sim_set_lifetime(self._h, float(lifetime_us), int(bool(fluctuate))))

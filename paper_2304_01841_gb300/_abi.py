@@ -46,6 +46,11 @@ class wct_depos_t(ctypes.Structure):
                 ("n", c_i64), ("event_id", c_u64)]
 
 
+class wct_adc_t(ctypes.Structure):
+    _fields_ = [("gain", ctypes.c_double), ("baseline", ctypes.c_double), ("noise_rms", ctypes.c_double),
+                ("bits", c_i32), ("add_noise", c_i32)]
+
+
 class wct_host_depos_t(ctypes.Structure):
     _fields_ = [("t0_us", c_vp), ("x_mm", c_vp), ("y_mm", c_vp), ("z_mm", c_vp), ("q_e", c_vp),
                 ("n", c_i64), ("event_id", c_u64)]
@@ -68,6 +73,7 @@ EXPORTS = {
     "wct_sim_set_impact_responses": ([c_vp, ctypes.c_int, ctypes.POINTER(wct_response_t), ctypes.c_int], ctypes.c_int),
     "wct_sim_convolve_impact": ([c_vp, ctypes.c_int, c_vp, c_vp, c_vp], ctypes.c_int),
     "wct_sim_run_host": ([c_vp, ctypes.POINTER(wct_host_depos_t), ctypes.c_int, ctypes.POINTER(c_vp)], ctypes.c_int),
+    "wct_sim_digitize": ([c_vp, ctypes.c_int, c_vp, c_vp, ctypes.POINTER(wct_adc_t), c_u64, c_vp], ctypes.c_int),
     "wct_sim_set_lifetime": ([c_vp, ctypes.c_double, c_i32], ctypes.c_int),
     "wct_sim_sync": ([c_vp, c_vp], ctypes.c_int),
     "wct_sim_plane_info": ([c_vp, ctypes.c_int, ctypes.POINTER(c_i64)], ctypes.c_int),

@@ -15,8 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libwctsim.so")
-SOURCES = ["wct_sim.cu", "k_depo.cu", "k_raster.cu", "k_fft.cu"]
-HEADERS = ["wct_internal.cuh", "wct_device.cuh"]
+SOURCES = ["wct_sim.cu", "k_depo.cu", "k_raster.cu", "k_fft.cu", "k_adc.cu"]
+HEADERS = ["wct_internal.cuh", "wct_device.cuh", "wct_tma.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

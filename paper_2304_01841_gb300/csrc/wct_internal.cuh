@@ -164,6 +164,14 @@ cudaError_t launch_row_r2c(const FFTPlan &p, const float *in, int64_t in_stride,
 cudaError_t launch_wire_stage(const FFTPlan &p, const float2 *spec, const float2 *resp_spec, int n_wires,
                               float2 *out, cudaStream_t s, int32_t *status = nullptr, const ClearJob *clear = nullptr,
                               bool accumulate = false);
+// Noise + digitisation: code = clamp(floor(gain v + baseline + noise_rms z + 1/2), 0, max_code)
+struct AdcParams {
+    float gain, baseline, noise_rms, max_code;
+    int32_t add_noise;
+    uint32_t rk[20];   // Philox round keys of the seed
+};
+cudaError_t launch_digitize(const float *wf, int16_t *adc, int n_wires, int n_ticks, const AdcParams &a, uint32_t c3,
+                            cudaStream_t s);
 // Impact-resolution scatter of unfused patches onto n_imp phase grids [phase][wire][tick].
 cudaError_t launch_scatter_phases(int64_t n, const float *patches, const int64_t *desc, int n_imp, int n_wires,
                                   int n_ticks, float *grids, cudaStream_t s);

@@ -1245,6 +1245,30 @@ wct_status_t wct_sim_convolve_impact(wct_sim_t *s, int plane, const float *phase
     return WCT_OK;
 }
 
+wct_status_t wct_sim_digitize(wct_sim_t *s, int plane, const float *waveform, int16_t *adc, const wct_adc_t *params,
+                              uint64_t event_id, void *stream) {
+    wct_status_t st = plane_check(s, plane);
+    if (st) return st;
+    if (!waveform || !adc || !params) return fail(s, WCT_EINVAL, "waveform, adc and params are required");
+    const wct_adc_t &a = *params;
+    if (!std::isfinite(a.gain) || !std::isfinite(a.baseline) || !std::isfinite(a.noise_rms) || a.noise_rms < 0 ||
+        a.bits < 1 || a.bits > 15)
+        return fail(s, WCT_EINVAL, "bad digitiser parameters (finite gain / baseline, noise_rms >= 0, 1 <= bits <= 15)");
+    const PlaneState &ps = s->planes[plane];
+    AdcParams ap{};
+    ap.gain = (float)a.gain;
+    ap.baseline = (float)a.baseline;
+    ap.noise_rms = (float)a.noise_rms;
+    ap.max_code = (float)((1 << a.bits) - 1);
+    ap.add_noise = a.add_noise && a.noise_rms > 0 ? 1 : 0;
+    for (int k = 0; k < 20; ++k) ap.rk[k] = ps.pp.rk[k];
+    const uint32_t c3 = ((uint32_t)(0x80 | plane) << 24) | ((uint32_t)event_id & 0xFFFFFFu);
+    const cudaError_t e = launch_digitize(waveform, adc, ps.g.n_wires, ps.g.n_ticks, ap, c3, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "digitize");
+    s->launches += 1;
+    return WCT_OK;
+}
+
 wct_status_t wct_sim_set_lifetime(wct_sim_t *s, double lifetime_us, int32_t fluctuate) {
     if (!s) return WCT_EINVAL;
     if (std::isnan(lifetime_us)) return fail(s, WCT_EINVAL, "lifetime is NaN");
