@@ -332,7 +332,8 @@ def measure_impact(n_events=4, reps=2):
             "events_per_s": 1.0 / t_impact, "depos_per_s": n / t_impact, "ms_per_event": 1e3 * t_impact,
             "folded_ms_per_event": 1e3 * t_folded,
             "stages_us": {"patches_rasterize_scatter": round(stages["raster_scatter"] + stages["prep_binning"], 1),
-                          "phase_transforms_and_stencils": round(stages["row_r2c"], 1),
+                          "phase_transforms": round(stages["row_r2c"], 1),
+                          "phase_stencils": round(stages["wire_stage"], 1),
                           "inverse_transform": round(stages["row_c2r"], 1)}}
 
 

@@ -912,9 +912,10 @@ constexpr int kStageWiresMax = 128;      // output wires per CTA at most (runtim
 constexpr int kGroupRows = 8;
 constexpr int kRingGroups = 4;
 
-__global__ void __launch_bounds__(kStageFB + 32)
+__global__ void __launch_bounds__(kStageFB + 32, 3)
 k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, int Fs, int Fu, int n_wires,
-                 int wires_per_cta, float2 *__restrict__ T, int32_t *status, const ClearJob clear, int accumulate) {
+                 int wires_per_cta, float2 *__restrict__ T, int32_t *status, const ClearJob clear, int accumulate,
+                 int n_phases, int64_t s_phase_stride, int64_t r_phase_stride) {
     __shared__ __align__(16) float2 ring[kRingGroups * kGroupRows][kStageFB];
     __shared__ uint64_t full[kRingGroups], empty[kRingGroups];
     const int tid = threadIdx.x;
@@ -938,18 +939,21 @@ k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, in
     __syncthreads();
     if (tid >= kStageFB) {
         // producer: lane 0 of the extra warp issues the copies group by group
+        // (impact mode: the groups of every phase in turn, one ring sequence)
         if (tid == kStageFB) {
-            for (int g = 0; g < n_groups; ++g) {
-                const int gs = g % kRingGroups, use = g / kRingGroups;
+            for (int gg = 0; gg < n_phases * n_groups; ++gg) {
+                const int ph = gg / n_groups, g = gg - ph * n_groups;
+                const int gs = gg % kRingGroups, use = gg / kRingGroups;
                 if (use > 0 && !mbar_wait(&empty[gs], (use - 1) & 1)) {
                     set_status(status, ST_ETIMEOUT);
                     break;
                 }
                 const int r0 = g * kGroupRows, r1 = min(r0 + kGroupRows, n_rows);
+                const float2 *Sp = S + (size_t)ph * s_phase_stride;
                 fence_proxy_async_smem();
                 mbar_arrive_expect_tx(&full[gs], row_bytes * (uint32_t)(r1 - r0));
                 for (int r = r0; r < r1; ++r)
-                    bulk_g2s(ring[gs * kGroupRows + (r - r0)], S + (size_t)(w0 - KC + m_lo + r) * Fs + f0, row_bytes,
+                    bulk_g2s(ring[gs * kGroupRows + (r - r0)], Sp + (size_t)(w0 - KC + m_lo + r) * Fs + f0, row_bytes,
                              &full[gs]);
             }
         }
@@ -966,18 +970,14 @@ k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, in
     constexpr int kOutBlock = 8;
     constexpr int kWin = kOutBlock + 2 * KC;
     float2 rr[KW], ri[KW];                             // (re, re) and (im, im) of each tap
-#pragma unroll
-    for (int k = 0; k < KW; ++k) {
-        const float2 v = live ? Rt[(size_t)k * Fs + f] : make_float2(0.f, 0.f);
-        rr[k] = make_float2(v.x, v.x);
-        ri[k] = make_float2(v.y, v.y);
-    }
     bool ok = true;
+    int gbase = 0;                                     // ring sequence number of the phase's group 0
     auto load_row = [&](int m) -> float2 {
         float2 x = make_float2(0.f, 0.f);
         if (m >= m_lo && m < m_hi) {
             const int idx = m - m_lo;
-            const int g = idx / kGroupRows, in_g = idx - g * kGroupRows, gs = g % kRingGroups;
+            const int gl = idx / kGroupRows, in_g = idx - gl * kGroupRows;
+            const int g = gbase + gl, gs = g % kRingGroups;
             if (in_g == 0 && ok && !mbar_wait(&full[gs], (g / kRingGroups) & 1)) {
                 set_status(status, ST_ETIMEOUT);
                 ok = false;
@@ -988,10 +988,19 @@ k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, in
         }
         return x;
     };
+    const int n_out = w1 - w0;
+    for (int ph = 0; ph < n_phases; ++ph, gbase += n_groups) {
+    const float2 *Rp = Rt + (size_t)ph * r_phase_stride;
+#pragma unroll
+    for (int k = 0; k < KW; ++k) {
+        const float2 v = live ? Rp[(size_t)k * Fs + f] : make_float2(0.f, 0.f);
+        rr[k] = make_float2(v.x, v.x);
+        ri[k] = make_float2(v.y, v.y);
+    }
+    const bool acc = accumulate || ph > 0;
     float2 win[kWin];
 #pragma unroll
     for (int t = 0; t < 2 * KC; ++t) win[t] = load_row(t);
-    const int n_out = w1 - w0;
     for (int b = 0; b < n_out; b += kOutBlock) {
 #pragma unroll
         for (int t = 0; t < kOutBlock; ++t) win[2 * KC + t] = load_row(b + 2 * KC + t);
@@ -1016,16 +1025,17 @@ k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, in
             if (live && b + j < n_out) {
                 float2 v = make_float2(A.x - B.y, A.y + B.x);
                 float2 *dst = &T[(size_t)(w0 + b + j) * Fs + f];
-                if (accumulate) v = cadd(v, *dst);
+                if (acc) v = cadd(v, *dst);
                 *dst = v;
             }
         }
 #pragma unroll
         for (int t = 0; t < 2 * KC; ++t) win[t] = win[t + kOutBlock];
     }
+    }
     if (!ok && tid == 0) {
         // after a timeout, wait (bounded) for the last group this CTA issued before leaving
-        const int g = n_groups - 1;
+        const int g = n_phases * n_groups - 1;
         mbar_wait(&full[g % kRingGroups], (g / kRingGroups) & 1);
     }
 }
@@ -1274,7 +1284,7 @@ cudaError_t launch_row_c2r(const FFTPlan &p, const float2 *spec, int n_rows, flo
 }
 
 cudaError_t launch_wire_stage(const FFTPlan &p, const float2 *spec, const float2 *resp_spec, int n_wires, float2 *out,
-                              cudaStream_t s, int32_t *status, const ClearJob *clear, bool accumulate) {
+                              cudaStream_t s, int32_t *status, const ClearJob *clear, bool accumulate, int n_phases) {
     if (n_wires <= 0) return cudaSuccess;
     const ClearJob job = clear ? *clear : ClearJob{};
     if (aligned16(spec) && (p.Fs % 2) == 0 && (p.Fu % 2) == 0) {
@@ -1302,8 +1312,19 @@ cudaError_t launch_wire_stage(const FFTPlan &p, const float2 *spec, const float2
         }
         dim3 grid(fb, (n_wires + wpc - 1) / wpc);
         k_wire_stage_tma<<<grid, kStageFB + 32, 0, s>>>(spec, resp_spec, p.Fs, p.Fu, n_wires, wpc, out, status, job,
-                                                        accumulate ? 1 : 0);
+                                                        accumulate ? 1 : 0, n_phases, (int64_t)n_wires * p.Fs,
+                                                        (int64_t)KW * p.Fs);
         return cudaGetLastError();
+    }
+    if (n_phases > 1) {
+        // fallback kernel: one phase per launch, accumulating
+        for (int ph = 0; ph < n_phases; ++ph) {
+            const cudaError_t e = launch_wire_stage(p, spec + (size_t)ph * n_wires * p.Fs,
+                                                    resp_spec + (size_t)ph * KW * p.Fs, n_wires, out, s, status,
+                                                    ph == 0 ? clear : nullptr, accumulate || ph > 0, 1);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
     }
     dim3 grid((p.Fu + kStageThreads - 1) / kStageThreads, (n_wires + kStageRun - 1) / kStageRun);
     k_wire_stage<<<grid, kStageThreads, 0, s>>>(spec, resp_spec, p.Fs, p.Fu, n_wires, out, accumulate ? 1 : 0);

@@ -163,7 +163,9 @@ cudaError_t launch_row_r2c(const FFTPlan &p, const float *in, int64_t in_stride,
 // accumulate: out += the stencil instead of out = (the per-phase sum of the impact mode)
 cudaError_t launch_wire_stage(const FFTPlan &p, const float2 *spec, const float2 *resp_spec, int n_wires,
                               float2 *out, cudaStream_t s, int32_t *status = nullptr, const ClearJob *clear = nullptr,
-                              bool accumulate = false);
+                              bool accumulate = false, int n_phases = 1);
+// n_phases > 1 (impact mode): spec holds n_phases spectra [phase][wire][Fs] and resp_spec
+// n_phases response spectra [phase][21][Fs]; out = (out +) the sum over phases of their stencils
 // Noise + digitisation: code = clamp(floor(gain v + baseline + noise_rms z + 1/2), 0, max_code)
 struct AdcParams {
     float gain, baseline, noise_rms, max_code;

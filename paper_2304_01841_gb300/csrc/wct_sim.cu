@@ -57,6 +57,8 @@ struct wct_sim {
     // scratch
     float2 *spec = nullptr, *spec2 = nullptr;
     size_t spec_elems = 0;          // capacity of spec / spec2 (complex elements)
+    float2 *spec_imp = nullptr;     // impact mode: the spectra of every phase [phase][wire][Fs]
+    size_t spec_imp_elems = 0;
     // impact mode: unfused patches and their descriptors
     float *imp_patches = nullptr;
     int64_t imp_patch_cap = 0;
@@ -529,16 +531,14 @@ wct_status_t run_plane_impact(wct_sim *s, int p, const wct_depos_t *d, float *wf
     if (e != cudaSuccess) return cuda_fail(s, e, "phase scatter");
     s->launches += n > 0 ? 1 : 0;
     mark(s, slot, 2, cs);
-    const int KW = WCT_MAX_RESPONSE_WIRES;
-    for (int ph = 0; ph < ps.n_phases; ++ph) {
-        e = launch_row_r2c(ps.fft_imp, ps.phase_grids + (size_t)ph * nw * nt, nt, nt, nw, s->spec, cs, s->status);
-        if (e == cudaSuccess)
-            e = launch_wire_stage(ps.fft_imp, s->spec, ps.resp_imp + (size_t)ph * KW * ps.fft_imp.Fs, nw, s->spec2, cs,
-                                  s->status, nullptr, ph > 0);
-        if (e != cudaSuccess) return cuda_fail(s, e, "phase transform");
-        s->launches += 2;
-    }
+    // every phase grid's rows in one forward launch, one wire stage over all phases
+    e = launch_row_r2c(ps.fft_imp, ps.phase_grids, nt, nt, ps.n_phases * nw, s->spec_imp, cs, s->status);
+    if (e != cudaSuccess) return cuda_fail(s, e, "phase transforms");
     mark(s, slot, 3, cs);
+    e = launch_wire_stage(ps.fft_imp, s->spec_imp, ps.resp_imp, nw, s->spec2, cs, s->status, nullptr, false,
+                          ps.n_phases);
+    if (e != cudaSuccess) return cuda_fail(s, e, "phase stencils");
+    s->launches += 2;
     mark(s, slot, 4, cs);
     e = launch_row_c2r(ps.fft_imp, s->spec2, nw, wf, nt, nt, cs, s->status);
     if (e != cudaSuccess) return cuda_fail(s, e, "row c2r");
@@ -1216,6 +1216,14 @@ wct_status_t wct_sim_set_impact_responses(wct_sim_t *s, int plane, const wct_res
         ps.phase_grid_bytes = sizeof(float) * (size_t)n_phases * ps.g.n_wires * ps.g.n_ticks;
         st = dev_alloc(s, (void **)&ps.phase_grids, ps.phase_grid_bytes);
     }
+    const size_t need_imp = (size_t)n_phases * need;
+    if (st == WCT_OK && need_imp > s->spec_imp_elems) {
+        dev_free(s, s->spec_imp, sizeof(float2) * s->spec_imp_elems);
+        s->spec_imp = nullptr;
+        s->spec_imp_elems = 0;
+        st = dev_alloc(s, (void **)&s->spec_imp, sizeof(float2) * need_imp);
+        if (st == WCT_OK) s->spec_imp_elems = need_imp;
+    }
     if (st) {
         drop_impact(s, ps);
         return st;
@@ -1231,17 +1239,14 @@ wct_status_t wct_sim_convolve_impact(wct_sim_t *s, int plane, const float *phase
     if (ps.n_phases == 0) return fail(s, WCT_EINVAL, "plane has no impact responses");
     if (!phase_grids || !waveform) return fail(s, WCT_EINVAL, "phase_grids and waveform are required");
     cudaStream_t cs = (cudaStream_t)stream;
-    const int nw = ps.g.n_wires, nt = ps.g.n_ticks, KW = WCT_MAX_RESPONSE_WIRES;
-    cudaError_t e = cudaSuccess;
-    for (int ph = 0; ph < ps.n_phases && e == cudaSuccess; ++ph) {
-        e = launch_row_r2c(ps.fft_imp, phase_grids + (size_t)ph * nw * nt, nt, nt, nw, s->spec, cs, s->status);
-        if (e == cudaSuccess)
-            e = launch_wire_stage(ps.fft_imp, s->spec, ps.resp_imp + (size_t)ph * KW * ps.fft_imp.Fs, nw, s->spec2, cs,
-                                  s->status, nullptr, ph > 0);
-    }
+    const int nw = ps.g.n_wires, nt = ps.g.n_ticks;
+    cudaError_t e = launch_row_r2c(ps.fft_imp, phase_grids, nt, nt, ps.n_phases * nw, s->spec_imp, cs, s->status);
+    if (e == cudaSuccess)
+        e = launch_wire_stage(ps.fft_imp, s->spec_imp, ps.resp_imp, nw, s->spec2, cs, s->status, nullptr, false,
+                              ps.n_phases);
     if (e == cudaSuccess) e = launch_row_c2r(ps.fft_imp, s->spec2, nw, waveform, nt, nt, cs, s->status);
     if (e != cudaSuccess) return cuda_fail(s, e, "convolve impact");
-    s->launches += 2 * ps.n_phases + 1;
+    s->launches += 3;
     return WCT_OK;
 }
 
