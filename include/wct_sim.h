@@ -204,10 +204,10 @@ wct_status_t wct_sim_run_batch(wct_sim_t *sim, const wct_depos_t *events, int n_
  * response (same transform length).  From then on run_event / run_batch / run_host compute
  * that plane as
  *     out[w, t] = sum_{w', p} sum_tau G[n_imp w' + p, t - tau] * R_p[w - w' + kc, tau]
- * (unfused patches scattered onto n_phases phase grids, each transformed and stenciled with
- * its phase's response into one summed spectrum, one inverse transform); the patch sizes are
- * queried on the host, so those calls synchronise the stream, and run_batch runs such events
- * one after the other.  Library memory: n_phases grids of the plane and the phases' spectra.
+ * (every patch bin added to the phase grid of its sub-bin, every phase grid transformed in one
+ * launch, one wire stage summing all phases' stencils, one inverse transform); run_batch runs
+ * such events one after the other.  Library memory: n_phases grids of the plane and the
+ * spectra of every phase.
  * responses == NULL switches the plane back to the folded mode.  Synchronous. */
 wct_status_t wct_sim_set_impact_responses(wct_sim_t *sim, int plane, const wct_response_t *responses, int n_phases);
 

@@ -822,36 +822,114 @@ cudaError_t launch_raster_chunks(const wct_depos_t &d, const PlaneParams &pp, ui
     return cudaGetLastError();
 }
 
-// Impact-resolution scatter: patch bin (tick lo_t + a, impact lo_p + j) of each depo is added
-// to grid[phase][wire][tick] with wire = impact / n_imp, phase = impact % n_imp (one warp per
-// depo, grid-stride; bins off the grid dropped).  patch_desc rows: off, lo_t, lo_p, nt, np.
-__global__ void __launch_bounds__(256)
-k_scatter_phases(int64_t n, const float *__restrict__ patches, const int64_t *__restrict__ desc, int n_imp,
-                 int n_wires, int n_ticks, float *__restrict__ grids) {
-    const int lane = threadIdx.x & 31;
-    const int64_t n_imp_bins = (int64_t)n_wires * n_imp;
-    for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < n;
-         i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-        const int64_t off = desc[5 * i], lo_t = desc[5 * i + 1], lo_p = desc[5 * i + 2];
-        const int nt = (int)desc[5 * i + 3], np = (int)desc[5 * i + 4];
-        for (int idx = lane; idx < nt * np; idx += 32) {
-            const int a = idx / np;
-            const int64_t tick = lo_t + a, j = lo_p + (idx - a * np);
-            if (tick < 0 || tick >= n_ticks || j < 0 || j >= n_imp_bins) continue;
-            const int64_t w = j / n_imp, phase = j - w * n_imp;
-            atomicAdd(&grids[(phase * n_wires + w) * n_ticks + tick], patches[off + idx]);
+// Impact mode, fused: one warp per depo (grid-stride) evaluates its patch at impact resolution
+// and adds every bin straight to the phase grid of its sub-bin (grid[phase][wire][tick], phase
+// = the sub-bin's position inside its wire), with no patch buffer and no size query.  The work
+// is flattened over (tick, wire, group of four sub-bins) units, one Philox call each, as the
+// counter defines the groups.  With fluctuation the bins are drawn twice: once for the
+// patch's fluctuated sum, once more to add them rescaled to the depo's charge.
+__global__ void __launch_bounds__(kPatchWarps * 32)
+k_raster_phases(int64_t n, const DepoDesc *__restrict__ desc, PlaneParams pp, uint32_t event_lo,
+                float *__restrict__ grids) {
+    __shared__ float wbuf[kPatchWarps][kWBuf];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float *wt = wbuf[warp];
+    float *wp = wt + kWT;
+    const uint32_t c3 = counter_c3(pp, event_lo);
+    const int n_imp = pp.n_imp, G = (n_imp + 3) >> 2;
+    const int64_t nwarps = (int64_t)gridDim.x * kPatchWarps;
+    for (int64_t di = (int64_t)blockIdx.x * kPatchWarps + warp; di < n; di += nwarps) {
+        const DepoDesc d = desc[di];
+        const int nt = d.nt, np = d.np;
+        if (nt == 0) continue;
+        axis_weights(wt, nt, d.mu_t, d.inv_t, lane);
+        axis_weights(wp, np, d.mu_p, d.inv_p, lane);
+        const int lo_p = d.lo_p, hi_p = d.lo_p + np;
+        const int wl = floor_div(lo_p, n_imp);
+        const int nw = floor_div(hi_p - 1, n_imp) - wl + 1;
+        // groups per tick row: the first wire's (it may start inside a group), G for interior
+        // wires, the last wire's (it may end inside one)
+        const int sub_lo0 = lo_p - wl * n_imp, g_lo0 = sub_lo0 >> 2;
+        const int cnt0 = ((min(n_imp, hi_p - wl * n_imp) - 1) >> 2) - g_lo0 + 1;
+        const int cnt_l = nw > 1 ? ((hi_p - (wl + nw - 1) * n_imp - 1) >> 2) + 1 : 0;
+        const int GD = cnt0 + (nw > 2 ? (nw - 2) * G : 0) + cnt_l;
+        const int U = nt * GD;
+        const float q = d.q;
+        // unit u -> (window tick a, wire, group g) and its lanes [l0, l1) of the group
+        auto unit = [&](int u, int &a, int &wire, int &g, int &l0, int &l1) {
+            a = u / GD;
+            const int r = u - a * GD;
+            int w;
+            if (r < cnt0) {
+                w = 0;
+                g = g_lo0 + r;
+            } else {
+                const int r2 = r - cnt0;
+                w = 1 + r2 / G;
+                g = r2 - (w - 1) * G;
+            }
+            wire = wl + w;
+            const int first = wire * n_imp;
+            const int sb = g << 2;
+            l0 = max(max(first, lo_p) - first - sb, 0);
+            l1 = min(min(first + n_imp, hi_p) - first - sb, 4);
+        };
+        auto draw = [&](int a, int wire, int g, float (&z)[4]) {
+            const uint4 x = philox4x32_10_rk(make_uint4((uint32_t)di, (uint32_t)(d.lo_t + a), (uint32_t)(wire * G + g), c3),
+                                             pp.rk);
+            const float2 p0 = box_muller(x.x, x.y), p1 = box_muller(x.z, x.w);
+            z[0] = p0.x, z[1] = p0.y, z[2] = p1.x, z[3] = p1.y;
+        };
+        float scale = 1.f;
+        if (pp.fluctuate) {
+            float part = 0.f;
+            for (int u = lane; u < U; u += 32) {
+                int a, wire, g, l0, l1;
+                unit(u, a, wire, g, l0, l1);
+                float z[4];
+                draw(a, wire, g, z);
+                const int jb = wire * n_imp + (g << 2) - lo_p;
+#pragma unroll
+                for (int l = 0; l < 4; ++l)
+                    if (l >= l0 && l < l1) {
+                        const float w = wt[a] * wp[jb + l], m = q * w;
+                        part += fmaxf(fmaf(sfu_sqrt(m * (1.f - w)), z[l], m), 0.f);
+                    }
+            }
+            const float sum = warp_sum(part);
+            scale = sum > 0.f ? q / sum : -1.f;                 // -1: keep the unfluctuated patch
         }
+        for (int u = lane; u < U; u += 32) {
+            int a, wire, g, l0, l1;
+            unit(u, a, wire, g, l0, l1);
+            const int tick = d.lo_t + a;
+            if (tick < 0 || tick >= pp.n_ticks || wire < 0 || wire >= pp.n_wires) continue;
+            float z[4] = {0.f, 0.f, 0.f, 0.f};
+            if (scale > 0.f && pp.fluctuate) draw(a, wire, g, z);
+            const int jb = wire * n_imp + (g << 2) - lo_p;
+#pragma unroll
+            for (int l = 0; l < 4; ++l)
+                if (l >= l0 && l < l1) {
+                    const float w = wt[a] * wp[jb + l], m = q * w;
+                    const float v = (pp.fluctuate && scale > 0.f) ? fmaxf(fmaf(sfu_sqrt(m * (1.f - w)), z[l], m), 0.f) * scale
+                                                                 : m;
+                    const int phase = (g << 2) + l;
+                    atomicAdd(&grids[((size_t)phase * pp.n_wires + wire) * pp.n_ticks + tick], v);
+                }
+        }
+        __syncwarp();
     }
 }
 
-cudaError_t launch_scatter_phases(int64_t n, const float *patches, const int64_t *desc, int n_imp, int n_wires,
-                                  int n_ticks, float *grids, cudaStream_t s) {
+cudaError_t launch_raster_phases(int64_t n, const DepoDesc *desc, const PlaneParams &pp, uint32_t event_lo,
+                                 float *grids, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    const int64_t want = (n + 7) / 8;
-    const int blocks = (int)(want < 152 * 16 ? want : 152 * 16);
-    k_scatter_phases<<<blocks, 256, 0, s>>>(n, patches, desc, n_imp, n_wires, n_ticks, grids);
+    int64_t blocks = (n + kPatchWarps - 1) / kPatchWarps;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_raster_phases<<<(unsigned)blocks, kPatchWarps * 32, 0, s>>>(n, desc, pp, event_lo, grids);
     return cudaGetLastError();
 }
+
 
 // Size of a plane's flag block: the flags, two counters and the tile list.
 size_t tile_flag_words(const PlaneParams &pp) { return 2 * (size_t)pp.n_tiles_w * pp.n_tiles_t + 2; }

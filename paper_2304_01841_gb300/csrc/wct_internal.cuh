@@ -174,9 +174,11 @@ struct AdcParams {
 };
 cudaError_t launch_digitize(const float *wf, int16_t *adc, int n_wires, int n_ticks, const AdcParams &a, uint32_t c3,
                             cudaStream_t s);
-// Impact-resolution scatter of unfused patches onto n_imp phase grids [phase][wire][tick].
-cudaError_t launch_scatter_phases(int64_t n, const float *patches, const int64_t *desc, int n_imp, int n_wires,
-                                  int n_ticks, float *grids, cudaStream_t s);
+// Impact mode, fused: patches of the depos (windows from launch_prep) added bin by bin to the
+// n_imp phase grids [phase][wire][tick], no patch buffer.
+cudaError_t launch_raster_phases(int64_t n, const DepoDesc *desc, const PlaneParams &pp, uint32_t event_lo,
+                                 float *grids, cudaStream_t s);
+
 cudaError_t launch_row_c2r(const FFTPlan &p, const float2 *spec, int n_rows, float *out, int64_t out_stride,
                            int n_out_cols, cudaStream_t s, int32_t *status = nullptr);
 cudaError_t launch_scale_spectrum(float2 *spec, int64_t n, float scale, cudaStream_t s);

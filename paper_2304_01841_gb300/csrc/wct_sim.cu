@@ -59,11 +59,7 @@ struct wct_sim {
     size_t spec_elems = 0;          // capacity of spec / spec2 (complex elements)
     float2 *spec_imp = nullptr;     // impact mode: the spectra of every phase [phase][wire][Fs]
     size_t spec_imp_elems = 0;
-    // impact mode: unfused patches and their descriptors
-    float *imp_patches = nullptr;
-    int64_t imp_patch_cap = 0;
-    int64_t *imp_desc = nullptr;
-    int64_t imp_desc_cap = 0;
+
     // Accumulation grids of run_event / run_batch: two sets of every plane's grid, kept all
     // zero between uses: the rasterizer flags the tiles it touches, and once the forward
     // transform has read a grid those tiles are cleared again.
@@ -493,43 +489,24 @@ void drop_impact(wct_sim *s, PlaneState &ps) {
     ps.n_phases = 0;
 }
 
-// The impact-mode hot path of one plane: unfused patches (sized by a synchronous query),
-// scattered onto the phase grids, each grid transformed and stenciled with its phase's
-// response into one summed spectrum, one inverse transform.
+// The impact-mode hot path of one plane: windows, then every patch bin added to the phase
+// grid of its sub-bin (fused, no patch buffer), every phase grid's rows transformed in one
+// launch, one wire stage summing all phases' stencils, one inverse transform.
 wct_status_t run_plane_impact(wct_sim *s, int p, const wct_depos_t *d, float *wf, cudaStream_t cs, int slot) {
     PlaneState &ps = s->planes[p];
     const int nw = ps.g.n_wires, nt = ps.g.n_ticks;
     const int64_t n = d->n;
-    wct_status_t st = WCT_OK;
-    if (n > s->imp_desc_cap) {
-        cudaStreamSynchronize(cs);
-        dev_free(s, s->imp_desc, sizeof(int64_t) * 5 * (size_t)s->imp_desc_cap);
-        s->imp_desc = nullptr;
-        s->imp_desc_cap = 0;
-        if ((st = dev_alloc(s, (void **)&s->imp_desc, sizeof(int64_t) * 5 * (size_t)n))) return st;
-        s->imp_desc_cap = n;
-    }
+    wct_status_t st = ensure_depo_capacity(s, n);
+    if (st) return st;
     mark(s, slot, 0, cs);
     cudaError_t e = cudaMemsetAsync(ps.phase_grids, 0, ps.phase_grid_bytes, cs);
     if (e != cudaSuccess) return cuda_fail(s, e, "phase grid clear");
     mark(s, slot, 1, cs);
-    int64_t total = 0;
-    st = wct_sim_rasterize(s, p, d, s->imp_patches, s->imp_patch_cap, s->imp_desc, &total, cs);
-    if ((st == WCT_OK || st == WCT_EINVAL) && total > s->imp_patch_cap) {
-        // the patch buffer was too small: grow it and rasterize again
-        cudaStreamSynchronize(cs);
-        dev_free(s, s->imp_patches, sizeof(float) * (size_t)s->imp_patch_cap);
-        s->imp_patches = nullptr;
-        s->imp_patch_cap = 0;
-        const int64_t cap = std::max<int64_t>(total, 1 << 20);
-        if ((st = dev_alloc(s, (void **)&s->imp_patches, sizeof(float) * (size_t)cap))) return st;
-        s->imp_patch_cap = cap;
-        st = wct_sim_rasterize(s, p, d, s->imp_patches, s->imp_patch_cap, s->imp_desc, &total, cs);
-    }
-    if (st) return st;
-    e = launch_scatter_phases(n, s->imp_patches, s->imp_desc, ps.n_phases, nw, nt, ps.phase_grids, cs);
-    if (e != cudaSuccess) return cuda_fail(s, e, "phase scatter");
-    s->launches += n > 0 ? 1 : 0;
+    const PlaneParams pp = plane_params(s, p);
+    e = launch_prep(*d, pp, s->desc, nullptr, nullptr, s->status, cs);
+    if (e == cudaSuccess) e = launch_raster_phases(n, s->desc, pp, (uint32_t)d->event_id, ps.phase_grids, cs);
+    if (e != cudaSuccess) return cuda_fail(s, e, "phase raster");
+    s->launches += n > 0 ? 2 : 0;
     mark(s, slot, 2, cs);
     // every phase grid's rows in one forward launch, one wire stage over all phases
     e = launch_row_r2c(ps.fft_imp, ps.phase_grids, nt, nt, ps.n_phases * nw, s->spec_imp, cs, s->status);
@@ -993,7 +970,7 @@ wct_status_t wct_sim_run_batch(wct_sim_t *s, const wct_depos_t *events, int n_ev
     cudaStream_t cs = (cudaStream_t)stream;
     for (int p = 0; p < s->n_planes; ++p)
         if (s->planes[p].n_phases > 0) {
-            // impact mode sizes its patches on the host: events one after the other
+            // impact mode: events one after the other (no batched rasterize launch)
             for (int e = 0; e < n_events; ++e) {
                 const wct_status_t st = wct_sim_run_event(s, &events[e], wfs + (size_t)e * s->n_planes, stream);
                 if (st) return st;
