@@ -121,6 +121,20 @@ __device__ __forceinline__ float fold_fluct(const Item &f, const float *wt, cons
     return acc;
 }
 
+// Flag the tiles (tile_w rows x tile_t ticks of a grid with n_tiles_t tiles per row band)
+// covering rows [r0, r1] x ticks [b0, b1], listing each newly flagged tile (layout below).
+__device__ __forceinline__ void flag_tiles(uint32_t *flags, int n_tiles, int n_tiles_t, int tile_w, int tile_t, int r0,
+                                           int r1, int b0, int b1) {
+    for (int tw = r0 / tile_w; tw <= r1 / tile_w; ++tw)
+        for (int tt = b0 / tile_t; tt <= b1 / tile_t; ++tt) {
+            const int t = tw * n_tiles_t + tt;
+            if (flags[t] == 0u && atomicExch(&flags[t], 1u) == 0u) {
+                const uint32_t slot = atomicAdd(&flags[n_tiles], 1u);
+                flags[n_tiles + 2 + slot] = (uint32_t)t;
+            }
+        }
+}
+
 // Flag the grid tiles that depo d's window overlaps (clamped to the grid).  flags holds
 // n_tiles flags, then a counter and a done-counter, then the list of flagged tiles: the
 // first depo to flag a tile appends it to the list.
@@ -129,15 +143,7 @@ __device__ __forceinline__ void mark_tiles(uint32_t *flags, const PlaneParams &p
     const int a0 = max(wl, 0), a1 = min(wl + nw - 1, pp.n_wires - 1);
     const int b0 = max(d.lo_t, 0), b1 = min(d.lo_t + (int)d.nt - 1, pp.n_ticks - 1);
     if (a0 > a1 || b0 > b1) return;
-    const int n_tiles = pp.n_tiles_w * pp.n_tiles_t;
-    for (int tw = a0 / pp.tile_w; tw <= a1 / pp.tile_w; ++tw)
-        for (int tt = b0 / pp.tile_t; tt <= b1 / pp.tile_t; ++tt) {
-            const int t = tw * pp.n_tiles_t + tt;
-            if (flags[t] == 0u && atomicExch(&flags[t], 1u) == 0u) {
-                const uint32_t slot = atomicAdd(&flags[n_tiles], 1u);
-                flags[n_tiles + 2 + slot] = (uint32_t)t;
-            }
-        }
+    flag_tiles(flags, pp.n_tiles_w * pp.n_tiles_t, pp.n_tiles_t, pp.tile_w, pp.tile_t, a0, a1, b0, b1);
 }
 
 __device__ __forceinline__ uint32_t counter_c3(const PlaneParams &pp, uint32_t event_lo) {
@@ -830,7 +836,7 @@ cudaError_t launch_raster_chunks(const wct_depos_t &d, const PlaneParams &pp, ui
 // patch's fluctuated sum, once more to add them rescaled to the depo's charge.
 __global__ void __launch_bounds__(kPatchWarps * 32)
 k_raster_phases(int64_t n, const DepoDesc *__restrict__ desc, PlaneParams pp, uint32_t event_lo,
-                float *__restrict__ grids) {
+                float *__restrict__ grids, uint32_t *flags) {
     __shared__ float wbuf[kPatchWarps][kWBuf];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float *wt = wbuf[warp];
@@ -855,6 +861,17 @@ k_raster_phases(int64_t n, const DepoDesc *__restrict__ desc, PlaneParams pp, ui
         const int GD = cnt0 + (nw > 2 ? (nw - 2) * G : 0) + cnt_l;
         const int U = nt * GD;
         const float q = d.q;
+        if (flags) {
+            // the phase grids form one grid of n_imp * n_wires rows: flag the tiles under this
+            // window in every phase's rows
+            const int a0 = max(wl, 0), a1 = min(wl + nw - 1, pp.n_wires - 1);
+            const int b0 = max(d.lo_t, 0), b1 = min(d.lo_t + nt - 1, pp.n_ticks - 1);
+            const int n_tiles_w = (n_imp * pp.n_wires + pp.tile_w - 1) / pp.tile_w;
+            if (a0 <= a1 && b0 <= b1)
+                for (int ph = lane; ph < n_imp; ph += 32)
+                    flag_tiles(flags, n_tiles_w * pp.n_tiles_t, pp.n_tiles_t, pp.tile_w, pp.tile_t, ph * pp.n_wires + a0,
+                               ph * pp.n_wires + a1, b0, b1);
+        }
         // unit u -> (window tick a, wire, group g) and its lanes [l0, l1) of the group
         auto unit = [&](int u, int &a, int &wire, int &g, int &l0, int &l1) {
             a = u / GD;
@@ -922,11 +939,11 @@ k_raster_phases(int64_t n, const DepoDesc *__restrict__ desc, PlaneParams pp, ui
 }
 
 cudaError_t launch_raster_phases(int64_t n, const DepoDesc *desc, const PlaneParams &pp, uint32_t event_lo,
-                                 float *grids, cudaStream_t s) {
+                                 float *grids, uint32_t *flags, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     int64_t blocks = (n + kPatchWarps - 1) / kPatchWarps;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    k_raster_phases<<<(unsigned)blocks, kPatchWarps * 32, 0, s>>>(n, desc, pp, event_lo, grids);
+    k_raster_phases<<<(unsigned)blocks, kPatchWarps * 32, 0, s>>>(n, desc, pp, event_lo, grids, flags);
     return cudaGetLastError();
 }
 

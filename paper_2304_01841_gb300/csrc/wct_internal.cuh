@@ -176,8 +176,10 @@ cudaError_t launch_digitize(const float *wf, int16_t *adc, int n_wires, int n_ti
                             cudaStream_t s);
 // Impact mode, fused: patches of the depos (windows from launch_prep) added bin by bin to the
 // n_imp phase grids [phase][wire][tick], no patch buffer.
+// flags: touched-tile flags of the phase grids seen as one (n_imp * n_wires) x n_ticks grid
+// with pp's tiling (or null)
 cudaError_t launch_raster_phases(int64_t n, const DepoDesc *desc, const PlaneParams &pp, uint32_t event_lo,
-                                 float *grids, cudaStream_t s);
+                                 float *grids, uint32_t *flags, cudaStream_t s);
 
 cudaError_t launch_row_c2r(const FFTPlan &p, const float2 *spec, int n_rows, float *out, int64_t out_stride,
                            int n_out_cols, cudaStream_t s, int32_t *status = nullptr);

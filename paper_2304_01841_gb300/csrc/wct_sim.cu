@@ -42,8 +42,11 @@ struct PlaneState {
     FFTPlan fft_imp{};
     float2 *resp_imp = nullptr;    // [n_phases][WCT_MAX_RESPONSE_WIRES][fft_imp.Fs], scaled by 1/M
     size_t resp_imp_bytes = 0;
-    float *phase_grids = nullptr;  // [n_phases][n_wires][n_ticks]
+    float *phase_grids = nullptr;  // [n_phases][n_wires][n_ticks], all zero between events
     size_t phase_grid_bytes = 0;
+    uint32_t *phase_flags = nullptr;   // touched-tile flags + list of the phase grids (one grid)
+    size_t phase_flag_bytes = 0;
+    int phase_tiles = 0;
 };
 
 }  // namespace
@@ -399,6 +402,11 @@ void clear_grids(wct_sim *s) {
         if (s->grids[b]) cudaMemset(s->grids[b], 0, sizeof(float) * s->grid_off[s->n_planes]);
         if (s->tile_flags[b]) cudaMemset(s->tile_flags[b], 0, sizeof(uint32_t) * s->flag_off[s->n_planes]);
     }
+    for (int p = 0; p < s->n_planes; ++p) {
+        const PlaneState &ps = s->planes[p];
+        if (ps.phase_grids) cudaMemset(ps.phase_grids, 0, ps.phase_grid_bytes);
+        if (ps.phase_flags) cudaMemset(ps.phase_flags, 0, ps.phase_flag_bytes);
+    }
     cudaDeviceSynchronize();
 }
 
@@ -483,10 +491,27 @@ double spectrum_max(const std::vector<float2> &h, const FFTPlan &full) {
 void drop_impact(wct_sim *s, PlaneState &ps) {
     dev_free(s, ps.resp_imp, ps.resp_imp_bytes);
     dev_free(s, ps.phase_grids, ps.phase_grid_bytes);
+    dev_free(s, ps.phase_flags, ps.phase_flag_bytes);
     ps.resp_imp = nullptr;
     ps.phase_grids = nullptr;
-    ps.resp_imp_bytes = ps.phase_grid_bytes = 0;
+    ps.phase_flags = nullptr;
+    ps.resp_imp_bytes = ps.phase_grid_bytes = ps.phase_flag_bytes = 0;
+    ps.phase_tiles = 0;
     ps.n_phases = 0;
+}
+
+// The clearing side job of the phase grids (one grid of n_phases * n_wires rows).
+ClearJob phase_clear_job(const PlaneState &ps) {
+    ClearJob j;
+    j.grid = ps.phase_grids;
+    j.flags = ps.phase_flags;
+    j.n_wires = ps.n_phases * ps.g.n_wires;
+    j.n_ticks = ps.g.n_ticks;
+    j.tile_w = ps.pp.tile_w;
+    j.tile_t = ps.pp.tile_t;
+    j.n_tiles_t = ps.pp.n_tiles_t;
+    j.n_tiles = ps.phase_tiles;
+    return j;
 }
 
 // The impact-mode hot path of one plane: windows, then every patch bin added to the phase
@@ -498,13 +523,13 @@ wct_status_t run_plane_impact(wct_sim *s, int p, const wct_depos_t *d, float *wf
     const int64_t n = d->n;
     wct_status_t st = ensure_depo_capacity(s, n);
     if (st) return st;
+    // the phase grids are all zero: the wire stage clears the tiles this event touches
     mark(s, slot, 0, cs);
-    cudaError_t e = cudaMemsetAsync(ps.phase_grids, 0, ps.phase_grid_bytes, cs);
-    if (e != cudaSuccess) return cuda_fail(s, e, "phase grid clear");
     mark(s, slot, 1, cs);
     const PlaneParams pp = plane_params(s, p);
-    e = launch_prep(*d, pp, s->desc, nullptr, nullptr, s->status, cs);
-    if (e == cudaSuccess) e = launch_raster_phases(n, s->desc, pp, (uint32_t)d->event_id, ps.phase_grids, cs);
+    cudaError_t e = launch_prep(*d, pp, s->desc, nullptr, nullptr, s->status, cs);
+    if (e == cudaSuccess)
+        e = launch_raster_phases(n, s->desc, pp, (uint32_t)d->event_id, ps.phase_grids, ps.phase_flags, cs);
     if (e != cudaSuccess) return cuda_fail(s, e, "phase raster");
     s->launches += n > 0 ? 2 : 0;
     mark(s, slot, 2, cs);
@@ -512,7 +537,8 @@ wct_status_t run_plane_impact(wct_sim *s, int p, const wct_depos_t *d, float *wf
     e = launch_row_r2c(ps.fft_imp, ps.phase_grids, nt, nt, ps.n_phases * nw, s->spec_imp, cs, s->status);
     if (e != cudaSuccess) return cuda_fail(s, e, "phase transforms");
     mark(s, slot, 3, cs);
-    e = launch_wire_stage(ps.fft_imp, s->spec_imp, ps.resp_imp, nw, s->spec2, cs, s->status, nullptr, false,
+    const ClearJob job = phase_clear_job(ps);
+    e = launch_wire_stage(ps.fft_imp, s->spec_imp, ps.resp_imp, nw, s->spec2, cs, s->status, &job, false,
                           ps.n_phases);
     if (e != cudaSuccess) return cuda_fail(s, e, "phase stencils");
     s->launches += 2;
@@ -842,7 +868,10 @@ wct_status_t wct_sim_run_event(wct_sim_t *s, const wct_depos_t *d, float *const 
         // accumulate into the library grid (all zero), which the forward transform clears
         // again as it reads it; the inverse transform writes the caller's waveform
         if (s->planes[p].n_phases > 0) {
-            if ((st = run_plane_impact(s, p, d, wfs[p], cs, acquire_slot(s)))) return st;
+            if ((st = run_plane_impact(s, p, d, wfs[p], cs, acquire_slot(s)))) {
+                clear_grids(s);
+                return st;
+            }
             continue;
         }
         float *grid = s->grids[0] + s->grid_off[p];
@@ -1193,6 +1222,18 @@ wct_status_t wct_sim_set_impact_responses(wct_sim_t *s, int plane, const wct_res
         ps.phase_grid_bytes = sizeof(float) * (size_t)n_phases * ps.g.n_wires * ps.g.n_ticks;
         st = dev_alloc(s, (void **)&ps.phase_grids, ps.phase_grid_bytes);
     }
+    if (st == WCT_OK) {
+        const int tiles_w = (n_phases * ps.g.n_wires + ps.pp.tile_w - 1) / ps.pp.tile_w;
+        ps.phase_tiles = tiles_w * ps.pp.n_tiles_t;
+        ps.phase_flag_bytes = sizeof(uint32_t) * (2 * (size_t)ps.phase_tiles + 2);
+        st = dev_alloc(s, (void **)&ps.phase_flags, ps.phase_flag_bytes);
+    }
+    if (st == WCT_OK) {
+        cudaError_t e = cudaMemset(ps.phase_grids, 0, ps.phase_grid_bytes);
+        if (e == cudaSuccess) e = cudaMemset(ps.phase_flags, 0, ps.phase_flag_bytes);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) st = cuda_fail(s, e, "phase grid init");
+    }
     const size_t need_imp = (size_t)n_phases * need;
     if (st == WCT_OK && need_imp > s->spec_imp_elems) {
         dev_free(s, s->spec_imp, sizeof(float2) * s->spec_imp_elems);
@@ -1275,13 +1316,9 @@ wct_status_t wct_sim_sync(wct_sim_t *s, void *stream) {
     e = cudaMemcpy(&code, s->status, sizeof(int32_t), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemset(s->status, 0, sizeof(int32_t));
     if (e == cudaSuccess && code != 0) {
-        // a device-side error may have left a grid row uncleared: restore the all-zero grids
-        for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
-            if (s->grids[b]) e = cudaMemset(s->grids[b], 0, sizeof(float) * s->grid_off[s->n_planes]);
-            if (e == cudaSuccess && s->tile_flags[b])
-                e = cudaMemset(s->tile_flags[b], 0, sizeof(uint32_t) * s->flag_off[s->n_planes]);
-        }
-        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        // a device-side error may have left a grid tile uncleared: restore the all-zero grids
+        clear_grids(s);
+        e = cudaGetLastError();
     }
     if (e != cudaSuccess) return cuda_fail(s, e, "status read");
     if (code == ST_EINVAL) return fail(s, WCT_EINVAL, "invalid depo(s) skipped (non-finite, x<0, q<0 or window too large)");
