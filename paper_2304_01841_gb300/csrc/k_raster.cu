@@ -398,6 +398,8 @@ __device__ __forceinline__ void raster_warp(WarpSmem &S, const float *__restrict
     if (c0 >= n) return;
     const int cn = (int)((n - c0) < kWarpDepos ? (n - c0) : kWarpDepos);
     const uint32_t c3 = counter_c3(pp, event_lo);
+    // per depo (lane < cn): window, its item / edge counts and clamped grid footprint
+    int ni = 0, nwt = 0, fa0 = INT_MAX, fa1 = INT_MIN, fb0 = INT_MAX, fb1 = INT_MIN;
     if (lane < cn) {
         const int64_t i = c0 + lane;
         DepoDesc d;
@@ -408,15 +410,50 @@ __device__ __forceinline__ void raster_warp(WarpSmem &S, const float *__restrict
         if (d.nt > 0) {
             wl = floor_div(d.lo_p, pp.n_imp);
             nw = floor_div(d.lo_p + d.np - 1, pp.n_imp) - wl + 1;
+            ni = (int)d.nt * nw;
+            nwt = (int)d.nt + (int)d.np + 2;
+            const int a0 = max(wl, 0), a1 = min(wl + nw - 1, pp.n_wires - 1);
+            const int b0 = max(d.lo_t, 0), b1 = min(d.lo_t + (int)d.nt - 1, pp.n_ticks - 1);
+            if (a0 <= a1 && b0 <= b1) fa0 = a0, fa1 = a1, fb0 = b0, fb1 = b1;
         }
         S.wl[lane] = wl;
         S.nw[lane] = nw;
         mark_tiles(flags, pp, d, wl, nw);
         S.sum[lane] = 0.f;
     }
+    // one pass for all cn depos when their items and edges fit (the common case): offsets by
+    // warp prefix sums, footprint by warp reductions; otherwise lane 0 packs passes greedily
+    int inc_i = ni, inc_w = nwt;
+#pragma unroll
+    for (int o = 1; o < kWarpDepos; o <<= 1) {
+        const int vi = __shfl_up_sync(0xffffffffu, inc_i, o), vw = __shfl_up_sync(0xffffffffu, inc_w, o);
+        if (lane >= o) inc_i += vi, inc_w += vw;
+    }
+    const int tot_i = __shfl_sync(0xffffffffu, inc_i, cn - 1), tot_w = __shfl_sync(0xffffffffu, inc_w, cn - 1);
+    const bool one_pass = tot_i <= kWItemCap && tot_w <= kWWCap;
+    if (one_pass) {
+        const int w0 = __reduce_min_sync(0xffffffffu, fa0), w1 = __reduce_max_sync(0xffffffffu, fa1);
+        const int t0b = __reduce_min_sync(0xffffffffu, fb0), t1b = __reduce_max_sync(0xffffffffu, fb1);
+        if (lane < cn) {
+            S.item_off[lane] = inc_i - ni;
+            S.w_off[lane] = inc_w - nwt;
+        }
+        if (lane == 0) {
+            S.item_off[cn] = tot_i;
+            S.w_off[cn] = tot_w;
+            S.pass_end = cn;
+            const bool any = w0 <= w1;
+            const int64_t area = any ? (int64_t)(w1 - w0 + 1) * (t1b - t0b + 1) : 0;
+            S.use_box = any && area <= kWBoxCap;
+            S.box_w0 = w0;
+            S.box_t0 = t0b;
+            S.box_nw = any ? w1 - w0 + 1 : 0;
+            S.box_nt = any ? t1b - t0b + 1 : 0;
+        }
+    }
     __syncwarp();
     for (int s = 0; s < cn;) {
-        if (lane == 0) {
+        if (lane == 0 && !one_pass) {
             int it = 0, ww = 0, e = s;
             int w0 = INT_MAX, w1 = INT_MIN, t0b = INT_MAX, t1b = INT_MIN;
             for (; e < cn; ++e) {
