@@ -207,6 +207,13 @@ def test_event_three_plane_reduced():
     _event_parity(wl, wl.depos(n_depos=100_000))
 
 
+def test_event_three_plane_full_waveforms():
+    # the full 1M-depo three-plane event (800k on 200 tracks + 200k isolated), waveforms of
+    # every plane against the oracle
+    wl = synth.workload("three_plane")
+    _event_parity(wl, wl.depos(), check_grid=False)
+
+
 # ------------------------------------------------------------------------------------------
 # Edge cases
 # ------------------------------------------------------------------------------------------
