@@ -264,6 +264,19 @@ typedef struct {
 wct_status_t wct_sim_digitize(wct_sim_t *sim, int plane, const float *waveform, int16_t *adc,
                               const wct_adc_t *params, uint64_t event_id, void *stream);
 
+/* Coloured noise for wct_sim_digitize on one plane: amplitude[f] (HOST, ADC counts) for the
+ * n_bins = fft_length / 2 + 1 bins of the plane's transform (wct_sim_plane_info info[3]).
+ * While set, the digitiser's noise is, per wire w, the first n_ticks samples of the inverse
+ * real DFT of length fft_length (normalised by 1 / fft_length) of
+ *     N[w][f] = noise_rms * amplitude[f] * (z_re + i z_im) / sqrt(2)
+ * (z_im = 0 at f = 0 and f = fft_length / 2), z from the Philox stream at counter
+ * (f / 2, wire, 1, (0x80 | plane) << 24 | event id), words 0,1 for bin 2k and 2,3 for bin 2k+1
+ * as Box-Muller pairs; E|N[w][f]|^2 = (noise_rms amplitude[f])^2 for the complex bins.
+ * amplitude == NULL switches back to white noise.  Library memory: the spectrum and waveform
+ * of one plane.  Synchronous.  WCT_EINVAL for a wrong n_bins or a negative / non-finite
+ * amplitude. */
+wct_status_t wct_sim_set_noise_spectrum(wct_sim_t *sim, int plane, const float *amplitude, int n_bins);
+
 /* Drift attenuation by the electron lifetime, the step before the rasterization of §2: every
  * depo's charge q becomes the surviving charge of Binomial(q, p), p = exp(-t_d / lifetime),
  * t_d = x / v_drift: its mean q p, or (fluctuate != 0) the normal approximation

@@ -282,19 +282,55 @@ def noise_normals(seed: int, n_wires: int, n_ticks: int, plane_index: int, event
     return z.reshape(n_wires, nq * 4)[:, :n_ticks]
 
 
+def coloured_noise(seed: int, n_wires: int, n_ticks: int, fft_length: int, amplitude: np.ndarray,
+                   noise_rms: float, plane_index: int, event_id: int) -> np.ndarray:
+    """Coloured noise [wire][tick] (FP64): the first n_ticks samples of the inverse real DFT of
+    length fft_length (numpy's normalisation, 1 / fft_length) of
+        N[w][f] = noise_rms * amplitude[f] * (z_re + i z_im) / sqrt(2),   f = 0 .. fft_length / 2,
+    z_im = 0 at f = 0 and f = fft_length / 2; z from Philox4x32-10 at counter
+    (f // 2, wire, 1, (0x80 | plane) << 24 | event id mod 2^24) under the seed's key, words
+    (0, 1) for bin 2k and (2, 3) for bin 2k+1 as Box-Muller pairs."""
+    F = fft_length // 2 + 1
+    pairs = (F + 1) // 2
+    w, k = np.meshgrid(np.arange(n_wires), np.arange(pairs), indexing="ij")
+    ctr = np.zeros((n_wires * pairs, 4), dtype=np.uint32)
+    ctr[:, 0] = k.ravel().astype(np.uint32)
+    ctr[:, 1] = w.ravel().astype(np.uint32)
+    ctr[:, 2] = 1
+    ctr[:, 3] = np.uint32(((0x80 | plane_index) << 24) | (int(event_id) & 0xFFFFFF))
+    x = philox4x32_10(ctr, (int(seed) & 0xFFFFFFFF, (int(seed) >> 32) & 0xFFFFFFFF)).astype(np.float64)
+    u = (x + 0.5) * 2.0 ** -32
+    r01 = np.sqrt(-2.0 * np.log(u[:, 0]))
+    r23 = np.sqrt(-2.0 * np.log(u[:, 2]))
+    zr = np.stack([r01 * np.cos(2 * np.pi * u[:, 1]), r23 * np.cos(2 * np.pi * u[:, 3])], axis=1)
+    zi = np.stack([r01 * np.sin(2 * np.pi * u[:, 1]), r23 * np.sin(2 * np.pi * u[:, 3])], axis=1)
+    zr = zr.reshape(n_wires, 2 * pairs)[:, :F]
+    zi = zi.reshape(n_wires, 2 * pairs)[:, :F].copy()
+    zi[:, 0] = 0.0
+    if fft_length % 2 == 0:
+        zi[:, F - 1] = 0.0
+    N = noise_rms * np.asarray(amplitude, dtype=np.float64)[None, :] * (zr + 1j * zi) / np.sqrt(2.0)
+    return np.fft.irfft(N, n=fft_length, axis=1)[:, :n_ticks]
+
+
 def digitize(waveform: np.ndarray, gain: float, baseline: float, noise_rms: float, bits: int, add_noise: bool,
-             seed: int, plane_index: int, event_id: int):
-    """ADC codes of a float32 waveform: code = clamp(floor(gain v + baseline + noise_rms z + 1/2),
+             seed: int, plane_index: int, event_id: int, noise_wave: Optional[np.ndarray] = None):
+    """ADC codes of a float32 waveform: code = clamp(floor(gain v + baseline + noise + 1/2),
     0, 2^bits - 1), the integer decided in FP32 with each operation rounded separately in that
-    order (as the device does), z = noise_normals(...) rounded to FP32.  Returns (codes int16,
-    the FP32 value before rounding)."""
+    order (as the device does).  noise = noise_rms z with z = noise_normals(...) rounded to FP32
+    (white), or the given noise waveform rounded to FP32 (coloured, see coloured_noise).
+    Returns (codes int16, the FP32 value before rounding)."""
     f32 = np.float32
     v = np.asarray(waveform, dtype=np.float32)
     nw, nt = v.shape
-    z = (noise_normals(seed, nw, nt, plane_index, event_id).astype(np.float32) if add_noise and noise_rms > 0
-         else np.zeros_like(v))
+    if add_noise and noise_wave is not None:
+        nz = np.asarray(noise_wave, dtype=np.float32)
+    elif add_noise and noise_rms > 0:
+        nz = f32(noise_rms) * noise_normals(seed, nw, nt, plane_index, event_id).astype(np.float32)
+    else:
+        nz = np.zeros_like(v)
     with np.errstate(invalid="ignore", over="ignore"):
-        s = (f32(gain) * v + f32(baseline)) + f32(noise_rms) * z
+        s = (f32(gain) * v + f32(baseline)) + nz
         code = np.floor(s + f32(0.5))
         code = np.where(np.isnan(code), f32(0), code)
         code = np.clip(code, f32(0), f32((1 << bits) - 1))

@@ -196,6 +196,14 @@ class Simulator:
                                                int(event_id) & 0xFFFFFFFFFFFFFFFF, _stream_handle(stream)))
         return out
 
+    def set_noise_spectrum(self, plane: int, amplitude: Optional[np.ndarray]):
+        """wct_sim_set_noise_spectrum: coloured-noise amplitudes per spectrum bin (None: white)."""
+        if amplitude is None:
+            self._check(self._lib.wct_sim_set_noise_spectrum(self._h, plane, None, 0))
+            return
+        a = np.ascontiguousarray(amplitude, dtype=np.float32)
+        self._check(self._lib.wct_sim_set_noise_spectrum(self._h, plane, a.ctypes.data, int(a.size)))
+
     def set_lifetime(self, lifetime_us: float, fluctuate: bool = False):
         """wct_sim_set_lifetime: electron-lifetime attenuation of the drifting charge (<= 0: off)."""
         self._check(self._lib.wct_sim_set_lifetime(self._h, float(lifetime_us), int(bool(fluctuate))))

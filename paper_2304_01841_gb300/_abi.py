@@ -74,6 +74,7 @@ EXPORTS = {
     "wct_sim_convolve_impact": ([c_vp, ctypes.c_int, c_vp, c_vp, c_vp], ctypes.c_int),
     "wct_sim_run_host": ([c_vp, ctypes.POINTER(wct_host_depos_t), ctypes.c_int, ctypes.POINTER(c_vp)], ctypes.c_int),
     "wct_sim_digitize": ([c_vp, ctypes.c_int, c_vp, c_vp, ctypes.POINTER(wct_adc_t), c_u64, c_vp], ctypes.c_int),
+    "wct_sim_set_noise_spectrum": ([c_vp, ctypes.c_int, c_vp, ctypes.c_int], ctypes.c_int),
     "wct_sim_set_lifetime": ([c_vp, ctypes.c_double, c_i32], ctypes.c_int),
     "wct_sim_sync": ([c_vp, c_vp], ctypes.c_int),
     "wct_sim_plane_info": ([c_vp, ctypes.c_int, ctypes.POINTER(c_i64)], ctypes.c_int),

@@ -170,8 +170,12 @@ cudaError_t launch_wire_stage(const FFTPlan &p, const float2 *spec, const float2
 struct AdcParams {
     float gain, baseline, noise_rms, max_code;
     int32_t add_noise;
-    uint32_t rk[20];   // Philox round keys of the seed
+    uint32_t rk[20];            // Philox round keys of the seed
+    const float *noise_wave;    // coloured noise [n_wires][n_ticks] to add (null: white noise)
 };
+// Coloured-noise spectrum [n_wires][Fs] (scale folds the inverse transform's 1/M and noise_rms)
+cudaError_t launch_noise_spectrum(const float *amp, int F, int M, int n_wires, int Fs, float scale, const AdcParams &a,
+                                  uint32_t c3, float2 *spec, cudaStream_t s);
 cudaError_t launch_digitize(const float *wf, int16_t *adc, int n_wires, int n_ticks, const AdcParams &a, uint32_t c3,
                             cudaStream_t s);
 // Impact mode, fused: patches of the depos (windows from launch_prep) added bin by bin to the

@@ -47,6 +47,11 @@ struct PlaneState {
     uint32_t *phase_flags = nullptr;   // touched-tile flags + list of the phase grids (one grid)
     size_t phase_flag_bytes = 0;
     int phase_tiles = 0;
+    // coloured noise of the digitiser: amplitude per spectrum bin, spectrum and waveform scratch
+    float *noise_amp = nullptr;
+    float2 *noise_spec = nullptr;
+    float *noise_wave = nullptr;
+    size_t noise_bytes[3] = {0, 0, 0};
 };
 
 }  // namespace
@@ -1285,11 +1290,66 @@ wct_status_t wct_sim_digitize(wct_sim_t *s, int plane, const float *waveform, in
     ap.max_code = (float)((1 << a.bits) - 1);
     ap.add_noise = a.add_noise && a.noise_rms > 0 ? 1 : 0;
     for (int k = 0; k < 20; ++k) ap.rk[k] = ps.pp.rk[k];
+    ap.noise_wave = nullptr;
     const uint32_t c3 = ((uint32_t)(0x80 | plane) << 24) | ((uint32_t)event_id & 0xFFFFFFu);
-    const cudaError_t e = launch_digitize(waveform, adc, ps.g.n_wires, ps.g.n_ticks, ap, c3, (cudaStream_t)stream);
+    cudaStream_t cs = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (ap.add_noise && ps.noise_amp) {
+        // coloured noise: spectrum from the plane's amplitudes, inverse row transform (the
+        // transform's 1/M folded into the scale), then added by the digitiser
+        FFTPlan full = ps.fft;
+        full.Fs = full.Fu = (int32_t)((full.M + 2) & ~1);
+        e = launch_noise_spectrum(ps.noise_amp, full.F, full.M, ps.g.n_wires, full.Fs, ap.noise_rms / (float)full.M, ap,
+                                  c3, ps.noise_spec, cs);
+        if (e == cudaSuccess)
+            e = launch_row_c2r(full, ps.noise_spec, ps.g.n_wires, ps.noise_wave, ps.g.n_ticks, ps.g.n_ticks, cs, s->status);
+        ap.noise_wave = ps.noise_wave;
+        s->launches += 2;
+    }
+    if (e == cudaSuccess) e = launch_digitize(waveform, adc, ps.g.n_wires, ps.g.n_ticks, ap, c3, cs);
     if (e != cudaSuccess) return cuda_fail(s, e, "digitize");
     s->launches += 1;
     return WCT_OK;
+}
+
+wct_status_t wct_sim_set_noise_spectrum(wct_sim_t *s, int plane, const float *amplitude, int n_bins) {
+    wct_status_t st = plane_check(s, plane);
+    if (st) return st;
+    PlaneState &ps = s->planes[plane];
+    cudaDeviceSynchronize();                           // nothing may still use the old buffers
+    dev_free(s, ps.noise_amp, ps.noise_bytes[0]);
+    dev_free(s, ps.noise_spec, ps.noise_bytes[1]);
+    dev_free(s, ps.noise_wave, ps.noise_bytes[2]);
+    ps.noise_amp = nullptr;
+    ps.noise_spec = nullptr;
+    ps.noise_wave = nullptr;
+    ps.noise_bytes[0] = ps.noise_bytes[1] = ps.noise_bytes[2] = 0;
+    if (!amplitude) return WCT_OK;                     // back to white noise
+    if (n_bins != ps.fft.F) return fail(s, WCT_EINVAL, "n_bins must equal the plane's spectrum bins (fft_length / 2 + 1)");
+    for (int f = 0; f < n_bins; ++f)
+        if (!std::isfinite(amplitude[f]) || amplitude[f] < 0.f) return fail(s, WCT_EINVAL, "amplitudes must be finite and >= 0");
+    const size_t fs_full = (size_t)((ps.fft.M + 2) & ~1);
+    const size_t bytes[3] = {sizeof(float) * (size_t)n_bins, sizeof(float2) * (size_t)ps.g.n_wires * fs_full,
+                             sizeof(float) * (size_t)ps.g.n_wires * ps.g.n_ticks};
+    void **ptr[3] = {(void **)&ps.noise_amp, (void **)&ps.noise_spec, (void **)&ps.noise_wave};
+    for (int k = 0; k < 3 && st == WCT_OK; ++k) {
+        st = dev_alloc(s, ptr[k], bytes[k]);
+        if (st == WCT_OK) ps.noise_bytes[k] = bytes[k];
+    }
+    if (st == WCT_OK) {
+        const cudaError_t e = cudaMemcpy(ps.noise_amp, amplitude, bytes[0], cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) st = cuda_fail(s, e, "noise spectrum");
+    }
+    if (st) {
+        dev_free(s, ps.noise_amp, ps.noise_bytes[0]);
+        dev_free(s, ps.noise_spec, ps.noise_bytes[1]);
+        dev_free(s, ps.noise_wave, ps.noise_bytes[2]);
+        ps.noise_amp = nullptr;
+        ps.noise_spec = nullptr;
+        ps.noise_wave = nullptr;
+        ps.noise_bytes[0] = ps.noise_bytes[1] = ps.noise_bytes[2] = 0;
+    }
+    return st;
 }
 
 wct_status_t wct_sim_set_lifetime(wct_sim_t *s, double lifetime_us, int32_t fluctuate) {

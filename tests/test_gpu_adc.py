@@ -62,3 +62,34 @@ def test_event_waveform_digitizes_in_range():
     sim.sync()
     assert codes.dtype == np.int16 and codes.min() >= 0 and codes.max() <= 4095
     assert abs(float(np.median(codes)) - 500.0) <= 2
+
+
+def test_coloured_noise_codes_match_oracle():
+    # a per-plane noise spectrum: the device's noise (spectrum from Philox, inverse row
+    # transform) against the FP64 oracle, through the codes of a flat waveform with unit gain:
+    # codes may differ only where the value sits within 1e-3 of a rounding boundary
+    nw, nt = 300, 9600
+    pl = synth.Plane(nw, nt)
+    sim = make_sim([pl], [synth.make_response("bipolar")], synth.Diffusion(seed=41))
+    info = sim.plane_info(0)
+    F, P = info["spectrum_bins"], info["fft_length"]
+    f = np.arange(F)
+    amp = (1.0 / (1.0 + (f / 300.0) ** 2)).astype(np.float32)          # low-pass shape
+    sim.set_noise_spectrum(0, amp)
+    rms = 2000.0                                                       # noise std ~ 6 counts
+    v = np.random.default_rng(8).normal(size=(nw, nt)).astype(np.float32) * 20.0
+    got = to_np(sim.digitize(0, torch.from_numpy(v).cuda(), 1.0, 1500.0, rms, bits=12, event_id=77))
+    sim.sync()
+    noise = oracle.coloured_noise(41, nw, nt, P, amp, rms, 0, 77)
+    assert noise.std() > 3.0                                           # the noise is there
+    want, s = oracle.digitize(v, 1.0, 1500.0, rms, 12, True, 41, 0, 77, noise_wave=noise)
+    diff = got.astype(np.int32) - want.astype(np.int32)
+    bad = diff != 0
+    dist = np.abs((s - np.floor(s)) - 0.5)
+    assert np.all(np.abs(diff) <= 1) and np.all(dist[bad] < 1e-3) and bad.mean() < 1e-3
+    # back to white noise
+    sim.set_noise_spectrum(0, None)
+    w = to_np(sim.digitize(0, torch.from_numpy(v).cuda(), 1.0, 1500.0, 2.0, bits=12, event_id=77))
+    sim.sync()
+    ww, _ = oracle.digitize(v, 1.0, 1500.0, 2.0, 12, True, 41, 0, 77)
+    assert (w != ww).mean() < 1e-3
