@@ -225,7 +225,6 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "planes": "1 x 3456 wires x 9600 ticks", "depos_per_event": 100_000,
                    "fluctuation": True, "sample_depos_per_step": ORACLE_SAMPLE_DEPOS},
-        "events_per_s": args.steps / total,
         "cpu_baseline": {"value": value, "unit": "depos/s", "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "depos/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
