@@ -49,7 +49,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched / served measurements")
     ap.add_argument("--schedule", type=int, default=-1,
-                    help="row-transform schedule: -1 default, 0 register-staged, 1 persistent bulk-copy")
+                    help="kernel schedule: -1 default, 0 register-staged rows, 1 persistent bulk-copy rows, "
+                         "4 paired rows, 8 paired rows with composite radices; +2 CTA-level rasterizer")
     return ap.parse_args()
 
 

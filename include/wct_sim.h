@@ -101,7 +101,10 @@ typedef struct {
 /*
  * Library options.  hbm_budget_bytes: upper bound on the library's own device memory
  * (0 = unlimited); a call whose scratch would exceed it returns WCT_ENOMEM.
- * schedule_id: kernel-schedule choice (-1 = the library's default / tuned choice).
+ * schedule_id: kernel-schedule choice, kept per handle.  -1 = the library's default
+ * (paired row transforms with composite radices, warp-level rasterizer).  Otherwise a bit set:
+ * row transforms 0 register-staged, 1 one persistent CTA per SM, 4 two paired CTAs per SM,
+ * 8 paired with composite radices; +2 selects the CTA-level rasterizer.
  * deterministic: reserved (0).
  */
 typedef struct {

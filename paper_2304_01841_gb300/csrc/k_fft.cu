@@ -149,6 +149,89 @@ struct Dft<5, INV> : DftOdd<5, INV> {};
 template <bool INV>
 struct Dft<7, INV> : DftOdd<7, INV> {};
 
+// ---- compile-time roots of unity for the composite butterflies --------------------------
+// Taylor series of sin / cos on [-pi, pi] (17 terms: the first omitted term is below 1e-19),
+// evaluated by the compiler in double and rounded once to float.
+__host__ __device__ constexpr double ct_sin(double x) {
+    double term = x, sum = x;
+    for (int n = 1; n <= 16; ++n) {
+        term *= -x * x / ((2.0 * n) * (2.0 * n + 1.0));
+        sum += term;
+    }
+    return sum;
+}
+__host__ __device__ constexpr double ct_cos(double x) {
+    double term = 1.0, sum = 1.0;
+    for (int n = 1; n <= 16; ++n) {
+        term *= -x * x / ((2.0 * n - 1.0) * (2.0 * n));
+        sum += term;
+    }
+    return sum;
+}
+// exp(s 2 pi i m / R), s = -1 forward, +1 inverse; the angle is reduced to (-pi, pi] exactly
+// through m mod R before it is formed
+template <int R, int m, bool INV>
+struct Root {
+    static constexpr int mm = ((m % R) + R) % R;
+    static constexpr int mr = 2 * mm > R ? mm - R : mm;
+    static constexpr double a = 2.0 * 3.14159265358979323846 * (double)mr / (double)R;
+    static constexpr float re = (float)ct_cos(a);
+    static constexpr float im = (float)((INV ? 1.0 : -1.0) * ct_sin(a));
+};
+
+// Size R1 R2 DFT in registers by one Cooley-Tukey split: with r = r1 + R1 r2 and
+// s = R2 s1 + s2, X[s] = sum_r1 w_R1^(r1 s1) [w_R^(r1 s2) sum_r2 v[r1 + R1 r2] w_R2^(r2 s2)]
+// (w_n = exp(s 2 pi i / n)): R1 DFTs of size R2, the inner twiddles, R2 DFTs of size R1.
+// Lets one Stockham pass through shared memory do the work of two.
+template <int R1, int R2, bool INV>
+struct DftComp {
+    static constexpr int R = R1 * R2;
+    template <int I>
+    __device__ __forceinline__ static void twiddle(float2 (&y)[R1][R2]) {
+        if constexpr (I < R) {
+            constexpr int r1 = I / R2, s2 = I % R2;
+            if constexpr (r1 > 0 && s2 > 0) {
+                using W = Root<R, r1 * s2, INV>;
+                y[r1][s2] = cmul(y[r1][s2], make_float2(W::re, W::im));
+            }
+            twiddle<I + 1>(y);
+        }
+    }
+    __device__ __forceinline__ static void run(float2 *v) {
+        float2 y[R1][R2];
+#pragma unroll
+        for (int r1 = 0; r1 < R1; ++r1) {
+#pragma unroll
+            for (int r2 = 0; r2 < R2; ++r2) y[r1][r2] = v[r1 + R1 * r2];
+            Dft<R2, INV>::run(y[r1]);
+        }
+        twiddle<0>(y);
+#pragma unroll
+        for (int s2 = 0; s2 < R2; ++s2) {
+            float2 c[R1];
+#pragma unroll
+            for (int r1 = 0; r1 < R1; ++r1) c[r1] = y[r1][s2];
+            Dft<R1, INV>::run(c);
+#pragma unroll
+            for (int s1 = 0; s1 < R1; ++s1) v[R2 * s1 + s2] = c[s1];
+        }
+    }
+};
+template <bool INV>
+struct Dft<20, INV> : DftComp<4, 5, INV> {};
+template <bool INV>
+struct Dft<25, INV> : DftComp<5, 5, INV> {};
+template <bool INV>
+struct Dft<28, INV> : DftComp<4, 7, INV> {};
+template <bool INV>
+struct Dft<35, INV> : DftComp<5, 7, INV> {};
+
+// R1 of a composite radix above (1 for a plain radix)
+template <int R>
+constexpr int inner_factor() {
+    return (R == 20 || R == 28) ? 4 : (R == 25 || R == 35) ? 5 : 1;
+}
+
 // One Stockham stage of radix R, out of place (in -> out).  With Ns = product of the radices
 // of the earlier stages, butterfly j (j < M/R) reads in[j + r M/R], applies the twiddles
 // exp(s 2 pi i r (j mod Ns) / (Ns R)), does a size-R DFT and writes out[(j div Ns) Ns R +
@@ -630,6 +713,7 @@ k_row_c2r_tma(FFTPlan p, const float2 *__restrict__ spec, int n_rows, float *__r
 // k.  The row copy lands in A; the transform runs A -> B -> A ...; for an odd stage count A is
 // free after the last stage, so the next row's copy overlaps the output pass.
 constexpr int kPairThreads = 512;
+constexpr int kPairThreadsComposite = 256;
 
 size_t row_pair_smem_bytes(int M) { return sizeof(float2) * (2 * (size_t)(M + 2) + (size_t)(M / 2 + 2)) + 16; }
 
@@ -658,11 +742,59 @@ __device__ __forceinline__ float2 rtw_half(const float2 *TWH, float2 c1, int k) 
     return (k & 1) ? cmul(w, c1) : w;
 }
 
+// v[r] *= w1^r, r = 1 .. R - 1 (the Stockham input twiddles of one butterfly)
+template <int R>
+__device__ __forceinline__ void apply_twiddles(float2 (&v)[R], float2 w1) {
+    constexpr int C = inner_factor<R>();
+    if constexpr (C > 1) {
+        // composite radix: w^(r1 + C r2) = w^r1 (w^C)^r2, two short power chains
+        float2 pw[C];
+        pw[1] = w1;
+#pragma unroll
+        for (int c = 2; c < C; ++c) pw[c] = cmul(pw[c - 1], w1);
+        const float2 WC = cmul(pw[C - 1], w1);
+#pragma unroll
+        for (int c = 1; c < C; ++c) v[c] = cmul(v[c], pw[c]);
+        float2 Q = WC;
+#pragma unroll
+        for (int r2 = 1; r2 < R / C; ++r2) {
+            v[C * r2] = cmul(v[C * r2], Q);
+#pragma unroll
+            for (int c = 1; c < C; ++c) v[c + C * r2] = cmul(v[c + C * r2], cmul(pw[c], Q));
+            if (r2 + 1 < R / C) Q = cmul(Q, WC);
+        }
+    } else {
+        float2 w = w1;
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+            v[r] = cmul(v[r], w);
+            if (r + 1 < R) w = cmul(w, w1);
+        }
+    }
+}
+
+// Butterfly j of a Stockham stage (radix R after stages of product NS): loads its R inputs
+// in[j + r M/R], applies the twiddles and the size-R DFT, leaving the outputs in v (output r
+// belongs at (j - j mod NS) R + j mod NS + r NS).
+template <int R, int NS, int M, bool INV>
+__device__ __forceinline__ void butterfly(const float2 *__restrict__ in, const float2 *__restrict__ TWH, int j,
+                                          float2 (&v)[R]) {
+    constexpr int NB = M / R;
+    constexpr int STRIDE = M / (NS * R);
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = in[j + r * NB];
+    if constexpr (NS > 1) {
+        float2 w1 = tw_half<M>(TWH, (j % NS) * STRIDE);
+        if (INV) w1.y = -w1.y;
+        apply_twiddles<R>(v, w1);
+    }
+    Dft<R, INV>::run(v);
+}
+
 template <int R, int NS, int M, int T, bool INV>
 __device__ __forceinline__ void stage_pair(const float2 *__restrict__ in, float2 *__restrict__ out,
                                            const float2 *__restrict__ TWH) {
     constexpr int NB = M / R;
-    constexpr int STRIDE = M / (NS * R);
     constexpr int ITER = (NB + T - 1) / T;
 #pragma unroll
     for (int it = 0; it < ITER; ++it) {
@@ -670,19 +802,7 @@ __device__ __forceinline__ void stage_pair(const float2 *__restrict__ in, float2
         if (ITER * T == NB || j < NB) {
             const int k = j % NS;
             float2 v[R];
-#pragma unroll
-            for (int r = 0; r < R; ++r) v[r] = in[j + r * NB];
-            if (NS > 1) {
-                float2 w1 = tw_half<M>(TWH, k * STRIDE);
-                if (INV) w1.y = -w1.y;
-                float2 w = w1;
-#pragma unroll
-                for (int r = 1; r < R; ++r) {
-                    v[r] = cmul(v[r], w);
-                    if (r + 1 < R) w = cmul(w, w1);
-                }
-            }
-            Dft<R, INV>::run(v);
+            butterfly<R, NS, M, INV>(in, TWH, j, v);
             const int base = (j - k) * R + k;
 #pragma unroll
             for (int r = 0; r < R; ++r) out[base + r * NS] = v[r];
@@ -717,8 +837,8 @@ __device__ __forceinline__ void release_to_copy() {
     __syncthreads();
 }
 
-template <int... Rs>
-__global__ void __launch_bounds__(kPairThreads, 2)
+template <int T, int... Rs>
+__global__ void __launch_bounds__(T, 2)
 k_row_r2c_pair(FFTPlan p, const float *__restrict__ in, int n_rows, int n_cols, float2 *__restrict__ spec,
                int32_t *status) {
     constexpr int M = (Rs * ...);
@@ -740,10 +860,10 @@ k_row_r2c_pair(FFTPlan p, const float *__restrict__ in, int n_rows, int n_cols, 
     }
     uint32_t parity = 0;
     for (; row < n_rows; row += gridDim.x) {
-        for (int k = half + threadIdx.x; k < M; k += kPairThreads) A[k] = make_float2(0.f, 0.f);   // zero pad
+        for (int k = half + threadIdx.x; k < M; k += T) A[k] = make_float2(0.f, 0.f);   // zero pad
         if (!row_tma_wait(bar, parity, status)) return;
         parity ^= 1u;
-        const float2 *Z = FftPair<M, kPairThreads, false, 1, Rs...>::run(A, A, B, TWH);
+        const float2 *Z = FftPair<M, T, false, 1, Rs...>::run(A, A, B, TWH);
         const int next = row + gridDim.x;
         if constexpr (kOdd) {
             release_to_copy();
@@ -753,7 +873,7 @@ k_row_r2c_pair(FFTPlan p, const float *__restrict__ in, int n_rows, int n_cols, 
             }
         }
         float2 *out = spec + (size_t)row * p.Fs;
-        for (int k = threadIdx.x; k < p.Fu; k += kPairThreads) {
+        for (int k = threadIdx.x; k < p.Fu; k += T) {
             float2 X = make_float2(0.f, 0.f);
             if (k <= M) {
                 const float2 a = Z[k == M ? 0 : k];
@@ -776,8 +896,8 @@ k_row_r2c_pair(FFTPlan p, const float *__restrict__ in, int n_rows, int n_cols, 
     }
 }
 
-template <int... Rs>
-__global__ void __launch_bounds__(kPairThreads, 2)
+template <int T, int... Rs>
+__global__ void __launch_bounds__(T, 2)
 k_row_c2r_pair(FFTPlan p, const float2 *__restrict__ spec, int n_rows, float *__restrict__ out, int n_cols,
                int32_t *status) {
     constexpr int M = (Rs * ...);
@@ -805,7 +925,7 @@ k_row_c2r_pair(FFTPlan p, const float2 *__restrict__ spec, int n_rows, float *__
         // Z[k] = E + i O, E = (X[k] + conj X[M-k]) / 2, O = exp(2 pi i k / P)(X[k] - conj X[M-k]) / 2,
         // in place: one thread forms Z[k] and Z[M-k] from X[k] and X[M-k]; exp(-i pi (M-k) / M)
         // = -conj exp(-i pi k / M)
-        for (int k = threadIdx.x; 2 * k <= M; k += kPairThreads) {
+        for (int k = threadIdx.x; 2 * k <= M; k += T) {
             const int k2 = M - k;
             const float2 xk = k < Fu ? A[k] : zero;
             const float2 xm = k2 < Fu ? A[k2] : zero;
@@ -824,7 +944,7 @@ k_row_c2r_pair(FFTPlan p, const float2 *__restrict__ spec, int n_rows, float *__
             }
         }
         __syncthreads();
-        const float2 *z = FftPair<M, kPairThreads, true, 1, Rs...>::run(A, A, B, TWH);
+        const float2 *z = FftPair<M, T, true, 1, Rs...>::run(A, A, B, TWH);
         const int next = row + gridDim.x;
         if constexpr (kOdd) {
             release_to_copy();
@@ -834,7 +954,7 @@ k_row_c2r_pair(FFTPlan p, const float2 *__restrict__ spec, int n_rows, float *__
             }
         }
         float *dst = out + (size_t)row * n_cols;
-        for (int n2 = threadIdx.x; 2 * n2 < n_cols; n2 += kPairThreads) reinterpret_cast<float2 *>(dst)[n2] = z[n2];
+        for (int n2 = threadIdx.x; 2 * n2 < n_cols; n2 += T) reinterpret_cast<float2 *>(dst)[n2] = z[n2];
         if constexpr (kOdd) {
             __syncthreads();
         } else {
@@ -1103,11 +1223,10 @@ size_t device_smem_per_sm() {
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
-// Row-transform schedule: 0 = register-staged small CTAs (compiled lengths), 1 = persistent
-// bulk-copy CTAs, one per SM, 2 = persistent paired CTAs, two per SM (compiled lengths; else
-// 1).  Chosen by set_row_schedule (wct_sim_create's schedule_id).
-int g_row_schedule = 2;
-int row_kernel_choice() { return g_row_schedule; }
+// Row-transform schedule (FFTPlan::row_schedule): 0 = register-staged small CTAs (compiled
+// lengths), 1 = persistent bulk-copy CTAs, one per SM, 2 = persistent paired CTAs, two per SM
+// (compiled lengths; else 1), 3 = 2 with composite radices where compiled.
+int row_kernel_choice(const FFTPlan &p) { return p.row_schedule; }
 
 // The persistent bulk-copy kernels need 16-byte aligned rows (n_cols % 4 == 0, dense rows)
 // and their five row-sized buffers in one CTA's shared memory.
@@ -1181,9 +1300,14 @@ bool launch_row_rs(const FFTPlan &p, Launch &&launch, cudaError_t &err) {
     return false;
 }
 
-// Paired kernels for the compiled lengths (4900, 3125, 625); false if none applies.
+// Paired kernels for the compiled lengths (4900, 3125, 625); false if none applies.  With
+// `composite`, M = 4900 runs three Stockham passes of radices 25, 28, 7 and M = 3125 three of
+// 5, 25, 25 (composite butterflies, 256 threads of up to 128 registers) instead of five passes
+// of 7, 4, 5, 5, 7 or 5, 5, 5, 5, 5 (512 threads): 40 % fewer shared-memory wavefronts under
+// the bank model of the plan's stage ordering (at 3456 x 9600: forward 72 -> 68 us, inverse
+// 83 -> 78 us; the rest is copy latency and barriers, not shared-memory bandwidth).
 template <bool R2C, class Launch>
-bool launch_row_pair(const FFTPlan &p, Launch &&launch, cudaError_t &err) {
+bool launch_row_pair(const FFTPlan &p, bool composite, Launch &&launch, cudaError_t &err) {
     auto is = [&](std::initializer_list<int> rs) {
         if ((int)rs.size() != p.n_stages) return false;
         int k = 0;
@@ -1193,22 +1317,27 @@ bool launch_row_pair(const FFTPlan &p, Launch &&launch, cudaError_t &err) {
     };
     const size_t smem = row_pair_smem_bytes(p.M);
     if (2 * smem + 2048 > (size_t)device_smem_per_sm() || smem > (size_t)device_smem_optin()) return false;
-    auto go = [&](auto kern) {
+    auto go = [&](auto kern, int threads) {
         err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err == cudaSuccess) {
-            launch(kern, smem);
+            launch(kern, smem, threads);
             err = cudaGetLastError();
         }
         return true;
     };
+    constexpr int T = kPairThreads, TC = kPairThreadsComposite;
     if constexpr (R2C) {
-        if (is({7, 4, 5, 5, 7})) return go(k_row_r2c_pair<7, 4, 5, 5, 7>);
-        if (is({5, 5, 5, 5, 5})) return go(k_row_r2c_pair<5, 5, 5, 5, 5>);
-        if (is({5, 5, 5, 5})) return go(k_row_r2c_pair<5, 5, 5, 5>);
+        if (composite && is({7, 4, 5, 5, 7})) return go(k_row_r2c_pair<TC, 25, 28, 7>, TC);
+        if (composite && is({5, 5, 5, 5, 5})) return go(k_row_r2c_pair<TC, 5, 25, 25>, TC);
+        if (is({7, 4, 5, 5, 7})) return go(k_row_r2c_pair<T, 7, 4, 5, 5, 7>, T);
+        if (is({5, 5, 5, 5, 5})) return go(k_row_r2c_pair<T, 5, 5, 5, 5, 5>, T);
+        if (is({5, 5, 5, 5})) return go(k_row_r2c_pair<T, 5, 5, 5, 5>, T);
     } else {
-        if (is({7, 4, 5, 5, 7})) return go(k_row_c2r_pair<7, 4, 5, 5, 7>);
-        if (is({5, 5, 5, 5, 5})) return go(k_row_c2r_pair<5, 5, 5, 5, 5>);
-        if (is({5, 5, 5, 5})) return go(k_row_c2r_pair<5, 5, 5, 5>);
+        if (composite && is({7, 4, 5, 5, 7})) return go(k_row_c2r_pair<TC, 25, 28, 7>, TC);
+        if (composite && is({5, 5, 5, 5, 5})) return go(k_row_c2r_pair<TC, 5, 25, 25>, TC);
+        if (is({7, 4, 5, 5, 7})) return go(k_row_c2r_pair<T, 7, 4, 5, 5, 7>, T);
+        if (is({5, 5, 5, 5, 5})) return go(k_row_c2r_pair<T, 5, 5, 5, 5, 5>, T);
+        if (is({5, 5, 5, 5})) return go(k_row_c2r_pair<T, 5, 5, 5, 5>, T);
     }
     return false;
 }
@@ -1218,18 +1347,18 @@ bool launch_row_pair(const FFTPlan &p, Launch &&launch, cudaError_t &err) {
 cudaError_t launch_row_r2c(const FFTPlan &p, const float *in, int64_t in_stride, int n_in_cols, int n_rows,
                            float2 *spec, cudaStream_t s, int32_t *status) {
     if (n_rows <= 0) return cudaSuccess;
-    if (row_kernel_choice() == 0 && (n_in_cols % 4 == 0) && in_stride == n_in_cols && aligned16(in) && aligned16(spec)) {
+    if (row_kernel_choice(p) == 0 && (n_in_cols % 4 == 0) && in_stride == n_in_cols && aligned16(in) && aligned16(spec)) {
         cudaError_t err = cudaSuccess;
         if (launch_row_rs<true>(p, [&](auto kern, size_t smem) {
                 kern<<<n_rows, kRsThreads, smem, s>>>(p, in, n_in_cols, spec);
             }, err))
             return err;
     }
-    if (row_kernel_choice() == 2 && use_row_tma(p, in_stride, n_in_cols, in) && aligned16(spec) && 2 * p.M >= n_in_cols) {
+    if (row_kernel_choice(p) >= 2 && use_row_tma(p, in_stride, n_in_cols, in) && aligned16(spec) && 2 * p.M >= n_in_cols) {
         cudaError_t err = cudaSuccess;
         const int grid = std::min(n_rows, 2 * device_sms());
-        if (launch_row_pair<true>(p, [&](auto kern, size_t smem) {
-                kern<<<grid, kPairThreads, smem, s>>>(p, in, n_rows, n_in_cols, spec, status);
+        if (launch_row_pair<true>(p, row_kernel_choice(p) == 3, [&](auto kern, size_t smem, int threads) {
+                kern<<<grid, threads, smem, s>>>(p, in, n_rows, n_in_cols, spec, status);
             }, err))
             return err;
     }
@@ -1251,7 +1380,7 @@ cudaError_t launch_row_r2c(const FFTPlan &p, const float *in, int64_t in_stride,
 cudaError_t launch_row_c2r(const FFTPlan &p, const float2 *spec, int n_rows, float *out, int64_t out_stride,
                            int n_out_cols, cudaStream_t s, int32_t *status) {
     if (n_rows <= 0) return cudaSuccess;
-    if (row_kernel_choice() == 0 && (n_out_cols % 4 == 0) && out_stride == n_out_cols && aligned16(out) &&
+    if (row_kernel_choice(p) == 0 && (n_out_cols % 4 == 0) && out_stride == n_out_cols && aligned16(out) &&
         aligned16(spec)) {
         cudaError_t err = cudaSuccess;
         if (launch_row_rs<false>(p, [&](auto kern, size_t smem) {
@@ -1259,12 +1388,12 @@ cudaError_t launch_row_c2r(const FFTPlan &p, const float2 *spec, int n_rows, flo
             }, err))
             return err;
     }
-    if (row_kernel_choice() == 2 && use_row_tma(p, out_stride, n_out_cols, out) && aligned16(spec) &&
+    if (row_kernel_choice(p) >= 2 && use_row_tma(p, out_stride, n_out_cols, out) && aligned16(spec) &&
         2 * p.M >= n_out_cols) {
         cudaError_t err = cudaSuccess;
         const int grid = std::min(n_rows, 2 * device_sms());
-        if (launch_row_pair<false>(p, [&](auto kern, size_t smem) {
-                kern<<<grid, kPairThreads, smem, s>>>(p, spec, n_rows, out, n_out_cols, status);
+        if (launch_row_pair<false>(p, row_kernel_choice(p) == 3, [&](auto kern, size_t smem, int threads) {
+                kern<<<grid, threads, smem, s>>>(p, spec, n_rows, out, n_out_cols, status);
             }, err))
             return err;
     }
@@ -1335,8 +1464,6 @@ cudaError_t launch_wire_stage(const FFTPlan &p, const float2 *spec, const float2
     }
     return e;
 }
-
-void set_row_schedule(int schedule) { g_row_schedule = schedule; }
 
 cudaError_t launch_make_twiddles(const FFTPlan &p, cudaStream_t s) {
     k_make_twiddles<<<(p.M + 256) / 256, 256, 0, s>>>(p.tw, p.rtw, p.M);

@@ -824,17 +824,15 @@ constexpr int kTileW = 32, kTileT = 256;
 int tile_wires() { return kTileW; }
 int tile_ticks() { return kTileT; }
 
-// Raster schedule: 0 = warp-level chunks (default), 1 = CTA-level chunks.
-int g_raster_schedule = 0;
-void set_raster_schedule(int schedule) { g_raster_schedule = schedule; }
-
-int64_t raster_chunk_count(int64_t n) {
-    return g_raster_schedule == 1 ? (n + kChunk - 1) / kChunk : (n + kWarpDepos - 1) / kWarpDepos;
+// Raster schedule (PlaneParams::raster_schedule): 0 = warp-level chunks (default), 1 = CTA-level
+// chunks.
+int64_t raster_chunk_count(int64_t n, int schedule) {
+    return schedule == 1 ? (n + kChunk - 1) / kChunk : (n + kWarpDepos - 1) / kWarpDepos;
 }
 
 cudaError_t launch_raster_batch(const BatchTable &tab, int64_t total_chunks, int32_t *status, cudaStream_t s) {
     if (total_chunks <= 0) return cudaSuccess;
-    if (g_raster_schedule != 1) {
+    if (tab.plane[0].raster_schedule != 1) {
         const int64_t blocks = (total_chunks + kWarpsPerCta - 1) / kWarpsPerCta;
         k_raster_batch_warps<<<(unsigned)blocks, kWarpsPerCta * 32, 0, s>>>(tab, status);
         return cudaGetLastError();
@@ -849,7 +847,7 @@ cudaError_t launch_raster_batch(const BatchTable &tab, int64_t total_chunks, int
 cudaError_t launch_raster_chunks(const wct_depos_t &d, const PlaneParams &pp, uint32_t event_lo, float *grid,
                                  int32_t *status, cudaStream_t s, uint32_t *flags) {
     if (d.n <= 0) return cudaSuccess;
-    if (g_raster_schedule != 1) {
+    if (pp.raster_schedule != 1) {
         const int64_t chunks = (d.n + kWarpDepos - 1) / kWarpDepos;
         const int64_t blocks = (chunks + kWarpsPerCta - 1) / kWarpsPerCta;
         k_raster_warps<<<(unsigned)blocks, kWarpsPerCta * 32, 0, s>>>(d.t0_us, d.x_mm, d.y_mm, d.z_mm, d.q_e, d.n, pp,

@@ -39,6 +39,7 @@ struct PlaneParams {
     uint32_t key0, key1;
     uint32_t rk[20];                                     // Philox round keys of (key0, key1)
     int32_t tile_w, tile_t, n_tiles_w, n_tiles_t;
+    int32_t raster_schedule;                             // 0 warp-level chunks, 1 CTA-level chunks
 };
 
 // Device status word codes (same values as wct_status_t).
@@ -57,6 +58,8 @@ struct FFTPlan {
                           // response spectrum's support; bins above it are treated as zero
     float2 *tw;           // device: exp(-2 pi i k / M), k < M
     float2 *rtw;          // device: exp(-2 pi i k / P), k <= M
+    int32_t row_schedule; // row kernels: 0 register-staged, 1 one persistent CTA per SM,
+                          // 2 two paired CTAs per SM, 3 paired with composite radices
 };
 
 // One (event, plane) pair of a batched rasterize + scatter launch.
@@ -142,8 +145,7 @@ __device__ __forceinline__ void clear_listed_tiles(const ClearJob &job, unsigned
         if (tid == 0) flags[t] = 0u;
     }
 }
-int64_t raster_chunk_count(int64_t n);
-void set_raster_schedule(int schedule);   // 0 warp-level chunks, 1 CTA-level chunks
+int64_t raster_chunk_count(int64_t n, int schedule);
 cudaError_t launch_rasterize_patches(int64_t n, const DepoDesc *desc, const int64_t *offsets, const PlaneParams &pp,
                                      uint32_t event_lo, float *patches, int64_t *patch_desc, cudaStream_t s,
                                      int64_t slot = 0);
@@ -190,7 +192,6 @@ cudaError_t launch_row_c2r(const FFTPlan &p, const float2 *spec, int n_rows, flo
 cudaError_t launch_scale_spectrum(float2 *spec, int64_t n, float scale, cudaStream_t s);
 cudaError_t launch_make_twiddles(const FFTPlan &p, cudaStream_t s);
 cudaError_t launch_wait_selftest(long long limit, int32_t *status, cudaStream_t s);
-void set_row_schedule(int schedule);   // 0 register-staged row kernels, 1 persistent bulk-copy kernels
 cudaError_t launch_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, int64_t n, uint32_t *out, cudaStream_t s);
 
 }  // namespace wct

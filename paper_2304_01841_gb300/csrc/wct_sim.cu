@@ -180,6 +180,8 @@ int response_support_last(const wct_response_t &r, int P, int F, double thr) {
 }
 
 constexpr int kNumRadices = 6;
+// Row-transform schedule of a handle created with schedule_id -1 (FFTPlan::row_schedule)
+constexpr int kDefaultRowSchedule = 3;
 
 // Shared-memory wavefronts of one Stockham stage (radix R after stages of product NS) for a
 // length-M transform: each warp handles 32 consecutive butterflies j, reads its R inputs
@@ -287,6 +289,7 @@ bool plan_fft(int n_ticks, int kt, FFTPlan &p) {
     p.F = (int32_t)(M + 1);
     p.Fs = (int32_t)((M + 2) & ~1LL);
     p.Fu = p.Fs;
+    p.row_schedule = kDefaultRowSchedule;
     // radix multiset: largest radices first (fewest stages); their order is chosen below
     int64_t r = M;
     const int rads[kNumRadices] = {8, 7, 5, 4, 3, 2};
@@ -592,12 +595,14 @@ wct_status_t wct_sim_create(const wct_plane_t *planes, int n_planes, const wct_r
         s->opts.schedule_id = -1;
         s->opts.deterministic = 0;
     }
-    // schedule_id: -1 default; otherwise bits 0 and 2 = row transforms (0 register-staged,
-    // 1 persistent bulk-copy, 4 persistent paired), bit 1 = rasterize (0 warp-level chunks,
-    // 1 CTA-level chunks)
+    // schedule_id: -1 default; otherwise bits 0, 2 and 3 = row transforms (0 register-staged,
+    // 1 persistent bulk-copy, 4 persistent paired, 8 paired with composite radices), bit 1 =
+    // rasterize (0 warp-level chunks, 1 CTA-level chunks).  Kept per handle, in its plans.
+    int row_schedule = kDefaultRowSchedule, raster_schedule = 0;
     if (s->opts.schedule_id >= 0) {
-        set_row_schedule((s->opts.schedule_id & 4) ? 2 : (s->opts.schedule_id & 1));
-        set_raster_schedule((s->opts.schedule_id >> 1) & 1);
+        const int id = s->opts.schedule_id;
+        row_schedule = (id & 8) ? 3 : (id & 4) ? 2 : (id & 1);
+        raster_schedule = (id >> 1) & 1;
     }
     wct_status_t st = WCT_OK;
     size_t spec_elems = 0;
@@ -636,6 +641,7 @@ wct_status_t wct_sim_create(const wct_plane_t *planes, int n_planes, const wct_r
         pp.n_ticks = g.n_ticks;
         pp.plane_index = p;
         pp.fluctuate = df.fluctuate ? 1 : 0;
+        pp.raster_schedule = raster_schedule;
         pp.key0 = (uint32_t)(df.seed & 0xFFFFFFFFu);
         pp.key1 = (uint32_t)(df.seed >> 32);
         for (int r = 0; r < 10; ++r) {   // round r uses key + r * (0x9E3779B9, 0xBB67AE85), mod 2^32
@@ -656,6 +662,7 @@ wct_status_t wct_sim_create(const wct_plane_t *planes, int n_planes, const wct_r
             st = fail(s, WCT_EINVAL, "no FFT plan for this tick count (too long)");
             break;
         }
+        ps.fft.row_schedule = row_schedule;
         st = upload_twiddles(s, ps.fft);
     }
     if (st == WCT_OK) st = dev_alloc(s, (void **)&s->tile_count, sizeof(int32_t) * (max_tiles + 1));
@@ -958,7 +965,7 @@ wct_status_t enqueue_batch(wct_sim *s, const wct_depos_t *events, int n_events, 
             b.chunk_begin = chunks;
             b.event_lo = (uint32_t)d.event_id;
             b.plane = p;
-            chunks += raster_chunk_count(d.n);
+            chunks += raster_chunk_count(d.n, tab.plane[0].raster_schedule);
         }
         if (chunks > 0) {
             err = launch_raster_batch(tab, chunks, s->status, rs);
@@ -1186,6 +1193,7 @@ wct_status_t wct_sim_set_impact_responses(wct_sim_t *s, int plane, const wct_res
     if (!plan_fft(ps.g.n_ticks, kt, full)) return fail(s, WCT_EINVAL, "no FFT plan for this tick count (too long)");
     full.tw = ps.fft.tw;                               // same transform length as the plane's
     full.rtw = ps.fft.rtw;
+    full.row_schedule = ps.fft.row_schedule;
     if (full.M != ps.fft.M) return fail(s, WCT_EINVAL, "impact responses need the plane's transform length");
     // spectra of every phase, the common support, then one packed buffer
     const int KW = WCT_MAX_RESPONSE_WIRES;

