@@ -356,6 +356,47 @@ wct_status_t wct_philox4x32_10(const uint32_t *ctr, uint64_t seed, int64_t n, ui
 wct_status_t wct_convolve_static(const float *grid, int32_t n_wires, int32_t n_ticks, const float *response,
                                  int32_t n_wires_resp, int32_t n_ticks_resp, float *waveform, void *stream);
 
+/*
+ * A field response (input of the detector response of §2 step 3, which the paper takes as
+ * given): the current induced on ONE wire by a unit charge drifting along each of n_paths
+ * paths, the paths at charge positions path_pos_mm[j] across the pitch direction relative to
+ * that wire's centre (strictly increasing), every path sampled n_samples times at period_us
+ * from one common time origin: current[j][s], in unit charges per microsecond.  This is the
+ * form a field calculation produces (currents on a fine time grid for drift paths at
+ * sub-pitch spacing).  If every position is >= 0 the field is taken as mirror-symmetric,
+ * I(-x) = I(x).  Between paths the current is interpolated linearly in x; beyond the
+ * outermost path it is zero.  All HOST memory, read only during the call.
+ */
+typedef struct {
+    int32_t n_paths;            /* >= 2 */
+    int32_t n_samples;          /* >= 1 */
+    double period_us;           /* > 0 */
+    const double *path_pos_mm;  /* [n_paths] */
+    const double *current;      /* [n_paths][n_samples] */
+} wct_field_response_t;
+
+/*
+ * The tick-sampled detector response from a field response and an electronics impulse
+ * response electronics[0 .. n_elec) sampled at the same period (e.g. a CR-RC^2 shaper times
+ * its gain):
+ *     R_p[r][tau] = period * sum_s I(y_p - (r - K) pitch, s period) * E[tau m - s],
+ * the field current convolved with the electronics in time and sampled at the tick times
+ * (m = tick_us / period_us must be an integer), for the wire at offset r - K from the wire
+ * the charge is on (K = n_wires_resp / 2, n_wires_resp odd) and the charge at the centre of
+ * impact sub-bin p of its wire, y_p = ((p + 1/2) / n_impact - 1/2) pitch.
+ *   impact_out  HOST float [n_impact][n_wires_resp][n_ticks_resp] or NULL: the per-impact-
+ *               position responses (wct_sim_set_impact_responses, one per phase);
+ *   folded_out  HOST float [n_wires_resp][n_ticks_resp] or NULL: their average over the
+ *               n_impact phases, the response of a charge spread evenly across the pitch
+ *               (wct_sim_create's response for the folded mode).
+ * Host computation in FP64, no device work, no handle.  Returns WCT_OK or WCT_EINVAL (sizes,
+ * positions not strictly increasing, a tick that is not a whole number of periods, a
+ * non-finite value).
+ */
+wct_status_t wct_response_from_field(const wct_field_response_t *field, const double *electronics, int32_t n_elec,
+                                     double pitch_mm, int32_t n_impact, double tick_us, int32_t n_wires_resp,
+                                     int32_t n_ticks_resp, float *impact_out, float *folded_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,6 +23,10 @@ Parity status of each function (what pins it; see tests/test_oracle_*.py):
   impact-resolution    pinned: phase-independent responses reduce to the folded path,
   scatter / convolve   FFT form = literal loops, a single sub-bin charge places its phase's
                        response, the impact grid folds to the wire grid.
+  response from field  (oracle/response.py) pinned: delta electronics returns the sampled
+                       current, exact interpolation of a field linear in x, mirror symmetry,
+                       two-sided = mirrored one-sided, zero beyond the field's reach, an
+                       impulse current places the electronics response, literal loops.
 """
 from __future__ import annotations
 

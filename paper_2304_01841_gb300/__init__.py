@@ -18,7 +18,8 @@ import numpy as np
 from . import _abi
 from ._abi import WctError, load  # noqa: F401
 
-__all__ = ["Simulator", "DeviceDepos", "WctError", "load", "philox4x32_10"]
+__all__ = ["Simulator", "DeviceDepos", "WctError", "load", "philox4x32_10", "FieldResponse", "load_field_response",
+           "response_from_field"]
 
 
 def _torch():
@@ -324,3 +325,75 @@ def patch_slot_bins(plane, diffusion, x_max_mm: float) -> int:
     nt = int(math.floor(2.0 * diffusion.nsigma * s_t)) + 2
     n_p = int(math.floor(2.0 * diffusion.nsigma * s_p)) + 2
     return nt * n_p
+
+
+# --------------------------------------------------------------------------------------------
+# Field-response ingestion
+# --------------------------------------------------------------------------------------------
+
+@dataclass
+class FieldResponse:
+    """Currents induced on one wire by a unit charge drifting along paths across the pitch:
+    path_pos_mm [n_paths] (strictly increasing, relative to the wire centre; all >= 0 means a
+    mirror-symmetric field given on one side), current [n_paths, n_samples] in unit charges
+    per microsecond, sampled every period_us from a common origin."""
+    path_pos_mm: np.ndarray
+    current: np.ndarray
+    period_us: float
+
+
+FIELD_FORMAT = "wct-gb300-field-response/1"
+
+
+def load_field_response(path: str) -> FieldResponse:
+    """Read a field response from a JSON file of the form
+
+        {"format": "wct-gb300-field-response/1", "period_us": 0.1,
+         "paths": [{"pos_mm": 0.0, "current": [...]}, {"pos_mm": 0.3, "current": [...]}, ...]}
+
+    (every path with the same number of samples, positions strictly increasing; currents in
+    unit charges per microsecond)."""
+    import json
+    with open(path) as f:
+        doc = json.load(f)
+    if doc.get("format") != FIELD_FORMAT:
+        raise ValueError(f"{path}: not a {FIELD_FORMAT} file")
+    paths = doc["paths"]
+    pos = np.array([float(q["pos_mm"]) for q in paths], dtype=np.float64)
+    cur = np.array([np.asarray(q["current"], dtype=np.float64) for q in paths])
+    if cur.ndim != 2:
+        raise ValueError(f"{path}: paths have different sample counts")
+    return FieldResponse(pos, cur, float(doc["period_us"]))
+
+
+def save_field_response(path: str, field: FieldResponse) -> None:
+    """Write `field` in the JSON form load_field_response reads."""
+    import json
+    doc = {"format": FIELD_FORMAT, "period_us": float(field.period_us),
+           "paths": [{"pos_mm": float(p), "current": [float(v) for v in c]}
+                     for p, c in zip(field.path_pos_mm, field.current)]}
+    with open(path, "w") as f:
+        json.dump(doc, f)
+
+
+def response_from_field(field: FieldResponse, electronics, pitch_mm: float, n_impact: int, tick_us: float,
+                        n_wires_resp: int = 21, n_ticks_resp: int = 200):
+    """wct_response_from_field: (per-impact-position responses float32 [n_impact, n_wires_resp,
+    n_ticks_resp], their average over the phases float32 [n_wires_resp, n_ticks_resp]) from a
+    field response and an electronics impulse response sampled at the field's period.  The
+    first feeds Simulator.set_impact_responses, the second Simulator's create-time response."""
+    pos = np.ascontiguousarray(field.path_pos_mm, dtype=np.float64)
+    cur = np.ascontiguousarray(field.current, dtype=np.float64)
+    el = np.ascontiguousarray(electronics, dtype=np.float64).ravel()
+    if cur.ndim != 2 or cur.shape[0] != pos.shape[0]:
+        raise ValueError("current must be [n_paths, n_samples] with one row per position")
+    imp = np.empty((n_impact, n_wires_resp, n_ticks_resp), dtype=np.float32)
+    fold = np.empty((n_wires_resp, n_ticks_resp), dtype=np.float32)
+    fr = _abi.wct_field_response_t(pos.shape[0], cur.shape[1], float(field.period_us), pos.ctypes.data,
+                                   cur.ctypes.data)
+    rc = load().wct_response_from_field(ctypes.byref(fr), el.ctypes.data, el.shape[0], float(pitch_mm),
+                                        int(n_impact), float(tick_us), int(n_wires_resp), int(n_ticks_resp),
+                                        imp.ctypes.data, fold.ctypes.data)
+    if rc != 0:
+        raise WctError(rc, "wct_response_from_field: invalid field, electronics or sizes")
+    return imp, fold

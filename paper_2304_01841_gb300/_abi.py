@@ -51,6 +51,11 @@ class wct_adc_t(ctypes.Structure):
                 ("bits", c_i32), ("add_noise", c_i32)]
 
 
+class wct_field_response_t(ctypes.Structure):
+    _fields_ = [("n_paths", c_i32), ("n_samples", c_i32), ("period_us", c_dbl), ("path_pos_mm", c_vp),
+                ("current", c_vp)]
+
+
 class wct_host_depos_t(ctypes.Structure):
     _fields_ = [("t0_us", c_vp), ("x_mm", c_vp), ("y_mm", c_vp), ("z_mm", c_vp), ("q_e", c_vp),
                 ("n", c_i64), ("event_id", c_u64)]
@@ -85,6 +90,8 @@ EXPORTS = {
     "wct_sim_last_error": ([c_vp], ctypes.c_char_p),
     "wct_philox4x32_10": ([c_vp, c_u64, c_i64, c_vp, c_vp], ctypes.c_int),
     "wct_convolve_static": ([c_vp, c_i32, c_i32, c_vp, c_i32, c_i32, c_vp, c_vp], ctypes.c_int),
+    "wct_response_from_field": ([ctypes.POINTER(wct_field_response_t), c_vp, c_i32, c_dbl, c_i32, c_dbl, c_i32,
+                                 c_i32, c_vp, c_vp], ctypes.c_int),
 }
 
 _lock = threading.Lock()

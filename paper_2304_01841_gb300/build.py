@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libwctsim.so")
-SOURCES = ["wct_sim.cu", "k_depo.cu", "k_raster.cu", "k_fft.cu", "k_adc.cu"]
+SOURCES = ["wct_sim.cu", "k_depo.cu", "k_raster.cu", "k_fft.cu", "k_adc.cu", "wct_response.cu"]
 HEADERS = ["wct_internal.cuh", "wct_device.cuh", "wct_tma.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -171,6 +171,41 @@ def make_response_impact(kind: str = "bipolar", n_impact: int = 10, n_wires: int
     return out.astype(np.float32)
 
 
+def make_field_response(kind: str = "unipolar", pitch_mm: float = 3.0, path_step_mm: float = 0.3,
+                        reach_pitches: float = 10.5, period_us: float = 0.1, duration_us: float = 100.0):
+    """Synthetic field response in the form a field calculation produces: the current induced on
+    one wire by a unit charge drifting along paths at 0, path_step, ..., reach pitches from the
+    wire (one side; the field is mirror-symmetric), sampled every period_us.
+
+    Returns (path_pos_mm [n_paths], current [n_paths, n_samples] in unit charges per us).  At a
+    distance of d pitches the pulse is centred at 20 + 2d us with width 2 + d/4 us and area
+    exp(-d/2): a Gaussian (unipolar, collection) or its time derivative scaled by the width
+    (bipolar, induction), the continuous counterpart of make_response's field part."""
+    pos = np.arange(0.0, reach_pitches * pitch_mm + 1e-9, path_step_mm)
+    t = np.arange(int(round(duration_us / period_us))) * period_us
+    cur = np.zeros((pos.shape[0], t.shape[0]))
+    for j, x in enumerate(pos):
+        d = x / pitch_mm
+        c, b = 20.0 + 2.0 * d, 2.0 + 0.25 * d
+        g = np.exp(-0.5 * ((t - c) / b) ** 2) / (b * math.sqrt(2.0 * math.pi))
+        if kind == "unipolar":
+            f = g
+        elif kind == "bipolar":
+            f = -((t - c) / b) * g
+        else:
+            raise ValueError(kind)
+        cur[j] = f * math.exp(-0.5 * d)
+    return pos, cur
+
+
+def electronics_crrc2(period_us: float = 0.1, shaping_us: float = 1.0, n_samples: int = 200, gain: float = 1.0):
+    """CR-RC^2 shaper impulse response h(t) = (t / ts)^2 exp(-t / ts) sampled every period_us,
+    scaled to unit area (sum h * period = 1) times gain."""
+    s = np.arange(n_samples) * period_us / shaping_us
+    h = s * s * np.exp(-s)
+    return gain * h / (h.sum() * period_us)
+
+
 # --------------------------------------------------------------------------------------------
 # Depo generators
 # --------------------------------------------------------------------------------------------

@@ -38,15 +38,17 @@ def test_struct_layout_matches_header(tmp_path):
     from paper_2304_01841_gb300 import _abi
     c = tmp_path / "layout.c"
     c.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "wct_sim.h"\n'
-                 "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(wct_plane_t),"
+                 "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(wct_plane_t),"
                  " sizeof(wct_response_t), sizeof(wct_diffusion_t), sizeof(wct_opts_t), sizeof(wct_depos_t),"
-                 " offsetof(wct_diffusion_t, seed), offsetof(wct_depos_t, event_id)); return 0;}\n")
+                 " offsetof(wct_diffusion_t, seed), offsetof(wct_depos_t, event_id),"
+                 " sizeof(wct_field_response_t), offsetof(wct_field_response_t, current)); return 0;}\n")
     exe = tmp_path / "layout"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(c)])
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     want = [ctypes.sizeof(_abi.wct_plane_t), ctypes.sizeof(_abi.wct_response_t),
             ctypes.sizeof(_abi.wct_diffusion_t), ctypes.sizeof(_abi.wct_opts_t), ctypes.sizeof(_abi.wct_depos_t),
-            _abi.wct_diffusion_t.seed.offset, _abi.wct_depos_t.event_id.offset]
+            _abi.wct_diffusion_t.seed.offset, _abi.wct_depos_t.event_id.offset,
+            ctypes.sizeof(_abi.wct_field_response_t), _abi.wct_field_response_t.current.offset]
     assert got == want
 
 

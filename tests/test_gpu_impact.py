@@ -103,3 +103,28 @@ def test_impact_responses_are_validated():
         sim.set_impact_responses(0, synth.make_response_impact("bipolar", n_impact=4))     # phases != n_imp
     with pytest.raises(g.WctError):
         sim.convolve_impact(0, torch.zeros((10, 64, 500), device="cuda"))                  # not in impact mode
+
+
+def test_responses_ingested_from_a_field_response():
+    # field response -> tick responses through the C ABI; the folded and the impact modes with
+    # them against the oracle given the same arrays
+    import paper_2304_01841_gb300 as g
+    wl = synth.workload("tiny")
+    pl = wl.planes[0]
+    pos, cur = synth.make_field_response(pl.response_kind, pitch_mm=pl.pitch_mm)
+    e = synth.electronics_crrc2(0.1, 1.0, 200)
+    imp, fold = g.response_from_field(g.FieldResponse(pos, cur, 0.1), e, pl.pitch_mm, pl.n_impact_per_pitch,
+                                      pl.tick_us)
+    d = wl.depos()
+    diff = synth.Diffusion(fluctuate=True, seed=12)
+    sim = make_sim([pl], [fold], diff)
+    folded = to_np(sim.run_event(_dev(d))[0])
+    sim.set_impact_responses(0, imp)
+    resolved = to_np(sim.run_event(_dev(d))[0])
+    sim.sync()
+    _, _, ref_f = oracle.simulate_plane(d, pl, diff, fold)
+    _, _, ref_i = oracle.simulate_plane_impact(d, pl, diff, imp)
+    assert rel_l2(folded, ref_f) <= WAVE_RTOL
+    assert rel_l2(resolved, ref_i) <= WAVE_RTOL
+    # the field varies across the pitch, so resolving the impact position changes the answer
+    assert rel_l2(resolved, folded) > 10 * WAVE_RTOL
