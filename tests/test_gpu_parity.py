@@ -146,6 +146,73 @@ def test_convolve_every_row_schedule(nt):
         assert rel_l2(to_np(out), ref) <= WAVE_RTOL, sched
 
 
+def test_convolve_small_response_and_in_place():
+    pl = synth.Plane(64, 500)
+    resp = np.random.default_rng(3).normal(size=(5, 37)).astype(np.float32)
+    sim = make_sim([pl], [resp], synth.Diffusion())
+    g = np.random.default_rng(4).normal(size=(64, 500)).astype(np.float32)
+    buf = torch.from_numpy(g.copy()).cuda()
+    sim.convolve(0, buf, out=buf)          # in place
+    sim.sync()
+    ref = oracle.convolve_direct(g, resp)
+    assert rel_l2(to_np(buf), ref) <= WAVE_RTOL
+
+
+def test_convolve_delta_response_is_identity():
+    pl = synth.Plane(40, 777)
+    resp = np.zeros((21, 200), np.float32)
+    resp[10, 0] = 1.0
+    sim = make_sim([pl], [resp], synth.Diffusion())
+    g = np.random.default_rng(5).normal(size=(40, 777)).astype(np.float32)
+    out = sim.convolve(0, torch.from_numpy(g).cuda())
+    sim.sync()
+    assert np.abs(to_np(out) - g).max() <= 1e-5 * np.abs(g).max()
+    info = sim.plane_info(0)
+    assert info["spectrum_bins_used"] >= info["spectrum_bins"]      # a delta keeps every bin
+
+
+# ------------------------------------------------------------------------------------------
+def _event_parity(wl, d, check_grid=True):
+    sim = make_sim(wl.planes, wl.responses(), wl.diffusion)
+    dd = _dev(d)
+    wfs = sim.run_event(dd)
+    sim.sync()
+    for p, pl in enumerate(wl.planes):
+        pt, grid, wf = oracle.simulate_plane(d, pl, wl.diffusion, wl.responses()[p], plane_index=p)
+        err = rel_l2(to_np(wfs[p]), wf)
+        assert err <= WAVE_RTOL, (p, err)
+        if check_grid:
+            g = sim.scatter(p, dd)
+            sim.sync()
+            assert max_rel_bin(to_np(g), grid) <= BIN_TOL
+    return sim
+
+
+def test_event_tiny():
+    wl = synth.workload("tiny")
+    _event_parity(wl, wl.depos())
+
+
+def test_event_full_uboone_plane():
+    # the configuration the benchmark times: 3456 x 9600, 100k depos, fluctuation on
+    wl = synth.workload("uboone_plane")
+    _event_parity(wl, wl.depos())
+
+
+def test_event_three_plane_reduced():
+    # all three planes (angles +-60 deg, bipolar / unipolar), 100k depos of the 1M recipe
+    wl = synth.workload("three_plane")
+    _event_parity(wl, wl.depos(n_depos=100_000))
+
+
+def test_event_three_plane_full_waveforms():
+    # the full 1M-depo three-plane event (800k on 200 tracks + 200k isolated), waveforms of
+    # every plane against the oracle
+    wl = synth.workload("three_plane")
+    _event_parity(wl, wl.depos(), check_grid=False)
+
+
+# ------------------------------------------------------------------------------------------
 # Edge cases
 # ------------------------------------------------------------------------------------------
 @pytest.mark.parametrize("schedule", [-1, 6, 8])
