@@ -462,3 +462,29 @@ def test_lifetime_attenuation_matches_oracle(fluct):
     sim.sync()
     _, _, wf0 = oracle.simulate_plane(d, wl.planes[0], diff, wl.responses()[0], plane_index=0)
     assert rel_l2(to_np(back[0]), wf0) <= WAVE_RTOL
+
+
+def test_full_size_batch_as_benchmarked():
+    # the benchmark's launch: one run_batch of 16 uboone_plane events (3456 x 9600, 100k depos
+    # each, distinct seeds and event ids), called twice so the second call replays the recorded
+    # graph; the first and last events against the oracle, every event against its run_event
+    import bench
+    wl = synth.workload("uboone_plane")
+    pl = wl.planes[0]
+    hosts = [wl.depos(seed=s, event_id=e) for s, e in bench.shard_plan(0, 1, 16, wl.seed)]
+    dev = [_dev(h) for h in hosts]
+    sim = make_sim(wl.planes, wl.responses(), wl.diffusion)
+    outs = [[torch.empty((pl.n_wires, pl.n_ticks), dtype=torch.float32, device="cuda")] for _ in hosts]
+    sim.run_batch(dev, outs)
+    for o in outs:
+        o[0].fill_(float("nan"))
+    sim.run_batch(dev, outs)
+    sim.sync()
+    for e in (0, len(hosts) - 1):
+        _, _, ref = oracle.simulate_plane(hosts[e], pl, wl.diffusion, wl.responses()[0])
+        assert rel_l2(to_np(outs[e][0]), ref) <= WAVE_RTOL, e
+    for e, d in enumerate(dev):
+        single = sim.run_event(d)[0]
+        sim.sync()
+        scale = float(single.abs().max())
+        assert float((outs[e][0] - single).abs().max()) <= 1e-5 * scale, e
