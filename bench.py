@@ -337,6 +337,39 @@ def measure_impact(n_events=4, reps=2):
                           "inverse_transform": round(stages["row_c2r"], 1)}}
 
 
+def measure_deterministic(n_events=16, reps=5):
+    """Cost of the deterministic mode (fixed-point integer accumulation, bitwise reproducible):
+    one run_batch of n_events uboone_plane events on a deterministic handle against the default
+    handle, CUDA events around reps batches each (graph replay after the first call)."""
+    import torch
+    import paper_2304_01841_gb300 as pkg
+    import synth
+    wl = synth.workload(WORKLOAD)
+    pl = wl.planes[0]
+    evs = [pkg.DeviceDepos.from_host(wl.depos(seed=wl.seed + 200 + e, event_id=700 + e)) for e in range(n_events)]
+    outs = [[torch.empty((pl.n_wires, pl.n_ticks), dtype=torch.float32, device="cuda")] for _ in evs]
+    st = torch.cuda.current_stream()
+    res = {}
+    for det in (False, True):
+        sim = pkg.Simulator(wl.planes, wl.responses(), wl.diffusion, deterministic=det)
+        for _ in range(3):
+            sim.run_batch(evs, outs)
+        sim.sync()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for _ in range(reps):
+            sim.run_batch(evs, outs)
+        b.record(st)
+        torch.cuda.synchronize()
+        sim.sync()
+        res[det] = a.elapsed_time(b) / 1000.0 / (reps * n_events)
+        sim.close()
+    n = evs[0].n
+    return {"workload": f"{WORKLOAD}, {n_events}-event run_batch", "events_per_s": 1.0 / res[True],
+            "depos_per_s": n / res[True], "default_events_per_s": 1.0 / res[False],
+            "slowdown": res[True] / res[False]}
+
+
 def measure_scan_free(reps=5):
     """Unfused rasterize on the uboone_plane event: the prefix-sum version (size query, host
     synchronisation, packed patches) against the scan-free one (a fixed slot per depo sized for
@@ -643,6 +676,7 @@ def main():
         extras["batch"] = measure_batch()
         extras["serving"] = measure_serving()
         extras["impact_mode"] = measure_impact()
+        extras["deterministic"] = measure_deterministic()
         extras["scan_free_rasterize"] = measure_scan_free()
         extras["digitize"] = measure_digitize()
 

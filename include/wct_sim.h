@@ -105,7 +105,15 @@ typedef struct {
  * (paired row transforms with composite radices, warp-level rasterizer).  Otherwise a bit set:
  * row transforms 0 register-staged, 1 one persistent CTA per SM, 4 two paired CTAs per SM,
  * 8 paired with composite radices; +2 selects the CTA-level rasterizer.
- * deterministic: reserved (0).
+ * deterministic: 0 = the scatter-add sums in float32 with atomics, so the last bits of a grid
+ * bin can depend on the order in which contributions land (warp scheduling); 1 = bitwise
+ * reproducible: every contribution is rounded to fixed point (2^-20 electrons) and summed as a
+ * 64-bit integer, which is order independent, then converted once to float32 (the sum is exact
+ * to 2^-21 electrons per contribution, finer than float32 at any bin above 8 electrons).  The
+ * waveforms are then identical run to run, alone or in a batch, and for any order of the depos
+ * when fluctuation is off (the fluctuation is keyed by depo index).  Costs 8 bytes of device
+ * memory per grid bin per grid set (twice the float grids; the impact mode's phase grids
+ * likewise) and a conversion pass over the touched tiles; forces the warp-level rasterizer.
  */
 typedef struct {
     size_t hbm_budget_bytes;

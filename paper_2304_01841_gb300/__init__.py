@@ -69,7 +69,7 @@ class Simulator:
     """Owns one wct_sim handle (planes, responses, diffusion) on the current CUDA device."""
 
     def __init__(self, planes: Sequence, responses: Sequence[np.ndarray], diffusion,
-                 hbm_budget_bytes: int = 0, schedule_id: int = -1):
+                 hbm_budget_bytes: int = 0, schedule_id: int = -1, deterministic: bool = False):
         self._lib = load()
         self.planes = list(planes)
         n = len(self.planes)
@@ -83,7 +83,7 @@ class Simulator:
             R[i] = _abi.wct_response_t(r.shape[0], r.shape[1], r.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
         D = _abi.wct_diffusion_t(diffusion.DL_cm2_s, diffusion.DT_cm2_s, diffusion.v_drift_mm_us, diffusion.nsigma,
                                  int(bool(diffusion.fluctuate)), int(diffusion.seed) & 0xFFFFFFFFFFFFFFFF)
-        O = _abi.wct_opts_t(int(hbm_budget_bytes), int(schedule_id), 0)
+        O = _abi.wct_opts_t(int(hbm_budget_bytes), int(schedule_id), int(bool(deterministic)))
         h = ctypes.c_void_p()
         rc = self._lib.wct_sim_create(P, n, R, ctypes.byref(D), ctypes.byref(O), ctypes.byref(h))
         if rc != 0:

@@ -22,6 +22,25 @@ namespace wct {
 
 namespace {
 
+// Accumulation into a grid or a shared-memory box.  Deterministic mode (wct_opts_t::
+// deterministic): each contribution is rounded to fixed point (kFixScale units per electron)
+// and summed as a 64-bit integer; integer addition is associative, so the sums do not depend
+// on the order in which the atomics land (warp scheduling, batching, depo order).
+template <bool DET>
+struct Acc;
+template <>
+struct Acc<false> {
+    using T = float;
+    __device__ __forceinline__ static void add(float *p, float v) { atomicAdd(p, v); }
+};
+template <>
+struct Acc<true> {
+    using T = unsigned long long;
+    __device__ __forceinline__ static void add(unsigned long long *p, float v) {
+        atomicAdd(p, (unsigned long long)__float2ll_rn(v * kFixScale));   // two's complement sum
+    }
+};
+
 constexpr int kTileWarps = 8;
 constexpr int kWT = WCT_MAX_WINDOW_TICKS + 1;                 // per-warp time weights (+1 edge)
 constexpr int kWBuf = kWT + WCT_MAX_WINDOW_IMPACTS + 1;       // per-warp weight buffer (floats)
@@ -371,6 +390,7 @@ constexpr int kWItemCap = 384;
 constexpr int kWWCap = 648;        // >= 129 + 513, the bin edges of the largest window
 constexpr int kWBoxCap = 304;
 
+template <bool DET>
 struct WarpSmem {
     DepoDesc d[kWarpDepos];
     int item_off[kWarpDepos + 1];
@@ -383,15 +403,16 @@ struct WarpSmem {
     int pass_end, use_box, box_w0, box_t0, box_nw, box_nt;
     float w[kWWCap];           // per depo: nt + 1 tick edges, then np + 1 impact edges
     float val[kWItemCap];
-    float box[kWBoxCap];
+    typename Acc<DET>::T box[kWBoxCap];
     int tgt[kWItemCap];        // box or grid index of each cached item, -1 off the grid
     uint8_t slot[kWWCap];      // depo of each edge, then of each cached item
 };
 
-__device__ __forceinline__ void raster_warp(WarpSmem &S, const float *__restrict__ t0, const float *__restrict__ x,
+template <bool DET>
+__device__ __forceinline__ void raster_warp(WarpSmem<DET> &S, const float *__restrict__ t0, const float *__restrict__ x,
                                             const float *__restrict__ y, const float *__restrict__ z,
                                             const float *__restrict__ q, int64_t n, const PlaneParams &pp,
-                                            uint32_t event_lo, float *__restrict__ grid, int32_t *status,
+                                            uint32_t event_lo, typename Acc<DET>::T *__restrict__ grid, int32_t *status,
                                             int64_t chunk, const uint32_t (&RK)[20], uint32_t *flags) {
     const int lane = threadIdx.x & 31;
     const int64_t c0 = chunk * kWarpDepos;
@@ -493,7 +514,7 @@ __device__ __forceinline__ void raster_warp(WarpSmem &S, const float *__restrict
         const bool use_box = S.use_box;
         const int bnt = S.box_nt, bw0 = S.box_w0, bt0 = S.box_t0;
         if (use_box)
-            for (int k = lane; k < S.box_nw * bnt; k += 32) S.box[k] = 0.f;
+            for (int k = lane; k < S.box_nw * bnt; k += 32) S.box[k] = 0;
         // depo of every edge (a table instead of a search)
         for (int j = s; j < e; ++j)
             for (int k = S.w_off[j] - w_base + lane; k < S.w_off[j + 1] - w_base; k += 32) S.slot[k] = (uint8_t)j;
@@ -583,8 +604,8 @@ __device__ __forceinline__ void raster_warp(WarpSmem &S, const float *__restrict
                     v = fold_plain(f, wt, wt + d.nt + 1, d.q);
                 }
             }
-            if (use_box) atomicAdd(&S.box[t], v);
-            else atomicAdd(&grid[t], v);
+            if (use_box) Acc<DET>::add(&S.box[t], v);
+            else Acc<DET>::add(&grid[t], v);
         }
         // items beyond the cache (a single very wide depo) are recomputed
         for (int k = kWItemCap + lane; k < n_items; k += 32) {
@@ -600,15 +621,15 @@ __device__ __forceinline__ void raster_warp(WarpSmem &S, const float *__restrict
                 if (sm > 0.f) v *= d.q / sm;
                 else v = fold_plain(f, wt, wt + d.nt + 1, d.q);
             }
-            if (use_box) atomicAdd(&S.box[(f.wire - bw0) * bnt + (f.tick - bt0)], v);
-            else atomicAdd(&grid[(int64_t)f.wire * pp.n_ticks + f.tick], v);
+            if (use_box) Acc<DET>::add(&S.box[(f.wire - bw0) * bnt + (f.tick - bt0)], v);
+            else Acc<DET>::add(&grid[(int64_t)f.wire * pp.n_ticks + f.tick], v);
         }
         __syncwarp();
         if (use_box) {
             const int area = S.box_nw * bnt;
             for (int k = lane; k < area; k += 32) {
-                const float v = S.box[k];
-                if (v != 0.f) {
+                const auto v = S.box[k];
+                if (v != 0) {
                     const int r = k / bnt;
                     atomicAdd(&grid[(int64_t)(bw0 + r) * pp.n_ticks + bt0 + (k - r * bnt)], v);
                 }
@@ -619,21 +640,23 @@ __device__ __forceinline__ void raster_warp(WarpSmem &S, const float *__restrict
     }
 }
 
+template <bool DET>
 __global__ void __launch_bounds__(kWarpsPerCta * 32)
 k_raster_warps(const float *__restrict__ t0, const float *__restrict__ x, const float *__restrict__ y,
                const float *__restrict__ z, const float *__restrict__ q, int64_t n, PlaneParams pp,
-               uint32_t event_lo, float *__restrict__ grid, int32_t *status, uint32_t *flags) {
-    __shared__ WarpSmem S[kWarpsPerCta];
+               uint32_t event_lo, typename Acc<DET>::T *__restrict__ grid, int32_t *status, uint32_t *flags) {
+    __shared__ WarpSmem<DET> S[kWarpsPerCta];
     const int warp = threadIdx.x >> 5;
-    raster_warp(S[warp], t0, x, y, z, q, n, pp, event_lo, grid, status, (int64_t)blockIdx.x * kWarpsPerCta + warp, pp.rk,
-                flags);
+    raster_warp<DET>(S[warp], t0, x, y, z, q, n, pp, event_lo, grid, status, (int64_t)blockIdx.x * kWarpsPerCta + warp,
+                     pp.rk, flags);
 }
 
 // Batched: warp-chunk c of the whole launch belongs to the (event, plane) pair whose chunk
 // range (in warp-chunks) holds c.
+template <bool DET>
 __global__ void __launch_bounds__(kWarpsPerCta * 32)
 k_raster_batch_warps(const BatchTable tab, int32_t *status) {
-    __shared__ WarpSmem S[kWarpsPerCta];
+    __shared__ WarpSmem<DET> S[kWarpsPerCta];
     const int warp = threadIdx.x >> 5;
     const int64_t c = (int64_t)blockIdx.x * kWarpsPerCta + warp;
     int lo = 0, hi = tab.n_items;
@@ -644,8 +667,11 @@ k_raster_batch_warps(const BatchTable tab, int32_t *status) {
     }
     const BatchItem &it = tab.item[lo];
     // every plane shares the seed, hence the round keys: take them from plane 0 (static index)
-    raster_warp(S[warp], it.t0, it.x, it.y, it.z, it.q, it.n, tab.plane[it.plane], it.event_lo, it.grid, status,
-                c - it.chunk_begin, tab.plane[0].rk, it.flags);
+    typename Acc<DET>::T *grid;
+    if constexpr (DET) grid = it.grid64;
+    else grid = it.grid;
+    raster_warp<DET>(S[warp], it.t0, it.x, it.y, it.z, it.q, it.n, tab.plane[it.plane], it.event_lo, grid, status,
+                     c - it.chunk_begin, tab.plane[0].rk, it.flags);
 }
 
 __global__ void __launch_bounds__(kChunkThreads)
@@ -747,21 +773,23 @@ __global__ void k_write_patch_desc(int64_t n, const DepoDesc *__restrict__ desc,
     e[4] = d.np;
 }
 
-// Scatter caller-supplied patches: CTA per tile, items (tick, wire) fold the patch row.
-template <int TW, int TT>
+// Scatter caller-supplied patches: CTA per tile, items (tick, wire) fold the patch row.  The
+// tile is accumulated in shared memory (fixed point in the deterministic mode) and written once.
+template <int TW, int TT, bool DET>
 __global__ void __launch_bounds__(kTileWarps * 32)
 k_tile_scatter_patches(const int64_t *__restrict__ pd, const float *__restrict__ patches,
                        const int32_t *__restrict__ tile_off, const int32_t *__restrict__ tile_list, int64_t list_cap,
                        PlaneParams pp, float *__restrict__ grid) {
     extern __shared__ float4 smem4[];
-    float *tile = reinterpret_cast<float *>(smem4);
+    using T = typename Acc<DET>::T;
+    T *tile = reinterpret_cast<T *>(smem4);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int tile_id = blockIdx.x;
     const int tw = tile_id / pp.n_tiles_t;
     const int tt = tile_id - tw * pp.n_tiles_t;
     const int wire0 = tw * TW, tick0 = tt * TT;
     const int wire_end = min(wire0 + TW, pp.n_wires), tick_end = min(tick0 + TT, pp.n_ticks);
-    for (int i = threadIdx.x; i < TW * TT / 4; i += blockDim.x) smem4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = threadIdx.x; i < TW * TT; i += blockDim.x) tile[i] = 0;
     __syncthreads();
     const int beg = tile_off[tile_id];
     const int end = (int)min((int64_t)tile_off[tile_id + 1], list_cap);
@@ -784,11 +812,20 @@ k_tile_scatter_patches(const int64_t *__restrict__ pd, const float *__restrict__
                 const float *row = patches + off + (int64_t)f.a * np + f.j_base;
                 float s = 0.f;
                 for (int sub = f.sub_lo; sub < f.sub_hi; ++sub) s += row[sub];
-                atomicAdd(&tile[(f.wire - wire0) * TT + (f.tick - tick0)], s);
+                Acc<DET>::add(&tile[(f.wire - wire0) * TT + (f.tick - tick0)], s);
             }
         }
     }
     __syncthreads();
+    if constexpr (DET) {
+        for (int i = threadIdx.x; i < TW * TT; i += blockDim.x) {
+            const int r = i / TT, c = i - r * TT;
+            const int wire = wire0 + r, tick = tick0 + c;
+            if (wire < wire_end && tick < tick_end)
+                grid[(int64_t)wire * pp.n_ticks + tick] = __ll2float_rn((long long)tile[i]) * (1.f / kFixScale);
+        }
+        return;
+    }
     const bool vec = ((pp.n_ticks & 3) == 0) && ((reinterpret_cast<uintptr_t>(grid) & 15) == 0);
     for (int i = threadIdx.x; i < TW * TT / 4; i += blockDim.x) {
         const int r = i / (TT / 4);
@@ -830,11 +867,13 @@ int64_t raster_chunk_count(int64_t n, int schedule) {
     return schedule == 1 ? (n + kChunk - 1) / kChunk : (n + kWarpDepos - 1) / kWarpDepos;
 }
 
-cudaError_t launch_raster_batch(const BatchTable &tab, int64_t total_chunks, int32_t *status, cudaStream_t s) {
+cudaError_t launch_raster_batch(const BatchTable &tab, int64_t total_chunks, int32_t *status, cudaStream_t s,
+                                bool det) {
     if (total_chunks <= 0) return cudaSuccess;
-    if (tab.plane[0].raster_schedule != 1) {
+    if (det || tab.plane[0].raster_schedule != 1) {
         const int64_t blocks = (total_chunks + kWarpsPerCta - 1) / kWarpsPerCta;
-        k_raster_batch_warps<<<(unsigned)blocks, kWarpsPerCta * 32, 0, s>>>(tab, status);
+        if (det) k_raster_batch_warps<true><<<(unsigned)blocks, kWarpsPerCta * 32, 0, s>>>(tab, status);
+        else k_raster_batch_warps<false><<<(unsigned)blocks, kWarpsPerCta * 32, 0, s>>>(tab, status);
         return cudaGetLastError();
     }
     const size_t smem = sizeof(ChunkSmem);
@@ -845,13 +884,17 @@ cudaError_t launch_raster_batch(const BatchTable &tab, int64_t total_chunks, int
 }
 
 cudaError_t launch_raster_chunks(const wct_depos_t &d, const PlaneParams &pp, uint32_t event_lo, float *grid,
-                                 int32_t *status, cudaStream_t s, uint32_t *flags) {
+                                 int32_t *status, cudaStream_t s, uint32_t *flags, unsigned long long *grid64) {
     if (d.n <= 0) return cudaSuccess;
-    if (pp.raster_schedule != 1) {
+    if (grid64 || pp.raster_schedule != 1) {
         const int64_t chunks = (d.n + kWarpDepos - 1) / kWarpDepos;
         const int64_t blocks = (chunks + kWarpsPerCta - 1) / kWarpsPerCta;
-        k_raster_warps<<<(unsigned)blocks, kWarpsPerCta * 32, 0, s>>>(d.t0_us, d.x_mm, d.y_mm, d.z_mm, d.q_e, d.n, pp,
-                                                                      event_lo, grid, status, flags);
+        if (grid64)
+            k_raster_warps<true><<<(unsigned)blocks, kWarpsPerCta * 32, 0, s>>>(d.t0_us, d.x_mm, d.y_mm, d.z_mm, d.q_e,
+                                                                                d.n, pp, event_lo, grid64, status, flags);
+        else
+            k_raster_warps<false><<<(unsigned)blocks, kWarpsPerCta * 32, 0, s>>>(d.t0_us, d.x_mm, d.y_mm, d.z_mm, d.q_e,
+                                                                                 d.n, pp, event_lo, grid, status, flags);
         return cudaGetLastError();
     }
     const size_t smem = sizeof(ChunkSmem);
@@ -869,9 +912,10 @@ cudaError_t launch_raster_chunks(const wct_depos_t &d, const PlaneParams &pp, ui
 // is flattened over (tick, wire, group of four sub-bins) units, one Philox call each, as the
 // counter defines the groups.  With fluctuation the bins are drawn twice: once for the
 // patch's fluctuated sum, once more to add them rescaled to the depo's charge.
+template <bool DET>
 __global__ void __launch_bounds__(kPatchWarps * 32)
 k_raster_phases(int64_t n, const DepoDesc *__restrict__ desc, PlaneParams pp, uint32_t event_lo,
-                float *__restrict__ grids, uint32_t *flags) {
+                typename Acc<DET>::T *__restrict__ grids, uint32_t *flags) {
     __shared__ float wbuf[kPatchWarps][kWBuf];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float *wt = wbuf[warp];
@@ -966,7 +1010,7 @@ k_raster_phases(int64_t n, const DepoDesc *__restrict__ desc, PlaneParams pp, ui
                     const float v = (pp.fluctuate && scale > 0.f) ? fmaxf(fmaf(sfu_sqrt(m * (1.f - w)), z[l], m), 0.f) * scale
                                                                  : m;
                     const int phase = (g << 2) + l;
-                    atomicAdd(&grids[((size_t)phase * pp.n_wires + wire) * pp.n_ticks + tick], v);
+                    Acc<DET>::add(&grids[((size_t)phase * pp.n_wires + wire) * pp.n_ticks + tick], v);
                 }
         }
         __syncwarp();
@@ -974,11 +1018,47 @@ k_raster_phases(int64_t n, const DepoDesc *__restrict__ desc, PlaneParams pp, ui
 }
 
 cudaError_t launch_raster_phases(int64_t n, const DepoDesc *desc, const PlaneParams &pp, uint32_t event_lo,
-                                 float *grids, uint32_t *flags, cudaStream_t s) {
+                                 float *grids, uint32_t *flags, cudaStream_t s, unsigned long long *grids64) {
     if (n <= 0) return cudaSuccess;
     int64_t blocks = (n + kPatchWarps - 1) / kPatchWarps;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    k_raster_phases<<<(unsigned)blocks, kPatchWarps * 32, 0, s>>>(n, desc, pp, event_lo, grids, flags);
+    if (grids64) k_raster_phases<true><<<(unsigned)blocks, kPatchWarps * 32, 0, s>>>(n, desc, pp, event_lo, grids64, flags);
+    else k_raster_phases<false><<<(unsigned)blocks, kPatchWarps * 32, 0, s>>>(n, desc, pp, event_lo, grids, flags);
+    return cudaGetLastError();
+}
+
+// Deterministic mode: the fixed-point tiles listed in `flags` (layout of flag_tiles; the list
+// is only read) are added to the float grid, each value rounded once to float and scaled by
+// 1 / kFixScale (exact), and zeroed again.  One CTA per listed tile, grid-stride; a thread per
+// tick column of the tile.
+__global__ void __launch_bounds__(256)
+k_fix_tiles(const uint32_t *__restrict__ flags, int n_tiles, int n_tiles_t, int tile_w, int tile_t, int n_rows,
+            int n_cols, unsigned long long *__restrict__ g64, float *__restrict__ grid) {
+    const uint32_t count = flags[n_tiles];
+    for (uint32_t i = blockIdx.x; i < count; i += gridDim.x) {
+        const int t = (int)flags[n_tiles + 2 + i];
+        const int tw = t / n_tiles_t, tt = t - tw * n_tiles_t;
+        const int r0 = tw * tile_w, c0 = tt * tile_t;
+        const int r1 = min(r0 + tile_w, n_rows), c1 = min(c0 + tile_t, n_cols);
+        for (int r = r0; r < r1; ++r)
+            for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+                const size_t idx = (size_t)r * n_cols + c;
+                const unsigned long long v = g64[idx];
+                if (v != 0ull) {
+                    grid[idx] += __ll2float_rn((long long)v) * (1.f / kFixScale);
+                    g64[idx] = 0ull;
+                }
+            }
+    }
+}
+
+cudaError_t launch_fix_tiles(const uint32_t *flags, int n_rows, int n_cols, int tile_w, int tile_t,
+                             unsigned long long *g64, float *grid, cudaStream_t s) {
+    const int n_tiles_t = (n_cols + tile_t - 1) / tile_t;
+    const int n_tiles = ((n_rows + tile_w - 1) / tile_w) * n_tiles_t;
+    const int blocks = n_tiles < 2 * 152 ? n_tiles : 2 * 152;
+    if (blocks <= 0) return cudaSuccess;
+    k_fix_tiles<<<blocks, 256, 0, s>>>(flags, n_tiles, n_tiles_t, tile_w, tile_t, n_rows, n_cols, g64, grid);
     return cudaGetLastError();
 }
 
@@ -1037,12 +1117,20 @@ cudaError_t launch_fit_slots(int64_t n, DepoDesc *desc, int64_t slot, int32_t *s
 
 cudaError_t launch_tile_scatter_patches(const int64_t *patch_desc, const float *patches, const int32_t *tile_off,
                                         const int32_t *tile_list, int64_t list_cap, const PlaneParams &pp, float *grid,
-                                        cudaStream_t s) {
+                                        cudaStream_t s, bool det) {
     const int n_tiles = pp.n_tiles_w * pp.n_tiles_t;
     if (n_tiles <= 0) return cudaSuccess;
+    if (det) {
+        const size_t smem = sizeof(unsigned long long) * (size_t)kTileW * kTileT;   // 64 KB
+        auto kern = k_tile_scatter_patches<kTileW, kTileT, true>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<n_tiles, kTileWarps * 32, smem, s>>>(patch_desc, patches, tile_off, tile_list, list_cap, pp, grid);
+        return cudaGetLastError();
+    }
     const size_t smem = sizeof(float) * (size_t)kTileW * kTileT;
-    k_tile_scatter_patches<kTileW, kTileT><<<n_tiles, kTileWarps * 32, smem, s>>>(patch_desc, patches, tile_off,
-                                                                                  tile_list, list_cap, pp, grid);
+    k_tile_scatter_patches<kTileW, kTileT, false><<<n_tiles, kTileWarps * 32, smem, s>>>(patch_desc, patches, tile_off,
+                                                                                         tile_list, list_cap, pp, grid);
     return cudaGetLastError();
 }
 

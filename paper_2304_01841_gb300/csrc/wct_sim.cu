@@ -46,6 +46,8 @@ struct PlaneState {
     size_t phase_grid_bytes = 0;
     uint32_t *phase_flags = nullptr;   // touched-tile flags + list of the phase grids (one grid)
     size_t phase_flag_bytes = 0;
+    unsigned long long *phase_grids64 = nullptr;   // deterministic mode: fixed-point phase grids
+    size_t phase_grid64_bytes = 0;
     int phase_tiles = 0;
     // coloured noise of the digitiser: amplitude per spectrum bin, spectrum and waveform scratch
     float *noise_amp = nullptr;
@@ -75,6 +77,12 @@ struct wct_sim {
     size_t grid_off[kMaxPlanes + 1] = {};
     uint32_t *tile_flags[2] = {};
     size_t flag_off[kMaxPlanes + 1] = {};
+    // Deterministic mode: the rasterizers accumulate fixed-point integers into grids64 (same
+    // offsets as grids, all zero between uses) and launch_fix_tiles moves the touched tiles into
+    // the float grid; det_flags lists the touched tiles when the target is a caller's grid.
+    bool det = false;
+    unsigned long long *grids64[2] = {};
+    uint32_t *det_flags = nullptr;
     cudaEvent_t gev[2] = {};   // run_batch: a grid set's clearing transforms are done
     DepoDesc *desc = nullptr;
     int64_t *patch_size = nullptr, *patch_off = nullptr, *scan64 = nullptr;
@@ -408,29 +416,44 @@ void mark(wct_sim *s, int slot, int k, cudaStream_t st) {
 void clear_grids(wct_sim *s) {
     for (int b = 0; b < 2; ++b) {
         if (s->grids[b]) cudaMemset(s->grids[b], 0, sizeof(float) * s->grid_off[s->n_planes]);
+        if (s->grids64[b]) cudaMemset(s->grids64[b], 0, sizeof(unsigned long long) * s->grid_off[s->n_planes]);
         if (s->tile_flags[b]) cudaMemset(s->tile_flags[b], 0, sizeof(uint32_t) * s->flag_off[s->n_planes]);
     }
     for (int p = 0; p < s->n_planes; ++p) {
         const PlaneState &ps = s->planes[p];
         if (ps.phase_grids) cudaMemset(ps.phase_grids, 0, ps.phase_grid_bytes);
+        if (ps.phase_grids64) cudaMemset(ps.phase_grids64, 0, ps.phase_grid64_bytes);
         if (ps.phase_flags) cudaMemset(ps.phase_flags, 0, ps.phase_flag_bytes);
     }
+    if (s->det_flags) cudaMemset(s->det_flags, 0, sizeof(uint32_t) * s->flag_off[s->n_planes]);
     cudaDeviceSynchronize();
 }
 
 // Fused rasterize + scatter of one plane into `grid` (zeroed first unless it is known to be
 // zero, then accumulated).
+// Deterministic mode: into the fixed-point grid of grid set `gset`, then the touched tiles into
+// `grid` (listed in `flags`, or in det_flags, reset afterwards, when the grid is the caller's).
 wct_status_t raster_scatter(wct_sim *s, int plane, const wct_depos_t *d, float *grid, cudaStream_t st, int slot,
-                            bool clear = true, uint32_t *flags = nullptr) {
+                            bool clear = true, uint32_t *flags = nullptr, int gset = 0) {
     const PlaneState &ps = s->planes[plane];
     const PlaneParams pp = plane_params(s, plane);
     cudaError_t e = clear ? cudaMemsetAsync(grid, 0, sizeof(float) * (size_t)ps.g.n_wires * ps.g.n_ticks, st)
                           : cudaSuccess;
     if (e != cudaSuccess) return cuda_fail(s, e, "grid clear");
     mark(s, slot, 1, st);
-    e = launch_raster_chunks(*d, pp, (uint32_t)d->event_id, grid, s->status, st, flags);
+    if (s->det) {
+        unsigned long long *g64 = s->grids64[gset] + s->grid_off[plane];
+        uint32_t *fl = flags ? flags : s->det_flags + s->flag_off[plane];
+        e = launch_raster_chunks(*d, pp, (uint32_t)d->event_id, grid, s->status, st, fl, g64);
+        if (e == cudaSuccess) e = launch_fix_tiles(fl, ps.g.n_wires, ps.g.n_ticks, pp.tile_w, pp.tile_t, g64, grid, st);
+        if (e == cudaSuccess && !flags)
+            e = cudaMemsetAsync(fl, 0, sizeof(uint32_t) * tile_flag_words(pp), st);
+        s->launches += d->n > 0 ? 2 : 1;
+    } else {
+        e = launch_raster_chunks(*d, pp, (uint32_t)d->event_id, grid, s->status, st, flags);
+        s->launches += d->n > 0 ? 1 : 0;
+    }
     if (e != cudaSuccess) return cuda_fail(s, e, "raster-scatter");
-    s->launches += d->n > 0 ? 1 : 0;
     mark(s, slot, 2, st);
     return WCT_OK;
 }
@@ -500,6 +523,9 @@ void drop_impact(wct_sim *s, PlaneState &ps) {
     dev_free(s, ps.resp_imp, ps.resp_imp_bytes);
     dev_free(s, ps.phase_grids, ps.phase_grid_bytes);
     dev_free(s, ps.phase_flags, ps.phase_flag_bytes);
+    dev_free(s, ps.phase_grids64, ps.phase_grid64_bytes);
+    ps.phase_grids64 = nullptr;
+    ps.phase_grid64_bytes = 0;
     ps.resp_imp = nullptr;
     ps.phase_grids = nullptr;
     ps.phase_flags = nullptr;
@@ -537,9 +563,13 @@ wct_status_t run_plane_impact(wct_sim *s, int p, const wct_depos_t *d, float *wf
     const PlaneParams pp = plane_params(s, p);
     cudaError_t e = launch_prep(*d, pp, s->desc, nullptr, nullptr, s->status, cs);
     if (e == cudaSuccess)
-        e = launch_raster_phases(n, s->desc, pp, (uint32_t)d->event_id, ps.phase_grids, ps.phase_flags, cs);
+        e = launch_raster_phases(n, s->desc, pp, (uint32_t)d->event_id, ps.phase_grids, ps.phase_flags, cs,
+                                 ps.phase_grids64);
+    if (e == cudaSuccess && ps.phase_grids64)
+        e = launch_fix_tiles(ps.phase_flags, ps.n_phases * nw, nt, pp.tile_w, pp.tile_t, ps.phase_grids64,
+                             ps.phase_grids, cs);
     if (e != cudaSuccess) return cuda_fail(s, e, "phase raster");
-    s->launches += n > 0 ? 2 : 0;
+    s->launches += (n > 0 ? 2 : 0) + (ps.phase_grids64 ? 1 : 0);
     mark(s, slot, 2, cs);
     // every phase grid's rows in one forward launch, one wire stage over all phases
     e = launch_row_r2c(ps.fft_imp, ps.phase_grids, nt, nt, ps.n_phases * nw, s->spec_imp, cs, s->status);
@@ -604,6 +634,8 @@ wct_status_t wct_sim_create(const wct_plane_t *planes, int n_planes, const wct_r
         row_schedule = (id & 8) ? 3 : (id & 4) ? 2 : (id & 1);
         raster_schedule = (id >> 1) & 1;
     }
+    s->det = s->opts.deterministic != 0;
+    if (s->det) raster_schedule = 0;   // the fixed-point accumulation exists in the warp-level rasterizer
     wct_status_t st = WCT_OK;
     size_t spec_elems = 0;
     int max_tiles = 1;
@@ -745,6 +777,16 @@ wct_status_t wct_sim_create(const wct_plane_t *planes, int n_planes, const wct_r
         s->grid_off[p + 1] = s->grid_off[p] + (size_t)s->planes[p].g.n_wires * s->planes[p].g.n_ticks;
         s->flag_off[p + 1] = s->flag_off[p] + tile_flag_words(s->planes[p].pp);
     }
+    if (st == WCT_OK && s->det) {
+        for (int b = 0; b < 2 && st == WCT_OK; ++b) {
+            st = dev_alloc(s, (void **)&s->grids64[b], sizeof(unsigned long long) * s->grid_off[n_planes]);
+            if (st == WCT_OK && cudaMemset(s->grids64[b], 0, sizeof(unsigned long long) * s->grid_off[n_planes]))
+                st = fail(s, WCT_ECUDA, "grid init");
+        }
+        if (st == WCT_OK) st = dev_alloc(s, (void **)&s->det_flags, sizeof(uint32_t) * s->flag_off[n_planes]);
+        if (st == WCT_OK && cudaMemset(s->det_flags, 0, sizeof(uint32_t) * s->flag_off[n_planes]))
+            st = fail(s, WCT_ECUDA, "grid init");
+    }
     for (int b = 0; b < 2 && st == WCT_OK; ++b) {
         st = dev_alloc(s, (void **)&s->grids[b], sizeof(float) * s->grid_off[n_planes]);
         if (st == WCT_OK) st = dev_alloc(s, (void **)&s->tile_flags[b], sizeof(uint32_t) * s->flag_off[n_planes]);
@@ -854,7 +896,7 @@ wct_status_t wct_sim_scatter(wct_sim_t *s, int plane, const wct_depos_t *d, cons
         e = launch_fill_patches(d->n, patch_desc, pp, s->tile_off, s->tile_cursor, s->tile_list, s->list_cap,
                                 s->status, cs);
     if (e == cudaSuccess)
-        e = launch_tile_scatter_patches(patch_desc, patches, s->tile_off, s->tile_list, s->list_cap, pp, grid, cs);
+        e = launch_tile_scatter_patches(patch_desc, patches, s->tile_off, s->tile_list, s->list_cap, pp, grid, cs, s->det);
     if (e != cudaSuccess) return cuda_fail(s, e, "scatter patches");
     s->launches += 4 + (d->n > 0 ? 2 : 0);
     return WCT_OK;
@@ -961,6 +1003,7 @@ wct_status_t enqueue_batch(wct_sim *s, const wct_depos_t *events, int n_events, 
             b.q = d.q_e;
             b.n = d.n;
             b.grid = grid;
+            b.grid64 = s->det ? s->grids64[gb] + s->grid_off[p] : nullptr;
             b.flags = s->tile_flags[gb] + s->flag_off[p];
             b.chunk_begin = chunks;
             b.event_lo = (uint32_t)d.event_id;
@@ -968,9 +1011,16 @@ wct_status_t enqueue_batch(wct_sim *s, const wct_depos_t *events, int n_events, 
             chunks += raster_chunk_count(d.n, tab.plane[0].raster_schedule);
         }
         if (chunks > 0) {
-            err = launch_raster_batch(tab, chunks, s->status, rs);
+            err = launch_raster_batch(tab, chunks, s->status, rs, s->det);
             if (err != cudaSuccess) return cuda_fail(s, err, "batched raster-scatter");
             s->launches += 1;
+            for (int i = 0; s->det && i < tab.n_items; ++i) {
+                const BatchItem &b = tab.item[i];
+                const PlaneParams &pp = tab.plane[b.plane];
+                err = launch_fix_tiles(b.flags, pp.n_wires, pp.n_ticks, pp.tile_w, pp.tile_t, b.grid64, b.grid, rs);
+                if (err != cudaSuccess) return cuda_fail(s, err, "fixed-point grid");
+                s->launches += 1;
+            }
         }
         cudaEvent_t done = s->bev[1 + e % (kBatchEvents - 2)];
         err = cudaEventRecord(done, rs);
@@ -1240,6 +1290,12 @@ wct_status_t wct_sim_set_impact_responses(wct_sim_t *s, int plane, const wct_res
         ps.phase_tiles = tiles_w * ps.pp.n_tiles_t;
         ps.phase_flag_bytes = sizeof(uint32_t) * (2 * (size_t)ps.phase_tiles + 2);
         st = dev_alloc(s, (void **)&ps.phase_flags, ps.phase_flag_bytes);
+    }
+    if (st == WCT_OK && s->det) {
+        ps.phase_grid64_bytes = 2 * ps.phase_grid_bytes;
+        st = dev_alloc(s, (void **)&ps.phase_grids64, ps.phase_grid64_bytes);
+        if (st == WCT_OK && cudaMemset(ps.phase_grids64, 0, ps.phase_grid64_bytes) != cudaSuccess)
+            st = fail(s, WCT_ECUDA, "phase grid init");
     }
     if (st == WCT_OK) {
         cudaError_t e = cudaMemset(ps.phase_grids, 0, ps.phase_grid_bytes);
