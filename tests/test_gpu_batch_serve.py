@@ -148,3 +148,49 @@ def test_run_host_matches_run_event():
     sim.sync()
     for p in range(len(planes)):
         assert _close(out_np[0][p], want[p], np.abs(want[p]).max())
+
+
+def test_benchmarked_batch_of_64_three_plane_events_sampled():
+    # the batched configuration the benchmark times: 64 three-plane events (2400/2400/3456 x
+    # 9600), depo counts lognormal 10k..500k cut from track pools, one run_batch replayed from
+    # its graph; one event in 16 against the oracle on every plane
+    import bench
+    import oracle
+    import paper_2304_01841_gb300 as g
+    wl = synth.workload("three_plane")
+    counts = synth.batch_depo_counts(64)
+    pool = [wl.depos(n_depos=500_000, seed=wl.seed + k) for k in range(3)]
+    evs = bench._slice_pool(pool, counts, np.random.default_rng(7), 5000)
+    sim = make_sim(wl.planes, wl.responses(), wl.diffusion)
+    dev = [g.DeviceDepos.from_host(e) for e in evs]
+    outs = [[torch.empty((p.n_wires, p.n_ticks), dtype=torch.float32, device="cuda") for p in wl.planes]
+            for _ in evs]
+    sim.run_batch(dev, outs)
+    sim.run_batch(dev, outs)
+    sim.sync()
+    for e in range(0, 64, 16):
+        for p, pl in enumerate(wl.planes):
+            _, _, ref = oracle.simulate_plane(evs[e], pl, wl.diffusion, wl.responses()[p], plane_index=p)
+            assert rel_l2(to_np(outs[e][p]), ref) <= 1e-4, (e, p)
+
+
+def test_served_apa_mix_sampled():
+    # the served configuration: APA-like planes (800/800/960 x 6000), a heavy-tailed mix of
+    # small events and a 1M-depo one through the event server; the large event and a small one
+    # against the oracle
+    import bench
+    import oracle
+    from paper_2304_01841_gb300.serve import EventServer, pin_depos
+    wl = synth.workload("dune_apa")
+    pool = [wl.depos(n_depos=1_000_000, seed=wl.seed + 1)]
+    counts = [20_000, 1_000_000, 8_000, 45_000, 5_000, 30_000]
+    evs = bench._slice_pool(pool, counts, np.random.default_rng(11), 9000)
+    srv = EventServer(wl.planes, wl.responses(), wl.diffusion, n_slots=4, max_batch=8, hbm_budget_bytes=24 << 30,
+                      keep_results=True)
+    reqs = [srv.submit(pin_depos(e)) for e in evs]
+    srv.drain()
+    for i in (1, 2):
+        for p, pl in enumerate(wl.planes):
+            _, _, ref = oracle.simulate_plane(evs[i], pl, wl.diffusion, wl.responses()[p], plane_index=p)
+            assert rel_l2(np.asarray(reqs[i].waveforms[p]), ref) <= 1e-4, (i, p)
+    srv.close()
