@@ -399,7 +399,7 @@ struct WarpSmem {
     int nw[kWarpDepos];
     float nrm_t[kWarpDepos];
     float nrm_p[kWarpDepos];
-    float sum[kWarpDepos];
+    float sum[kWarpDepos];     // fluctuated sum of each depo's items, then its rescale q / sum
     int pass_end, use_box, box_w0, box_t0, box_nw, box_nt;
     float w[kWWCap];           // per depo: nt + 1 tick edges, then np + 1 impact edges
     float val[kWItemCap];
@@ -586,6 +586,12 @@ __device__ __forceinline__ void raster_warp(WarpSmem<DET> &S, const float *__res
             if (pp.fluctuate) segmented_add(j, v, S.sum);
         }
         __syncwarp();
+        // each depo's fluctuated sum -> its rescale factor q / sum (-1: keep the unfluctuated patch)
+        if (pp.fluctuate && lane < e - s) {
+            const float sm = S.sum[s + lane];
+            S.sum[s + lane] = sm > 0.f ? S.d[s + lane].q / sm : -1.f;
+        }
+        __syncwarp();
         // cached items: target, depo and value were stored by the pass above
         const int n_cached = min(n_items, kWItemCap);
         for (int k = lane; k < n_cached; k += 32) {
@@ -594,9 +600,9 @@ __device__ __forceinline__ void raster_warp(WarpSmem<DET> &S, const float *__res
             const int j = S.slot[k];
             float v = S.val[k];
             if (pp.fluctuate) {
-                const float sm = S.sum[j];
-                if (sm > 0.f) {
-                    v *= S.d[j].q / sm;
+                const float sc = S.sum[j];
+                if (sc > 0.f) {
+                    v *= sc;
                 } else {
                     const DepoDesc &d = S.d[j];
                     const Item f = make_item(i_base + k - S.item_off[j], S.nw[j], S.wl[j], d, pp.n_imp);
@@ -617,8 +623,8 @@ __device__ __forceinline__ void raster_warp(WarpSmem<DET> &S, const float *__res
             float v = pp.fluctuate ? fold_fluct(f, wt, wt + d.nt + 1, d.q, (uint32_t)(c0 + j), pp, c3, RK)
                                    : fold_plain(f, wt, wt + d.nt + 1, d.q);
             if (pp.fluctuate) {
-                const float sm = S.sum[j];
-                if (sm > 0.f) v *= d.q / sm;
+                const float sc = S.sum[j];
+                if (sc > 0.f) v *= sc;
                 else v = fold_plain(f, wt, wt + d.nt + 1, d.q);
             }
             if (use_box) Acc<DET>::add(&S.box[(f.wire - bw0) * bnt + (f.tick - bt0)], v);
