@@ -333,6 +333,12 @@ wct_status_t wct_sim_selftest_wait(wct_sim_t *sim, int64_t limit_cycles, void *s
 /* Human-readable description of the last error on this handle ("" if none). */
 const char *wct_sim_last_error(const wct_sim_t *sim);
 
+/* Fault injection for tests of the error paths: after this call the n-th device allocation
+ * the library makes (n = 0: the next one), in any handle or in wct_sim_create, fails as if the
+ * device were out of memory (WCT_ENOMEM, nothing allocated); later ones succeed again.  n < 0
+ * disarms it.  Process-wide, thread-safe; no device work.  Returns WCT_OK. */
+wct_status_t wct_debug_fail_alloc(int64_t n);
+
 /* The Philox4x32-10 generator the fluctuation uses (Salmon et al., SC'11; §4.1 of the
  * paper), exposed for testing: out[i] = Philox4x32-10(ctr[i], key) for i < n, where ctr
  * and out are DEVICE uint32 [n][4] and key = (seed low word, seed high word). */

@@ -89,6 +89,7 @@ EXPORTS = {
     "wct_sim_selftest_wait": ([c_vp, c_i64, c_vp], ctypes.c_int),
     "wct_sim_last_error": ([c_vp], ctypes.c_char_p),
     "wct_philox4x32_10": ([c_vp, c_u64, c_i64, c_vp, c_vp], ctypes.c_int),
+    "wct_debug_fail_alloc": ([c_i64], ctypes.c_int),
     "wct_convolve_static": ([c_vp, c_i32, c_i32, c_vp, c_i32, c_i32, c_vp, c_vp], ctypes.c_int),
     "wct_response_from_field": ([ctypes.POINTER(wct_field_response_t), c_vp, c_i32, c_dbl, c_i32, c_dbl, c_i32,
                                  c_i32, c_vp, c_vp], ctypes.c_int),

@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <atomic>
 #include <vector>
 
 #include "wct_internal.cuh"
@@ -92,7 +93,7 @@ struct wct_sim {
     int64_t list_cap = 0;
     int32_t *status = nullptr;
     size_t bytes = 0;
-    std::vector<void *> allocs;
+    std::vector<std::pair<void *, size_t>> allocs;   // live device allocations and their sizes
     std::string err;
     // stage timing: one slot of kStages + 1 events per (run_event call, plane)
     bool timing = false;
@@ -131,9 +132,20 @@ wct_status_t cuda_fail(wct_sim *s, cudaError_t e, const char *where) {
     return fail(s, WCT_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
+// Armed by wct_debug_fail_alloc: the allocation that finds the count at 0 fails (-1: disarmed).
+std::atomic<long long> g_fail_alloc{-1};
+
+bool injected_alloc_failure() {
+    long long k = g_fail_alloc.load(std::memory_order_relaxed);
+    while (k >= 0)
+        if (g_fail_alloc.compare_exchange_weak(k, k - 1)) return k == 0;
+    return false;
+}
+
 wct_status_t dev_alloc(wct_sim *s, void **p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
+    if (injected_alloc_failure()) return fail(s, WCT_ENOMEM, "injected allocation failure");
     if (s->opts.hbm_budget_bytes && s->bytes + bytes > s->opts.hbm_budget_bytes)
         return fail(s, WCT_ENOMEM, "scratch would exceed the HBM budget");
     cudaError_t e = cudaMalloc(p, bytes);
@@ -143,16 +155,33 @@ wct_status_t dev_alloc(wct_sim *s, void **p, size_t bytes) {
         return fail(s, WCT_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
     }
     s->bytes += bytes;
-    s->allocs.push_back(*p);
+    s->allocs.emplace_back(*p, bytes);
     return WCT_OK;
 }
 
-void dev_free(wct_sim *s, void *p, size_t bytes) {
+// Free one allocation (null: nothing); the size accounted is the one recorded at allocation.
+void dev_free(wct_sim *s, void *p, size_t /*bytes*/ = 0) {
     if (!p) return;
     cudaFree(p);
-    s->bytes -= bytes;
     for (auto &a : s->allocs)
-        if (a == p) a = nullptr;
+        if (a.first == p) {
+            s->bytes -= a.second;
+            a = {nullptr, 0};
+        }
+}
+
+// Allocate every (pointer, bytes) pair or none: after a failure the ones already taken are
+// freed again and every pointer of the set is null.
+wct_status_t dev_alloc_all(wct_sim *s, std::initializer_list<std::pair<void **, size_t>> set) {
+    wct_status_t st = WCT_OK;
+    for (const auto &a : set)
+        if ((st = dev_alloc(s, a.first, a.second)) != WCT_OK) break;
+    if (st != WCT_OK)
+        for (const auto &a : set) {
+            dev_free(s, *a.first);
+            *a.first = nullptr;
+        }
+    return st;
 }
 
 bool smooth7(int64_t m) {
@@ -370,12 +399,12 @@ wct_status_t ensure_depo_capacity(wct_sim *s, int64_t n) {
     }
     int per = 1;
     for (int p = 0; p < s->n_planes; ++p) per = std::max(per, s->planes[p].max_tiles_per_depo);
-    wct_status_t st;
-    if ((st = dev_alloc(s, (void **)&s->desc, sizeof(DepoDesc) * cap))) return st;
-    if ((st = dev_alloc(s, (void **)&s->patch_size, sizeof(int64_t) * cap))) return st;
-    if ((st = dev_alloc(s, (void **)&s->patch_off, sizeof(int64_t) * (cap + 1)))) return st;
-    if ((st = dev_alloc(s, (void **)&s->scan64, sizeof(int64_t) * scan_tmp_elems(cap)))) return st;
-    if ((st = dev_alloc(s, (void **)&s->tile_list, sizeof(int32_t) * cap * per))) return st;
+    const wct_status_t st = dev_alloc_all(s, {{(void **)&s->desc, sizeof(DepoDesc) * cap},
+                                              {(void **)&s->patch_size, sizeof(int64_t) * cap},
+                                              {(void **)&s->patch_off, sizeof(int64_t) * (cap + 1)},
+                                              {(void **)&s->scan64, sizeof(int64_t) * scan_tmp_elems(cap)},
+                                              {(void **)&s->tile_list, sizeof(int32_t) * cap * per}});
+    if (st) return st;
     s->depo_cap = cap;
     s->list_cap = cap * per;
     return WCT_OK;
@@ -798,8 +827,8 @@ wct_status_t wct_sim_create(const wct_plane_t *planes, int n_planes, const wct_r
         }
     }
     if (st != WCT_OK) {
-        for (void *a : s->allocs)
-            if (a) cudaFree(a);
+        for (auto &a : s->allocs)
+            if (a.first) cudaFree(a.first);
         delete s;
         return st;
     }
@@ -810,8 +839,8 @@ wct_status_t wct_sim_create(const wct_plane_t *planes, int n_planes, const wct_r
 wct_status_t wct_sim_destroy(wct_sim_t *s) {
     if (!s) return WCT_EINVAL;
     cudaDeviceSynchronize();
-    for (void *a : s->allocs)
-        if (a) cudaFree(a);
+    for (auto &a : s->allocs)
+        if (a.first) cudaFree(a.first);
     for (auto &slot : s->slots)
         for (auto &e : slot) cudaEventDestroy(e);
     for (auto &g : s->graphs) cudaGraphExecDestroy(g.exec);
@@ -1166,20 +1195,29 @@ wct_status_t wct_sim_run_host(wct_sim_t *s, const wct_host_depos_t *events, int 
     }
     wct_status_t st = WCT_OK;
     if (!s->h_wave[0][0]) {
+        // all staging waveforms or none (a failed first call leaves nothing half-allocated)
         for (int b = 0; b < 2 && st == WCT_OK; ++b)
             for (int p = 0; p < npl && st == WCT_OK; ++p)
                 st = dev_alloc(s, (void **)&s->h_wave[b][p],
                                sizeof(float) * (size_t)s->planes[p].g.n_wires * s->planes[p].g.n_ticks);
-        if (st) return st;
+        if (st) {
+            for (int b = 0; b < 2; ++b)
+                for (int p = 0; p < npl; ++p) {
+                    dev_free(s, s->h_wave[b][p]);
+                    s->h_wave[b][p] = nullptr;
+                }
+            return st;
+        }
     }
     if (max_n > s->h_cap) {
         // earlier calls returned only after their streams drained: the old staging is idle
         for (int b = 0; b < 2; ++b) {
-            dev_free(s, s->h_depo[b], sizeof(float) * 5 * (size_t)s->h_cap);
+            dev_free(s, s->h_depo[b]);
             s->h_depo[b] = nullptr;
         }
         s->h_cap = 0;
-        for (int b = 0; b < 2 && st == WCT_OK; ++b) st = dev_alloc(s, (void **)&s->h_depo[b], sizeof(float) * 5 * (size_t)max_n);
+        st = dev_alloc_all(s, {{(void **)&s->h_depo[0], sizeof(float) * 5 * (size_t)max_n},
+                               {(void **)&s->h_depo[1], sizeof(float) * 5 * (size_t)max_n}});
         if (st) return st;
         s->h_cap = max_n;
     }
@@ -1273,13 +1311,16 @@ wct_status_t wct_sim_set_impact_responses(wct_sim_t *s, int plane, const wct_res
     // spectrum scratch must hold n_wires x Fu
     const size_t need = (size_t)ps.g.n_wires * Fu;
     if (st == WCT_OK && need > s->spec_elems) {
-        dev_free(s, s->spec, sizeof(float2) * s->spec_elems);
-        dev_free(s, s->spec2, sizeof(float2) * s->spec_elems);
-        s->spec = s->spec2 = nullptr;
-        s->spec_elems = 0;
-        st = dev_alloc(s, (void **)&s->spec, sizeof(float2) * need);
-        if (st == WCT_OK) st = dev_alloc(s, (void **)&s->spec2, sizeof(float2) * need);
-        if (st == WCT_OK) s->spec_elems = need;
+        // the folded mode keeps using the old scratch if the larger one cannot be had
+        float2 *a = nullptr, *b = nullptr;
+        st = dev_alloc_all(s, {{(void **)&a, sizeof(float2) * need}, {(void **)&b, sizeof(float2) * need}});
+        if (st == WCT_OK) {
+            dev_free(s, s->spec);
+            dev_free(s, s->spec2);
+            s->spec = a;
+            s->spec2 = b;
+            s->spec_elems = need;
+        }
     }
     if (st == WCT_OK) {
         ps.phase_grid_bytes = sizeof(float) * (size_t)n_phases * ps.g.n_wires * ps.g.n_ticks;
@@ -1507,6 +1548,11 @@ wct_status_t wct_sim_selftest_wait(wct_sim_t *s, int64_t limit_cycles, void *str
     if (!s || limit_cycles < 0) return WCT_EINVAL;
     cudaError_t e = launch_wait_selftest((long long)limit_cycles, s->status, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "wait self-test");
+    return WCT_OK;
+}
+
+wct_status_t wct_debug_fail_alloc(int64_t n) {
+    g_fail_alloc.store(n < 0 ? -1 : (long long)n);
     return WCT_OK;
 }
 

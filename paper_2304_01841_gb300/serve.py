@@ -15,6 +15,12 @@ up to the FP32 summation order of the scatter.
 
 The scheduling logic (admission, budget, FIFO order) is independent of the device: the device
 work goes through a backend object (`CudaBackend` here; tests drive the scheduler with a fake).
+
+Failures stay with their batch: if a backend's launch or retire raises (an invalid event, an
+allocation beyond the budget, a device error reported at sync), every request of that batch
+completes with `error` set, its memory is released and the server carries on with the others.
+A pending request can be cancelled (it is never launched); cancelling one already on the
+device only drops its results.
 """
 from __future__ import annotations
 
@@ -36,6 +42,8 @@ class Request:
     t_done: float = 0.0
     waveforms: Optional[List] = None   # host float32 arrays, one per plane (if keep_results)
     done: threading.Event = field(default_factory=threading.Event)
+    cancelled: bool = False            # cancel() was called: no results are kept
+    error: Optional[BaseException] = None   # the device work of its batch failed
 
     @property
     def latency(self) -> float:
@@ -133,6 +141,33 @@ class EventServer:
             self.pending.append(r)
         return r
 
+    def cancel(self, r: Request) -> bool:
+        """Cancel a request: True if it was still pending (it completes now, never launched);
+        False if it is already on the device or done (its results, if any, are dropped)."""
+        with self.lock:
+            r.cancelled = True
+            if r in self.pending:
+                self.pending.remove(r)
+                r.t_done = time.perf_counter()
+                r.done.set()
+                self.completed.append(r)
+                return True
+        r.waveforms = None
+        return False
+
+    def _finish(self, slot: "_Slot", error: Optional[BaseException]):
+        now = time.perf_counter()
+        for r in slot.batch:
+            r.t_done = now
+            if error is not None:
+                r.error = error
+            if r.cancelled or error is not None:
+                r.waveforms = None
+            r.done.set()
+            self.completed.append(r)
+        self.in_use -= slot.bytes
+        slot.batch, slot.bytes = [], 0
+
     def request_bytes(self, r: Request) -> int:
         return 20 * int(len(r.depos.t0)) + self.plane_bytes
 
@@ -142,14 +177,12 @@ class EventServer:
         Returns the number of requests still pending or in flight."""
         for slot in self.slots:
             if slot.batch and slot.backend.done():
-                now = time.perf_counter()
-                slot.backend.retire(slot.batch)
-                for r in slot.batch:
-                    r.t_done = now
-                    r.done.set()
-                    self.completed.append(r)
-                self.in_use -= slot.bytes
-                slot.batch, slot.bytes = [], 0
+                err = None
+                try:
+                    slot.backend.retire(slot.batch)
+                except Exception as e:          # noqa: BLE001 - the batch carries the error
+                    err = e
+                self._finish(slot, err)
         for slot in self.slots:
             if slot.batch:
                 continue
@@ -169,7 +202,10 @@ class EventServer:
                 r.t_admit = now
             slot.batch, slot.bytes = batch, need_total
             self.in_use += need_total
-            slot.backend.launch(batch)
+            try:
+                slot.backend.launch(batch)
+            except Exception as e:              # noqa: BLE001 - the batch carries the error
+                self._finish(slot, e)
         with self.lock:
             return len(self.pending) + sum(len(s.batch) for s in self.slots)
 

@@ -84,3 +84,53 @@ def test_requests_arriving_later_join_as_slots_free():
     srv.drain()
     launches = [b for kind, _, b in FakeBackend.log if kind == "launch"]
     assert launches[0] == (0,) and launches[1] == (1, 2, 3)
+
+
+class FailingBackend(FakeBackend):
+    """Raises on the launch (or the retire) of any batch holding a request id in `bad`."""
+
+    def __init__(self, bad, where, passes=2):
+        super().__init__(passes)
+        self.bad, self.where = set(bad), where
+
+    def launch(self, batch):
+        super().launch(batch)
+        if self.where == "launch" and self.bad & {r.rid for r in batch}:
+            raise RuntimeError("injected launch failure")
+
+    def retire(self, batch):
+        super().retire(batch)
+        if self.where == "retire" and self.bad & {r.rid for r in batch}:
+            raise RuntimeError("injected device error at sync")
+
+
+def test_cancel_pending_and_in_flight():
+    srv = _server(passes=3, n_slots=1, max_batch=1, hbm_budget_bytes=1 << 30)
+    reqs = [srv.submit(_depos(10)) for _ in range(4)]
+    srv.step()                                       # request 0 on the device
+    assert srv.cancel(reqs[2]) is True               # pending: never launched
+    assert reqs[2].done.is_set() and reqs[2].cancelled
+    assert srv.cancel(reqs[0]) is False              # in flight: finishes, results dropped
+    srv.drain()
+    launched = [rid for kind, _, b in FakeBackend.log if kind == "launch" for rid in b]
+    assert launched == [0, 1, 3]
+    assert all(r.done.is_set() for r in reqs)
+    assert reqs[0].cancelled and reqs[0].waveforms is None and reqs[0].error is None
+    assert not reqs[1].cancelled and not reqs[3].cancelled
+    assert srv.in_use == 0
+
+
+def test_failed_batches_complete_with_their_error_and_the_server_carries_on():
+    for where in ("launch", "retire"):
+        FakeBackend.log = []
+        srv = EventServer(PLANES, None, None, n_slots=2, max_batch=2, hbm_budget_bytes=1 << 30,
+                          backend_factory=lambda: FailingBackend({3}, where))
+        reqs = [srv.submit(_depos(10)) for _ in range(8)]
+        srv.drain()
+        assert all(r.done.is_set() for r in reqs)
+        failed = [r.rid for r in reqs if r.error is not None]
+        batch_of_3 = next(b for kind, _, b in FakeBackend.log if kind == "launch" and 3 in b)
+        assert sorted(failed) == sorted(batch_of_3), where      # only the failing batch
+        assert all("injected" in str(reqs[i].error) for i in failed)
+        assert sorted(r.rid for r in srv.completed) == list(range(8))
+        assert srv.in_use == 0
