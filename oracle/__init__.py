@@ -64,11 +64,15 @@ def build(force: bool = False) -> str:
 
 
 def lib():
+    """The compiled oracle (built on first use).  $WCT_ORACLE_LIB names another build of the
+    same source instead (the sanitizer test loads an ASan / UBSan build this way)."""
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            L = ctypes.CDLL(_LIB)
+            path = os.environ.get("WCT_ORACLE_LIB")
+            if not path:
+                path = build()
+            L = ctypes.CDLL(path)
             P = ctypes.c_void_p
             i64, i32, u64, dbl = ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_double
             L.or_philox_batch.argtypes = [i64, P, P, P]
