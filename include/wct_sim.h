@@ -339,6 +339,14 @@ const char *wct_sim_last_error(const wct_sim_t *sim);
  * disarms it.  Process-wide, thread-safe; no device work.  Returns WCT_OK. */
 wct_status_t wct_debug_fail_alloc(int64_t n);
 
+/* Bounds-checked builds (compiled with -DWCT_BOUNDS_CHECK; a debugging aid standing in for a
+ * memory checker): the kernels check the computed indices of the scatter targets, shared-memory
+ * boxes, ring slots, tile clears and conversions before use; a violation skips the access,
+ * makes the next wct_sim_sync return WCT_EDEVICE and records the first one.  out (HOST int64
+ * [3]) receives {source line, index, limit} of that first violation, or zeros.  Synchronous.
+ * Returns WCT_OK in a bounds-checked build, WCT_EINVAL in a release build (nothing recorded). */
+wct_status_t wct_debug_bounds(wct_sim_t *sim, int64_t *out);
+
 /* The Philox4x32-10 generator the fluctuation uses (Salmon et al., SC'11; §4.1 of the
  * paper), exposed for testing: out[i] = Philox4x32-10(ctr[i], key) for i < n, where ctr
  * and out are DEVICE uint32 [n][4] and key = (seed low word, seed high word). */

@@ -90,6 +90,7 @@ EXPORTS = {
     "wct_sim_last_error": ([c_vp], ctypes.c_char_p),
     "wct_philox4x32_10": ([c_vp, c_u64, c_i64, c_vp, c_vp], ctypes.c_int),
     "wct_debug_fail_alloc": ([c_i64], ctypes.c_int),
+    "wct_debug_bounds": ([c_vp, ctypes.POINTER(c_i64)], ctypes.c_int),
     "wct_convolve_static": ([c_vp, c_i32, c_i32, c_vp, c_i32, c_i32, c_vp, c_vp], ctypes.c_int),
     "wct_response_from_field": ([ctypes.POINTER(wct_field_response_t), c_vp, c_i32, c_dbl, c_i32, c_dbl, c_i32,
                                  c_i32, c_vp, c_vp], ctypes.c_int),
@@ -104,12 +105,13 @@ def lib_path() -> str:
 
 
 def load(build_if_missing: bool = False):
-    """Load the CUDA library (building it first only if asked)."""
+    """Load the CUDA library (building it first only if asked).  $WCT_LIB names another build
+    of the same sources instead (e.g. the bounds-checked one, build.build(bounds_check=True))."""
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
-        path = _build.LIB
+        path = os.environ.get("WCT_LIB") or _build.LIB
         if not os.path.exists(path):
             if not build_if_missing:
                 raise RuntimeError(f"CUDA library not built ({path}); run __graft_entry__.build() first")

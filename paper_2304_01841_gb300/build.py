@@ -38,8 +38,13 @@ def _stale(outputs, inputs) -> bool:
     return any(os.path.getmtime(i) > t_out for i in inputs)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = False, bounds_check: bool = False) -> str:
+    """Compile every translation unit (in parallel, only what changed) and link the library.
+    bounds_check builds the debugging variant (-DWCT_BOUNDS_CHECK: the kernels check their
+    computed indices) into _build_checked/ instead; returns the library's path."""
     nvcc = _nvcc()
+    BUILD = os.path.join(HERE, "_build_checked" if bounds_check else "_build")
+    LIB = os.path.join(BUILD, "libwctsim_checked.so" if bounds_check else "libwctsim.so")
     os.makedirs(BUILD, exist_ok=True)
     hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(HERE, "..", "include", "wct_sim.h"),
                                                        os.path.abspath(__file__)]
@@ -47,6 +52,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
                      "--expt-relaxed-constexpr", "-I", os.path.join(HERE, "..", "include")]
     if ptxas_verbose:
         common += ["-Xptxas", "-v"]
+    if bounds_check:
+        common += ["-DWCT_BOUNDS_CHECK"]
     objs = []
     jobs = []
     for src in SOURCES:

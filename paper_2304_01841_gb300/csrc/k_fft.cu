@@ -1073,8 +1073,9 @@ k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, in
                 fence_proxy_async_smem();
                 mbar_arrive_expect_tx(&full[gs], row_bytes * (uint32_t)(r1 - r0));
                 for (int r = r0; r < r1; ++r)
-                    bulk_g2s(ring[gs * kGroupRows + (r - r0)], Sp + (size_t)(w0 - KC + m_lo + r) * Fs + f0, row_bytes,
-                             &full[gs]);
+                    if (WCT_IDX_OK(status, w0 - KC + m_lo + r, n_wires))
+                        bulk_g2s(ring[gs * kGroupRows + (r - r0)], Sp + (size_t)(w0 - KC + m_lo + r) * Fs + f0,
+                                 row_bytes, &full[gs]);
             }
         }
         return;
@@ -1102,7 +1103,8 @@ k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, in
                 set_status(status, ST_ETIMEOUT);
                 ok = false;
             }
-            if (ok && live) x = ring[gs * kGroupRows + in_g][tid];
+            if (ok && live && WCT_IDX_OK(status, gs * kGroupRows + in_g, kRingGroups * kGroupRows))
+                x = ring[gs * kGroupRows + in_g][tid];
             if (in_g == kGroupRows - 1 || idx == n_rows - 1)
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[gs])) : "memory");
         }
@@ -1142,7 +1144,7 @@ k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, in
             }
             A = add2(A, A2);
             B = add2(B, B2);
-            if (live && b + j < n_out) {
+            if (live && b + j < n_out && WCT_IDX_OK(status, (int64_t)(w0 + b + j) * Fs + f, (int64_t)n_wires * Fs)) {
                 float2 v = make_float2(A.x - B.y, A.y + B.x);
                 float2 *dst = &T[(size_t)(w0 + b + j) * Fs + f];
                 if (acc) v = cadd(v, *dst);

@@ -511,8 +511,9 @@ __device__ __forceinline__ void raster_warp(WarpSmem<DET> &S, const float *__res
         const int i_base = S.item_off[s];
         const int n_w = S.w_off[e] - S.w_off[s];
         const int w_base = S.w_off[s];
-        const bool use_box = S.use_box;
+        const bool use_box = S.use_box && WCT_IDX_OK(status, S.box_nw * S.box_nt - 1, kWBoxCap);
         const int bnt = S.box_nt, bw0 = S.box_w0, bt0 = S.box_t0;
+        if (!WCT_IDX_OK(status, n_w, kWWCap + 1)) break;   // never: the pass planning caps n_w
         if (use_box)
             for (int k = lane; k < S.box_nw * bnt; k += 32) S.box[k] = 0;
         // depo of every edge (a table instead of a search)
@@ -610,8 +611,11 @@ __device__ __forceinline__ void raster_warp(WarpSmem<DET> &S, const float *__res
                     v = fold_plain(f, wt, wt + d.nt + 1, d.q);
                 }
             }
-            if (use_box) Acc<DET>::add(&S.box[t], v);
-            else Acc<DET>::add(&grid[t], v);
+            if (use_box) {
+                if (WCT_IDX_OK(status, t, S.box_nw * bnt)) Acc<DET>::add(&S.box[t], v);
+            } else if (WCT_IDX_OK(status, t, (int64_t)pp.n_wires * pp.n_ticks)) {
+                Acc<DET>::add(&grid[t], v);
+            }
         }
         // items beyond the cache (a single very wide depo) are recomputed
         for (int k = kWItemCap + lane; k < n_items; k += 32) {
@@ -627,8 +631,13 @@ __device__ __forceinline__ void raster_warp(WarpSmem<DET> &S, const float *__res
                 if (sc > 0.f) v *= sc;
                 else v = fold_plain(f, wt, wt + d.nt + 1, d.q);
             }
-            if (use_box) Acc<DET>::add(&S.box[(f.wire - bw0) * bnt + (f.tick - bt0)], v);
-            else Acc<DET>::add(&grid[(int64_t)f.wire * pp.n_ticks + f.tick], v);
+            if (use_box) {
+                const int t = (f.wire - bw0) * bnt + (f.tick - bt0);
+                if (WCT_IDX_OK(status, t, S.box_nw * bnt)) Acc<DET>::add(&S.box[t], v);
+            } else {
+                const int64_t t = (int64_t)f.wire * pp.n_ticks + f.tick;
+                if (WCT_IDX_OK(status, t, (int64_t)pp.n_wires * pp.n_ticks)) Acc<DET>::add(&grid[t], v);
+            }
         }
         __syncwarp();
         if (use_box) {
@@ -637,7 +646,8 @@ __device__ __forceinline__ void raster_warp(WarpSmem<DET> &S, const float *__res
                 const auto v = S.box[k];
                 if (v != 0) {
                     const int r = k / bnt;
-                    atomicAdd(&grid[(int64_t)(bw0 + r) * pp.n_ticks + bt0 + (k - r * bnt)], v);
+                    const int64_t t = (int64_t)(bw0 + r) * pp.n_ticks + bt0 + (k - r * bnt);
+                    if (WCT_IDX_OK(status, t, (int64_t)pp.n_wires * pp.n_ticks)) atomicAdd(&grid[t], v);
                 }
             }
         }
@@ -785,7 +795,7 @@ template <int TW, int TT, bool DET>
 __global__ void __launch_bounds__(kTileWarps * 32)
 k_tile_scatter_patches(const int64_t *__restrict__ pd, const float *__restrict__ patches,
                        const int32_t *__restrict__ tile_off, const int32_t *__restrict__ tile_list, int64_t list_cap,
-                       PlaneParams pp, float *__restrict__ grid) {
+                       PlaneParams pp, float *__restrict__ grid, int32_t *status) {
     extern __shared__ float4 smem4[];
     using T = typename Acc<DET>::T;
     T *tile = reinterpret_cast<T *>(smem4);
@@ -818,7 +828,8 @@ k_tile_scatter_patches(const int64_t *__restrict__ pd, const float *__restrict__
                 const float *row = patches + off + (int64_t)f.a * np + f.j_base;
                 float s = 0.f;
                 for (int sub = f.sub_lo; sub < f.sub_hi; ++sub) s += row[sub];
-                Acc<DET>::add(&tile[(f.wire - wire0) * TT + (f.tick - tick0)], s);
+                const int t = (f.wire - wire0) * TT + (f.tick - tick0);
+                if (WCT_IDX_OK(status, t, TW * TT)) Acc<DET>::add(&tile[t], s);
             }
         }
     }
@@ -921,7 +932,7 @@ cudaError_t launch_raster_chunks(const wct_depos_t &d, const PlaneParams &pp, ui
 template <bool DET>
 __global__ void __launch_bounds__(kPatchWarps * 32)
 k_raster_phases(int64_t n, const DepoDesc *__restrict__ desc, PlaneParams pp, uint32_t event_lo,
-                typename Acc<DET>::T *__restrict__ grids, uint32_t *flags) {
+                typename Acc<DET>::T *__restrict__ grids, uint32_t *flags, int32_t *status) {
     __shared__ float wbuf[kPatchWarps][kWBuf];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float *wt = wbuf[warp];
@@ -1016,7 +1027,8 @@ k_raster_phases(int64_t n, const DepoDesc *__restrict__ desc, PlaneParams pp, ui
                     const float v = (pp.fluctuate && scale > 0.f) ? fmaxf(fmaf(sfu_sqrt(m * (1.f - w)), z[l], m), 0.f) * scale
                                                                  : m;
                     const int phase = (g << 2) + l;
-                    Acc<DET>::add(&grids[((size_t)phase * pp.n_wires + wire) * pp.n_ticks + tick], v);
+                    const int64_t t = ((int64_t)phase * pp.n_wires + wire) * pp.n_ticks + tick;
+                    if (WCT_IDX_OK(status, t, (int64_t)n_imp * pp.n_wires * pp.n_ticks)) Acc<DET>::add(&grids[t], v);
                 }
         }
         __syncwarp();
@@ -1024,12 +1036,15 @@ k_raster_phases(int64_t n, const DepoDesc *__restrict__ desc, PlaneParams pp, ui
 }
 
 cudaError_t launch_raster_phases(int64_t n, const DepoDesc *desc, const PlaneParams &pp, uint32_t event_lo,
-                                 float *grids, uint32_t *flags, cudaStream_t s, unsigned long long *grids64) {
+                                 float *grids, uint32_t *flags, cudaStream_t s, unsigned long long *grids64,
+                                 int32_t *status) {
     if (n <= 0) return cudaSuccess;
     int64_t blocks = (n + kPatchWarps - 1) / kPatchWarps;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    if (grids64) k_raster_phases<true><<<(unsigned)blocks, kPatchWarps * 32, 0, s>>>(n, desc, pp, event_lo, grids64, flags);
-    else k_raster_phases<false><<<(unsigned)blocks, kPatchWarps * 32, 0, s>>>(n, desc, pp, event_lo, grids, flags);
+    if (grids64)
+        k_raster_phases<true><<<(unsigned)blocks, kPatchWarps * 32, 0, s>>>(n, desc, pp, event_lo, grids64, flags, status);
+    else
+        k_raster_phases<false><<<(unsigned)blocks, kPatchWarps * 32, 0, s>>>(n, desc, pp, event_lo, grids, flags, status);
     return cudaGetLastError();
 }
 
@@ -1039,10 +1054,11 @@ cudaError_t launch_raster_phases(int64_t n, const DepoDesc *desc, const PlanePar
 // tick column of the tile.
 __global__ void __launch_bounds__(256)
 k_fix_tiles(const uint32_t *__restrict__ flags, int n_tiles, int n_tiles_t, int tile_w, int tile_t, int n_rows,
-            int n_cols, unsigned long long *__restrict__ g64, float *__restrict__ grid) {
+            int n_cols, unsigned long long *__restrict__ g64, float *__restrict__ grid, int32_t *status) {
     const uint32_t count = flags[n_tiles];
     for (uint32_t i = blockIdx.x; i < count; i += gridDim.x) {
         const int t = (int)flags[n_tiles + 2 + i];
+        if (!WCT_IDX_OK(status, t, n_tiles)) continue;
         const int tw = t / n_tiles_t, tt = t - tw * n_tiles_t;
         const int r0 = tw * tile_w, c0 = tt * tile_t;
         const int r1 = min(r0 + tile_w, n_rows), c1 = min(c0 + tile_t, n_cols);
@@ -1059,12 +1075,12 @@ k_fix_tiles(const uint32_t *__restrict__ flags, int n_tiles, int n_tiles_t, int 
 }
 
 cudaError_t launch_fix_tiles(const uint32_t *flags, int n_rows, int n_cols, int tile_w, int tile_t,
-                             unsigned long long *g64, float *grid, cudaStream_t s) {
+                             unsigned long long *g64, float *grid, cudaStream_t s, int32_t *status) {
     const int n_tiles_t = (n_cols + tile_t - 1) / tile_t;
     const int n_tiles = ((n_rows + tile_w - 1) / tile_w) * n_tiles_t;
     const int blocks = n_tiles < 2 * 152 ? n_tiles : 2 * 152;
     if (blocks <= 0) return cudaSuccess;
-    k_fix_tiles<<<blocks, 256, 0, s>>>(flags, n_tiles, n_tiles_t, tile_w, tile_t, n_rows, n_cols, g64, grid);
+    k_fix_tiles<<<blocks, 256, 0, s>>>(flags, n_tiles, n_tiles_t, tile_w, tile_t, n_rows, n_cols, g64, grid, status);
     return cudaGetLastError();
 }
 
@@ -1123,7 +1139,7 @@ cudaError_t launch_fit_slots(int64_t n, DepoDesc *desc, int64_t slot, int32_t *s
 
 cudaError_t launch_tile_scatter_patches(const int64_t *patch_desc, const float *patches, const int32_t *tile_off,
                                         const int32_t *tile_list, int64_t list_cap, const PlaneParams &pp, float *grid,
-                                        cudaStream_t s, bool det) {
+                                        cudaStream_t s, bool det, int32_t *status) {
     const int n_tiles = pp.n_tiles_w * pp.n_tiles_t;
     if (n_tiles <= 0) return cudaSuccess;
     if (det) {
@@ -1131,12 +1147,12 @@ cudaError_t launch_tile_scatter_patches(const int64_t *patch_desc, const float *
         auto kern = k_tile_scatter_patches<kTileW, kTileT, true>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        kern<<<n_tiles, kTileWarps * 32, smem, s>>>(patch_desc, patches, tile_off, tile_list, list_cap, pp, grid);
+        kern<<<n_tiles, kTileWarps * 32, smem, s>>>(patch_desc, patches, tile_off, tile_list, list_cap, pp, grid, status);
         return cudaGetLastError();
     }
     const size_t smem = sizeof(float) * (size_t)kTileW * kTileT;
-    k_tile_scatter_patches<kTileW, kTileT, false><<<n_tiles, kTileWarps * 32, smem, s>>>(patch_desc, patches, tile_off,
-                                                                                         tile_list, list_cap, pp, grid);
+    k_tile_scatter_patches<kTileW, kTileT, false><<<n_tiles, kTileWarps * 32, smem, s>>>(
+        patch_desc, patches, tile_off, tile_list, list_cap, pp, grid, status);
     return cudaGetLastError();
 }
 

@@ -104,6 +104,29 @@ __device__ __forceinline__ void set_status(int32_t *status, int32_t code) {
     if (status) atomicCAS(status, 0, code);
 }
 
+// Bounds-checked build (-DWCT_BOUNDS_CHECK, a debugging aid in place of a memory checker): the
+// computed indices of the scatter targets, shared-memory boxes, ring slots, tile clears and
+// conversions are checked before use.  A violation skips the access, sets the status word to
+// WCT_EDEVICE and records the first (source line, index, limit) in status[1..3] (read by
+// wct_debug_bounds).  The release build compiles every check to `true`.
+#ifdef WCT_BOUNDS_CHECK
+static __device__ __noinline__ bool bounds_fail(int32_t *status, long long i, long long n, int line) {
+    if (status) {
+        atomicCAS(status, 0, ST_EDEVICE);
+        if (atomicCAS(status + 1, 0, line) == 0) {
+            status[2] = (int32_t)i;
+            status[3] = (int32_t)n;
+        }
+    }
+    return false;
+}
+#define WCT_IDX_OK(status, i, n) \
+    ((unsigned long long)(long long)(i) < (unsigned long long)(long long)(n) ? true \
+                                                                             : bounds_fail((status), (i), (n), __LINE__))
+#else
+#define WCT_IDX_OK(status, i, n) true
+#endif
+
 // +-nsigma window on one axis, decided in FP64 with explicitly rounded operations so the
 // bounds match a host FP64 evaluation of the same expressions bit for bit.
 __device__ __forceinline__ void axis_window(double mu, double s, double nsigma, long long &lo, long long &n) {

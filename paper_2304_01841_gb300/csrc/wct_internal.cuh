@@ -102,7 +102,7 @@ cudaError_t launch_raster_batch(const BatchTable &tab, int64_t total_chunks, int
 // grid[r][c] += g64[r][c] / kFixScale and g64[r][c] = 0 over the tiles listed in flags (the
 // flag layout below, for an n_rows x n_cols grid with tile_w x tile_t tiles; flags only read)
 cudaError_t launch_fix_tiles(const uint32_t *flags, int n_rows, int n_cols, int tile_w, int tile_t,
-                             unsigned long long *g64, float *grid, cudaStream_t s);
+                             unsigned long long *g64, float *grid, cudaStream_t s, int32_t *status = nullptr);
 // Touched-tile flags: the fused rasterizers set flags[tile] = 1 for every tile (tile_w wires x
 // tile_t ticks, pp's tiling) that a depo's window overlaps and list each such tile once
 // (flags: n_tiles flags, a count, a done-counter, the list; tile_flag_words(pp) words, all
@@ -169,7 +169,7 @@ cudaError_t launch_fill_patches(int64_t n, const int64_t *patch_desc, const Plan
                                 cudaStream_t s);
 cudaError_t launch_tile_scatter_patches(const int64_t *patch_desc, const float *patches, const int32_t *tile_off,
                                         const int32_t *tile_list, int64_t list_cap, const PlaneParams &pp, float *grid,
-                                        cudaStream_t s, bool det = false);
+                                        cudaStream_t s, bool det = false, int32_t *status = nullptr);
 
 cudaError_t launch_row_r2c(const FFTPlan &p, const float *in, int64_t in_stride, int n_in_cols, int n_rows,
                            float2 *spec, cudaStream_t s, int32_t *status = nullptr);
@@ -196,7 +196,8 @@ cudaError_t launch_digitize(const float *wf, int16_t *adc, int n_wires, int n_ti
 // flags: touched-tile flags of the phase grids seen as one (n_imp * n_wires) x n_ticks grid
 // with pp's tiling (or null)
 cudaError_t launch_raster_phases(int64_t n, const DepoDesc *desc, const PlaneParams &pp, uint32_t event_lo,
-                                 float *grids, uint32_t *flags, cudaStream_t s, unsigned long long *grids64 = nullptr);
+                                 float *grids, uint32_t *flags, cudaStream_t s, unsigned long long *grids64 = nullptr,
+                                 int32_t *status = nullptr);
 
 cudaError_t launch_row_c2r(const FFTPlan &p, const float2 *spec, int n_rows, float *out, int64_t out_stride,
                            int n_out_cols, cudaStream_t s, int32_t *status = nullptr);

@@ -474,7 +474,8 @@ wct_status_t raster_scatter(wct_sim *s, int plane, const wct_depos_t *d, float *
         unsigned long long *g64 = s->grids64[gset] + s->grid_off[plane];
         uint32_t *fl = flags ? flags : s->det_flags + s->flag_off[plane];
         e = launch_raster_chunks(*d, pp, (uint32_t)d->event_id, grid, s->status, st, fl, g64);
-        if (e == cudaSuccess) e = launch_fix_tiles(fl, ps.g.n_wires, ps.g.n_ticks, pp.tile_w, pp.tile_t, g64, grid, st);
+        if (e == cudaSuccess)
+            e = launch_fix_tiles(fl, ps.g.n_wires, ps.g.n_ticks, pp.tile_w, pp.tile_t, g64, grid, st, s->status);
         if (e == cudaSuccess && !flags)
             e = cudaMemsetAsync(fl, 0, sizeof(uint32_t) * tile_flag_words(pp), st);
         s->launches += d->n > 0 ? 2 : 1;
@@ -593,10 +594,10 @@ wct_status_t run_plane_impact(wct_sim *s, int p, const wct_depos_t *d, float *wf
     cudaError_t e = launch_prep(*d, pp, s->desc, nullptr, nullptr, s->status, cs);
     if (e == cudaSuccess)
         e = launch_raster_phases(n, s->desc, pp, (uint32_t)d->event_id, ps.phase_grids, ps.phase_flags, cs,
-                                 ps.phase_grids64);
+                                 ps.phase_grids64, s->status);
     if (e == cudaSuccess && ps.phase_grids64)
         e = launch_fix_tiles(ps.phase_flags, ps.n_phases * nw, nt, pp.tile_w, pp.tile_t, ps.phase_grids64,
-                             ps.phase_grids, cs);
+                             ps.phase_grids, cs, s->status);
     if (e != cudaSuccess) return cuda_fail(s, e, "phase raster");
     s->launches += (n > 0 ? 2 : 0) + (ps.phase_grids64 ? 1 : 0);
     mark(s, slot, 2, cs);
@@ -730,9 +731,9 @@ wct_status_t wct_sim_create(const wct_plane_t *planes, int n_planes, const wct_r
     if (st == WCT_OK) st = dev_alloc(s, (void **)&s->tile_off, sizeof(int32_t) * (max_tiles + 1));
     if (st == WCT_OK) st = dev_alloc(s, (void **)&s->tile_cursor, sizeof(int32_t) * (max_tiles + 1));
     if (st == WCT_OK) st = dev_alloc(s, (void **)&s->scan32, sizeof(int32_t) * scan_tmp_elems(max_tiles + 1));
-    if (st == WCT_OK) st = dev_alloc(s, (void **)&s->status, sizeof(int32_t));
+    if (st == WCT_OK) st = dev_alloc(s, (void **)&s->status, 4 * sizeof(int32_t));   // code + bounds record
     if (st == WCT_OK) {
-        cudaError_t e = cudaMemset(s->status, 0, sizeof(int32_t));
+        cudaError_t e = cudaMemset(s->status, 0, 4 * sizeof(int32_t));
         if (e != cudaSuccess) st = cuda_fail(s, e, "status init");
     }
     // Response spectra: pad each response to 21 centred rows, real-FFT the rows along ticks
@@ -925,7 +926,8 @@ wct_status_t wct_sim_scatter(wct_sim_t *s, int plane, const wct_depos_t *d, cons
         e = launch_fill_patches(d->n, patch_desc, pp, s->tile_off, s->tile_cursor, s->tile_list, s->list_cap,
                                 s->status, cs);
     if (e == cudaSuccess)
-        e = launch_tile_scatter_patches(patch_desc, patches, s->tile_off, s->tile_list, s->list_cap, pp, grid, cs, s->det);
+        e = launch_tile_scatter_patches(patch_desc, patches, s->tile_off, s->tile_list, s->list_cap, pp, grid, cs, s->det,
+                                        s->status);
     if (e != cudaSuccess) return cuda_fail(s, e, "scatter patches");
     s->launches += 4 + (d->n > 0 ? 2 : 0);
     return WCT_OK;
@@ -1046,7 +1048,8 @@ wct_status_t enqueue_batch(wct_sim *s, const wct_depos_t *events, int n_events, 
             for (int i = 0; s->det && i < tab.n_items; ++i) {
                 const BatchItem &b = tab.item[i];
                 const PlaneParams &pp = tab.plane[b.plane];
-                err = launch_fix_tiles(b.flags, pp.n_wires, pp.n_ticks, pp.tile_w, pp.tile_t, b.grid64, b.grid, rs);
+                err = launch_fix_tiles(b.flags, pp.n_wires, pp.n_ticks, pp.tile_w, pp.tile_t, b.grid64, b.grid, rs,
+                                       s->status);
                 if (err != cudaSuccess) return cuda_fail(s, err, "fixed-point grid");
                 s->launches += 1;
             }
@@ -1549,6 +1552,19 @@ wct_status_t wct_sim_selftest_wait(wct_sim_t *s, int64_t limit_cycles, void *str
     cudaError_t e = launch_wait_selftest((long long)limit_cycles, s->status, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "wait self-test");
     return WCT_OK;
+}
+
+wct_status_t wct_debug_bounds(wct_sim_t *s, int64_t *out) {
+    if (!s || !out) return WCT_EINVAL;
+    int32_t rec[3] = {0, 0, 0};
+    const cudaError_t e = cudaMemcpy(rec, s->status + 1, sizeof(rec), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(s, e, "bounds record");
+    for (int k = 0; k < 3; ++k) out[k] = rec[k];
+#ifdef WCT_BOUNDS_CHECK
+    return WCT_OK;
+#else
+    return WCT_EINVAL;   // not a bounds-checked build: nothing is recorded
+#endif
 }
 
 wct_status_t wct_debug_fail_alloc(int64_t n) {
