@@ -9,7 +9,8 @@ literal quadruple loop for small grids.
 Parity status of each function (what pins it; see tests/test_oracle_*.py):
   windows / weights    pinned: mpmath Gaussian bin integrals, brute-force window sets,
                        hand-computed drift / diffusion values, moments of the patch.
-  rasterize (no fluct) pinned: patch sums to q, outer-product structure, shift invariance.
+  rasterize (no fluct) pinned: patch sums to q, outer-product structure, shift invariance;
+                       hypothesis-drawn edge cases (bin edges, sigma = 0, off-grid depos).
   rasterize (fluct)    pinned statistically: per-bin mean / variance of the multinomial,
                        large-q limit; the Philox4x32-10 stream by the published Random123
                        known-answer vectors (tests/golden).
