@@ -182,7 +182,7 @@ def max_over_ranks(value: float, world: int, device=None) -> float:
     return float(t.item())
 
 
-def oracle_sample(wl, n_sample=ORACLE_SAMPLE_DEPOS, seed_offset=0):
+def oracle_sample(wl, n_sample=ORACLE_SAMPLE_DEPOS, seed_offset=0, threads=None):
     """Time the FP64 oracle on a bounded sample of one event: the first n_sample depos
     rasterized + scattered (C, 1 thread) and the full-grid FFT convolution (scipy, all cores).
     Returns (estimated seconds for the whole event, threads): the raster part scales with the
@@ -191,7 +191,7 @@ def oracle_sample(wl, n_sample=ORACLE_SAMPLE_DEPOS, seed_offset=0):
     d = wl.depos(seed=wl.seed + seed_offset).subset(slice(0, n_sample))
     plane = wl.planes[0]
     resp = wl.responses()[0]
-    threads = os.cpu_count() or 1
+    threads = threads or os.cpu_count() or 1
     t0 = time.perf_counter()
     pt = oracle.rasterize(d, plane, wl.diffusion)
     grid = oracle.scatter(pt, plane)
@@ -724,7 +724,9 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t, threads = oracle_sample(wl)
+        t1, _ = oracle_sample(wl, threads=1)
         cpu = {"value": wl.n_depos / t, "unit": "depos/s", "cores": threads, "kind": "oracle",
+               "value_one_thread": wl.n_depos / t1,
                "sample": f"one event: {ORACLE_SAMPLE_DEPOS} of its {wl.n_depos} depos rasterized + scattered "
                          f"(C FP64, 1 thread; time scaled to the whole event) + the full-grid FFT convolution "
                          f"(scipy FP64, {threads} threads), one run"}
