@@ -90,3 +90,11 @@ def test_argument_errors_return_before_cuda_work(lib):
     assert lib.wct_sim_sync(None, None) == E
     assert lib.wct_sim_destroy(None) == E
     assert lib.wct_philox4x32_10(None, 0, -1, None, None) == E
+
+
+def test_debug_entry_points_without_a_gpu(lib):
+    import ctypes
+    assert lib.wct_debug_fail_alloc(3) == 0          # arms without device work
+    assert lib.wct_debug_fail_alloc(-1) == 0         # disarms
+    rec = (ctypes.c_int64 * 3)()
+    assert lib.wct_debug_bounds(None, rec) == 1      # WCT_EINVAL: no handle
