@@ -429,7 +429,7 @@ def measure_scan_free(reps=5):
     d = wl.depos()
     dd = pkg.DeviceDepos.from_host(d)
     sim = pkg.Simulator(wl.planes, wl.responses(), wl.diffusion)
-    slot = pkg.patch_slot_bins(pl, wl.diffusion, float(d.x.max()))
+    slot = sim.patch_slot_bins(0, float(d.x.max()))
     desc, patches = sim.rasterize(0, dd)
     total = patches.numel()
     desc_f, patches_f = sim.rasterize_fixed(0, dd, slot)

@@ -170,6 +170,17 @@ wct_status_t wct_sim_rasterize(wct_sim_t *sim, int plane, const wct_depos_t *dep
 wct_status_t wct_sim_rasterize_fixed(wct_sim_t *sim, int plane, const wct_depos_t *depos, float *patches,
                                      int64_t slot_bins, int64_t *patch_desc, void *stream);
 
+/* The fixed patch slot of wct_sim_rasterize_fixed for depos that drift at most x_max_mm: the
+ * bins of the largest +-nsigma window such a depo can have on `plane` (§2 item 1's patch,
+ * §3.3's fixed slot).  The widths grow with the drift distance, sigma = sqrt(2 D x / v), so the
+ * widest windows are those at x_max; per axis the window rule (bins overlapping
+ * [mu - n sigma, mu + n sigma]) gives at most floor(2 n sigma) + 2 bins (1 for a point charge),
+ * capped at the largest valid window (WCT_MAX_WINDOW_TICKS x WCT_MAX_WINDOW_IMPACTS).
+ * *slot_bins (HOST int64) receives the product of the two extents.  Host computation in FP64
+ * with the rasterizer's own expressions; no device work.  WCT_EINVAL for a NULL output or a
+ * negative / non-finite x_max_mm. */
+wct_status_t wct_sim_patch_slot_bins(wct_sim_t *sim, int plane, double x_max_mm, int64_t *slot_bins);
+
 /*
  * Scatter-add onto the plane grid (§2 step 2).  grid: DEVICE float32 [n_wires][n_ticks],
  * fully overwritten (no need to clear it).  With patches == NULL the patches are computed
@@ -198,7 +209,10 @@ wct_status_t wct_sim_run_event(wct_sim_t *sim, const wct_depos_t *depos, float *
  * all its planes rasterized and scattered by one launch on a library stream, and each grid
  * is then convolved in place on a second library stream, so the rasterize of event e + 1
  * overlaps the convolution of event e; both streams are ordered after earlier work on
- * `stream`, and `stream` waits for both before later work.  When a call repeats an earlier call's pointers, depo counts
+ * `stream`, and `stream` waits for both before later work.  The two library streams are
+ * created at the first call: the rasterize stream with the priority of that call's `stream`,
+ * the convolution stream one step higher (so a caller ranks one handle's batches above
+ * another's by the priority of the stream it passes first).  When a call repeats an earlier call's pointers, depo counts
  * and event ids, the sequence is recorded as a CUDA graph, and later repeats replay it (up
  * to 8 graphs are kept per handle); the depo values themselves may change between replays.  Results equal
  * those of wct_sim_run_event for each event. */
@@ -368,15 +382,34 @@ wct_status_t wct_philox4x32_10(const uint32_t *ctr, uint64_t seed, int64_t n, ui
  * on every GPU that loads the library and held until the process exits.  Sizes whose
  * spectra and tables do not fit in it (roughly 2 * n_wires * (fft_length/2 + 2) * 8 bytes
  * plus the response spectrum and twiddle tables) are rejected with WCT_EINVAL before any
- * launch.  The first call on a device looks up the array's device address (with that device
- * current); make that first call before any stream capture.  Every call shares the one
- * array and leaves its contents behind: calls that overlap on the GPU (other streams, other
- * host threads) race with each other and must be serialised by the caller.
- * Returns WCT_OK, WCT_EINVAL (arguments, or too large) or WCT_ECUDA.
+ * launch.  The first call on a device looks up the array's device address and clears its
+ * status word (with that device current, synchronously); make that first call before any
+ * stream capture.  Every call shares the one array and leaves its contents behind: calls that
+ * overlap on the GPU (other streams, other host threads) race with each other and must be
+ * serialised by the caller.
+ * Device-side errors: the kernels' bounded waits (a bulk copy that never lands) record
+ * WCT_ETIMEOUT in a status word at the head of the array instead of aborting; it stays set,
+ * across calls, until wct_convolve_static_status reads it.  Returns WCT_OK, WCT_EINVAL
+ * (arguments, or too large) or WCT_ECUDA (a launch failed); the launches are asynchronous, so
+ * WCT_OK means "enqueued": read wct_convolve_static_status before trusting the waveform.
  */
 #define WCT_CONVOLVE_STATIC_SCRATCH_BYTES (16u << 20)
 wct_status_t wct_convolve_static(const float *grid, int32_t n_wires, int32_t n_ticks, const float *response,
                                  int32_t n_wires_resp, int32_t n_ticks_resp, float *waveform, void *stream);
+
+/* Status of the wct_convolve_static calls on the current device since the last read:
+ * synchronises `stream` (the stream of those calls), then returns and clears the status word
+ * of the fixed array: WCT_OK, WCT_ETIMEOUT (a bounded wait gave up: that call's waveform is
+ * incomplete) or WCT_EDEVICE; WCT_ECUDA if the synchronisation or the read failed.  Allocates
+ * nothing.  (The paper has no counterpart.) */
+wct_status_t wct_convolve_static_status(void *stream);
+
+/* Self-test of that error path: one kernel whose bounded wait on a shared-memory barrier can
+ * never complete gives up after limit_cycles SM clocks and records WCT_ETIMEOUT in the fixed
+ * array's status word, as the convolution's copy-fed kernels do when a bulk copy never lands;
+ * wct_convolve_static_status then returns WCT_ETIMEOUT and the context stays usable.
+ * Allocates nothing.  (The paper has no counterpart.) */
+wct_status_t wct_convolve_static_selftest_wait(int64_t limit_cycles, void *stream);
 
 /*
  * A field response (input of the detector response of §2 step 3, which the paper takes as

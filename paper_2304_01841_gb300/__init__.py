@@ -151,6 +151,13 @@ class Simulator:
                                                       _ptr(desc), _stream_handle(stream)))
         return desc[: depos.n], patches
 
+    def patch_slot_bins(self, plane: int, x_max_mm: float) -> int:
+        """wct_sim_patch_slot_bins: the fixed slot (bins) of rasterize_fixed for depos that drift
+        at most x_max_mm on this plane."""
+        out = ctypes.c_int64()
+        self._check(self._lib.wct_sim_patch_slot_bins(self._h, plane, float(x_max_mm), ctypes.byref(out)))
+        return int(out.value)
+
     def scatter(self, plane: int, depos: DeviceDepos, patches=None, patch_desc=None, out=None, stream=None):
         """wct_sim_scatter: fused (patches None) or from given patches; returns the grid."""
         grid = self._grid(plane, out)
@@ -312,19 +319,6 @@ def philox4x32_10(ctr, seed: int, stream=None):
     if rc != 0:
         raise WctError(rc, "wct_philox4x32_10 failed")
     return out
-
-
-def patch_slot_bins(plane, diffusion, x_max_mm: float) -> int:
-    """Bins of the largest window a depo drifting at most x_max_mm can have (the fixed slot of
-    the scan-free rasterize): per axis floor(2 n sigma_max / bin) + 2 bins, with sigma from the
-    drift / diffusion relations of the window (sigma_L,T = sqrt(2 D t_d), t_d = x / v)."""
-    import math
-    td = x_max_mm / diffusion.v_drift_mm_us
-    s_t = math.sqrt(2.0 * diffusion.DL_cm2_s * 1e-4 * td) / diffusion.v_drift_mm_us / plane.tick_us
-    s_p = math.sqrt(2.0 * diffusion.DT_cm2_s * 1e-4 * td) / (plane.pitch_mm / plane.n_impact_per_pitch)
-    nt = int(math.floor(2.0 * diffusion.nsigma * s_t)) + 2
-    n_p = int(math.floor(2.0 * diffusion.nsigma * s_p)) + 2
-    return nt * n_p
 
 
 # --------------------------------------------------------------------------------------------

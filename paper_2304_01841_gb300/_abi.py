@@ -70,6 +70,7 @@ EXPORTS = {
                            ctypes.POINTER(c_i64), c_vp], ctypes.c_int),
     "wct_sim_rasterize_fixed": ([c_vp, ctypes.c_int, ctypes.POINTER(wct_depos_t), c_vp, c_i64, c_vp, c_vp],
                                 ctypes.c_int),
+    "wct_sim_patch_slot_bins": ([c_vp, ctypes.c_int, c_dbl, ctypes.POINTER(c_i64)], ctypes.c_int),
     "wct_sim_scatter": ([c_vp, ctypes.c_int, ctypes.POINTER(wct_depos_t), c_vp, c_vp, c_vp, c_vp], ctypes.c_int),
     "wct_sim_convolve": ([c_vp, ctypes.c_int, c_vp, c_vp, c_vp], ctypes.c_int),
     "wct_sim_run_event": ([c_vp, ctypes.POINTER(wct_depos_t), ctypes.POINTER(c_vp), c_vp], ctypes.c_int),
@@ -92,6 +93,8 @@ EXPORTS = {
     "wct_debug_fail_alloc": ([c_i64], ctypes.c_int),
     "wct_debug_bounds": ([c_vp, ctypes.POINTER(c_i64)], ctypes.c_int),
     "wct_convolve_static": ([c_vp, c_i32, c_i32, c_vp, c_i32, c_i32, c_vp, c_vp], ctypes.c_int),
+    "wct_convolve_static_status": ([c_vp], ctypes.c_int),
+    "wct_convolve_static_selftest_wait": ([c_i64, c_vp], ctypes.c_int),
     "wct_response_from_field": ([ctypes.POINTER(wct_field_response_t), c_vp, c_i32, c_dbl, c_i32, c_dbl, c_i32,
                                  c_i32, c_vp, c_vp], ctypes.c_int),
 }

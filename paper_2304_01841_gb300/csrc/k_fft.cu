@@ -20,6 +20,7 @@
 
 #include <algorithm>
 #include <initializer_list>
+#include <mutex>
 
 namespace wct {
 
@@ -1038,6 +1039,7 @@ k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, in
                  int n_phases, int64_t s_phase_stride, int64_t r_phase_stride) {
     __shared__ __align__(16) float2 ring[kRingGroups * kGroupRows][kStageFB];
     __shared__ uint64_t full[kRingGroups], empty[kRingGroups];
+    __shared__ int s_issued, s_prod_done;               // groups the producer issued; it has stopped
     const int tid = threadIdx.x;
     const int f0 = blockIdx.x * kStageFB;
     const int nf = min(kStageFB, Fu - f0);             // even (Fu even, f0 multiple of 128)
@@ -1054,6 +1056,8 @@ k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, in
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], kStageFB);
         }
+        s_issued = 0;
+        s_prod_done = 0;
         fence_mbar_init();
     }
     __syncthreads();
@@ -1076,7 +1080,10 @@ k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, in
                     if (WCT_IDX_OK(status, w0 - KC + m_lo + r, n_wires))
                         bulk_g2s(ring[gs * kGroupRows + (r - r0)], Sp + (size_t)(w0 - KC + m_lo + r) * Fs + f0,
                                  row_bytes, &full[gs]);
+                *(volatile int *)&s_issued = gg + 1;
             }
+            __threadfence_block();
+            *(volatile int *)&s_prod_done = 1;
         }
         return;
     }
@@ -1092,6 +1099,7 @@ k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, in
     constexpr int kWin = kOutBlock + 2 * KC;
     float2 rr[KW], ri[KW];                             // (re, re) and (im, im) of each tap
     bool ok = true;
+    int g_fail = 0;                                    // first group whose wait ran out (if !ok)
     int gbase = 0;                                     // ring sequence number of the phase's group 0
     auto load_row = [&](int m) -> float2 {
         float2 x = make_float2(0.f, 0.f);
@@ -1102,10 +1110,13 @@ k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, in
             if (in_g == 0 && ok && !mbar_wait(&full[gs], (g / kRingGroups) & 1)) {
                 set_status(status, ST_ETIMEOUT);
                 ok = false;
+                g_fail = g;
             }
             if (ok && live && WCT_IDX_OK(status, gs * kGroupRows + in_g, kRingGroups * kGroupRows))
                 x = ring[gs * kGroupRows + in_g][tid];
-            if (in_g == kGroupRows - 1 || idx == n_rows - 1)
+            // after a timeout this thread releases no slot: a slot whose copy may still land is
+            // never handed to the producer again (it then gives up on its own bounded wait)
+            if (ok && (in_g == kGroupRows - 1 || idx == n_rows - 1))
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[gs])) : "memory");
         }
         return x;
@@ -1156,9 +1167,15 @@ k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, in
     }
     }
     if (!ok && tid == 0) {
-        // after a timeout, wait (bounded) for the last group this CTA issued before leaving
-        const int g = n_phases * n_groups - 1;
-        mbar_wait(&full[g % kRingGroups], (g / kRingGroups) & 1);
+        // after a timeout: once the producer has stopped issuing (bounded), wait (bounded) for
+        // every group it issued from the one that ran out on; they sit in distinct slots (a
+        // slot is reissued only after this thread released it), so no copy lands in the
+        // shared memory of a CTA that has left
+        const long long t0 = clock64();
+        while (!*(volatile int *)&s_prod_done && clock64() - t0 < kWaitCycles) {
+        }
+        const int issued = *(volatile int *)&s_issued;
+        for (int g = g_fail; g < issued; ++g) mbar_wait(&full[g % kRingGroups], (g / kRingGroups) & 1);
     }
 }
 
@@ -1224,6 +1241,31 @@ size_t device_smem_per_sm() {
 }
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+// CTAs of k_wire_stage_tma resident on the whole current device (occupancy x SMs), computed
+// once per device under a lock and cached.
+constexpr int kMaxDevicesFft = 64;
+std::mutex g_resident_mu;
+int g_resident[kMaxDevicesFft] = {};
+
+int wire_stage_resident() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevicesFft) {
+        cudaGetLastError();
+        return std::max(device_sms(), 1);
+    }
+    std::lock_guard<std::mutex> lock(g_resident_mu);
+    if (g_resident[dev] == 0) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wire_stage_tma, kStageFB + 32, 0) != cudaSuccess ||
+            per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+        g_resident[dev] = per_sm * std::max(device_sms(), 1);
+    }
+    return g_resident[dev];
+}
 
 // Row-transform schedule (FFTPlan::row_schedule): 0 = register-staged small CTAs (compiled
 // lengths), 1 = persistent bulk-copy CTAs, one per SM, 2 = persistent paired CTAs, two per SM
@@ -1423,14 +1465,7 @@ cudaError_t launch_wire_stage(const FFTPlan &p, const float2 *spec, const float2
         // and the launch takes ceil(CTAs / resident CTAs) waves, so pick the wpc that
         // minimises waves x (wpc + 20): a last, nearly empty wave costs a full CTA time.
         const int fb = (p.Fu + kStageFB - 1) / kStageFB;
-        static int resident = 0;
-        if (resident == 0) {
-            int per_sm = 0;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wire_stage_tma, kStageFB + 32, 0) != cudaSuccess ||
-                per_sm < 1)
-                per_sm = 1;
-            resident = per_sm * std::max(device_sms(), 1);
-        }
+        const int resident = wire_stage_resident();
         int wpc = kStageWiresMax;
         int64_t best = INT64_MAX;
         for (int c = 16; c <= kStageWiresMax; ++c) {

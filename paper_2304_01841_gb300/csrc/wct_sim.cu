@@ -906,6 +906,28 @@ wct_status_t wct_sim_rasterize_fixed(wct_sim_t *s, int plane, const wct_depos_t 
     return WCT_OK;
 }
 
+wct_status_t wct_sim_patch_slot_bins(wct_sim_t *s, int plane, double x_max_mm, int64_t *slot_bins) {
+    wct_status_t st = plane_check(s, plane);
+    if (st) return st;
+    if (!slot_bins) return fail(s, WCT_EINVAL, "slot_bins is NULL");
+    if (!std::isfinite(x_max_mm) || x_max_mm < 0.0) return fail(s, WCT_EINVAL, "x_max_mm must be finite and >= 0");
+    // the widths as depo_window_f64 forms them (sigma grows with the drift distance, so the
+    // widest windows are those at x_max), then the window rule: the bins overlapping
+    // [mu - n sigma, mu + n sigma] number floor(mu + n sigma) - floor(mu - n sigma) + 1, at most
+    // floor(2 n sigma) + 2 over every position mu; a point charge (sigma < 1e-6 bin) takes one bin
+    const PlaneParams &pp = s->planes[plane].pp;
+    const double td = x_max_mm / pp.v;
+    const double s_t = std::sqrt((2.0 * pp.DL) * td) / pp.v / pp.tick;
+    const double s_p = std::sqrt((2.0 * pp.DT) * td) / pp.dp;
+    auto extent = [&](double sg, int64_t cap) -> int64_t {
+        if (sg < 1e-6) return 1;
+        const double e = std::floor(2.0 * (pp.nsigma * sg)) + 2.0;
+        return e < (double)cap ? (int64_t)e : cap;   // a wider window is an invalid depo, never rasterized
+    };
+    *slot_bins = extent(s_t, WCT_MAX_WINDOW_TICKS) * extent(s_p, WCT_MAX_WINDOW_IMPACTS);
+    return WCT_OK;
+}
+
 wct_status_t wct_sim_scatter(wct_sim_t *s, int plane, const wct_depos_t *d, const float *patches,
                              const int64_t *patch_desc, float *grid, void *stream) {
     wct_status_t st = plane_check(s, plane);
@@ -983,14 +1005,21 @@ constexpr size_t kMaxGraphs = 8;
 // of up to kBatchItems pairs, then the convolution of every grid (in place).
 // Library streams and events used to overlap the rasterize of one event with the
 // convolution of the previous one inside run_batch.
-wct_status_t batch_streams(wct_sim *s) {
+wct_status_t batch_streams(wct_sim *s, cudaStream_t caller) {
     if (s->rs_stream) return WCT_OK;
-    // the convolution stream gets the higher priority, so its CTAs go first whenever SMs free
-    // up and the rasterize CTAs fill the remaining room
-    int lo = 0, hi = 0;
+    // the rasterize stream takes the priority of the stream of the first run_batch call and the
+    // convolution stream the next higher one, so the convolution's CTAs go first whenever SMs
+    // free up and the rasterize CTAs fill the remaining room, and a caller can rank one
+    // handle's batches above another's (lower numbers run first)
+    int lo = 0, hi = 0, own = 0;
     cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
-    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->rs_stream, cudaStreamNonBlocking, lo);
-    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->cv_stream, cudaStreamNonBlocking, hi);
+    if (e == cudaSuccess && cudaStreamGetPriority(caller, &own) != cudaSuccess) {
+        cudaGetLastError();
+        own = lo;
+    }
+    own = std::min(std::max(own, hi), lo);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->rs_stream, cudaStreamNonBlocking, own);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->cv_stream, cudaStreamNonBlocking, std::max(hi, own - 1));
     for (int i = 0; e == cudaSuccess && i < kBatchEvents; ++i)
         e = cudaEventCreateWithFlags(&s->bev[i], cudaEventDisableTiming);
     for (int b = 0; e == cudaSuccess && b < 2; ++b) e = cudaEventCreateWithFlags(&s->gev[b], cudaEventDisableTiming);
@@ -1004,7 +1033,7 @@ wct_status_t batch_streams(wct_sim *s) {
 // use different units: the raster is integer / SFU bound, the transforms shared-memory
 // bound).  Both streams fork from and join back into `st`.
 wct_status_t enqueue_batch(wct_sim *s, const wct_depos_t *events, int n_events, float *const *wfs, cudaStream_t st) {
-    wct_status_t r = batch_streams(s);
+    wct_status_t r = batch_streams(s, st);
     if (r) return r;
     const int npl = s->n_planes;
     static thread_local BatchTable tab;   // ~21 KB: kept off the stack
@@ -1589,6 +1618,7 @@ wct_status_t wct_philox4x32_10(const uint32_t *ctr, uint64_t seed, int64_t n, ui
 namespace {
 
 constexpr size_t kStaticElems = (size_t)WCT_CONVOLVE_STATIC_SCRATCH_BYTES / sizeof(float2);
+constexpr size_t kStaticHead = 32;   // float2 = 256 bytes at the head: the status word (+ bounds record)
 constexpr int kMaxDevices = 64;
 __device__ __align__(256) float2 g_convolve_scratch[kStaticElems];
 
@@ -1596,8 +1626,9 @@ std::mutex g_static_mu;
 float2 *g_static_addr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device.  Looked up once per device
-// (with that device current) and cached; the name g_convolve_scratch itself is only a
-// host-side stand-in and must never be passed to a kernel.
+// (with that device current) and cached, and the status word at its head cleared then; the
+// name g_convolve_scratch itself is only a host-side stand-in and must never be passed to a
+// kernel.
 cudaError_t static_scratch(float2 **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1607,6 +1638,9 @@ cudaError_t static_scratch(float2 **out) {
     if (!g_static_addr[dev]) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_convolve_scratch);
+        if (e != cudaSuccess) return e;
+        e = cudaMemset(p, 0, sizeof(float2) * kStaticHead);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
         if (e != cudaSuccess) return e;
         g_static_addr[dev] = static_cast<float2 *>(p);
     }
@@ -1632,14 +1666,17 @@ wct_status_t wct_convolve_static(const float *grid, int32_t n_wires, int32_t n_t
     const size_t n_tw = round_up_256((size_t)p.M), n_rtw = round_up_256((size_t)p.M + 1);
     const size_t n_resp = round_up_256((size_t)KW * p.Fs);
     const size_t n_spec = round_up_256((size_t)n_wires * p.Fs);
-    if (n_tw + n_rtw + n_resp + 2 * n_spec > kStaticElems) return WCT_EINVAL;   // beyond the reserved scratch
+    if (kStaticHead + n_tw + n_rtw + n_resp + 2 * n_spec > kStaticElems) return WCT_EINVAL;   // beyond the scratch
     float2 *base = nullptr;
     if (static_scratch(&base) != cudaSuccess) {
         cudaGetLastError();
         return WCT_ECUDA;
     }
-    p.tw = base;
-    p.rtw = base + n_tw;
+    // the kernels' bounded waits record a timeout here (it stays set until read by
+    // wct_convolve_static_status)
+    int32_t *status = reinterpret_cast<int32_t *>(base);
+    p.tw = base + kStaticHead;
+    p.rtw = p.tw + n_tw;
     float2 *resp_spec = p.rtw + n_rtw;
     float2 *S = resp_spec + n_resp;
     float2 *T = S + n_spec;
@@ -1648,11 +1685,42 @@ wct_status_t wct_convolve_static(const float *grid, int32_t n_wires, int32_t n_t
     cudaError_t e = launch_make_twiddles(p, cs);
     if (e == cudaSuccess) e = cudaMemsetAsync(resp_spec, 0, sizeof(float2) * (size_t)KW * p.Fs, cs);
     if (e == cudaSuccess)
-        e = launch_row_r2c(p, response, n_ticks_resp, n_ticks_resp, n_wires_resp, resp_spec + (size_t)off * p.Fs, cs);
+        e = launch_row_r2c(p, response, n_ticks_resp, n_ticks_resp, n_wires_resp, resp_spec + (size_t)off * p.Fs, cs,
+                           status);
     if (e == cudaSuccess) e = launch_scale_spectrum(resp_spec, (int64_t)KW * p.Fs, 1.0f / (float)p.M, cs);
-    if (e == cudaSuccess) e = launch_row_r2c(p, grid, n_ticks, n_ticks, n_wires, S, cs);
-    if (e == cudaSuccess) e = launch_wire_stage(p, S, resp_spec, n_wires, T, cs);
-    if (e == cudaSuccess) e = launch_row_c2r(p, T, n_wires, waveform, n_ticks, n_ticks, cs);
+    if (e == cudaSuccess) e = launch_row_r2c(p, grid, n_ticks, n_ticks, n_wires, S, cs, status);
+    if (e == cudaSuccess) e = launch_wire_stage(p, S, resp_spec, n_wires, T, cs, status);
+    if (e == cudaSuccess) e = launch_row_c2r(p, T, n_wires, waveform, n_ticks, n_ticks, cs, status);
+    return e == cudaSuccess ? WCT_OK : WCT_ECUDA;
+}
+
+wct_status_t wct_convolve_static_status(void *stream) {
+    float2 *base = nullptr;
+    if (static_scratch(&base) != cudaSuccess) {
+        cudaGetLastError();
+        return WCT_ECUDA;
+    }
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    int32_t code = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&code, base, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && code != 0) e = cudaMemset(base, 0, sizeof(float2) * kStaticHead);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return WCT_ECUDA;
+    }
+    if (code == ST_ETIMEOUT) return WCT_ETIMEOUT;
+    return code == 0 ? WCT_OK : WCT_EDEVICE;
+}
+
+wct_status_t wct_convolve_static_selftest_wait(int64_t limit_cycles, void *stream) {
+    if (limit_cycles < 0) return WCT_EINVAL;
+    float2 *base = nullptr;
+    if (static_scratch(&base) != cudaSuccess) {
+        cudaGetLastError();
+        return WCT_ECUDA;
+    }
+    const cudaError_t e =
+        launch_wait_selftest((long long)limit_cycles, reinterpret_cast<int32_t *>(base), (cudaStream_t)stream);
     return e == cudaSuccess ? WCT_OK : WCT_ECUDA;
 }
 

@@ -2,12 +2,21 @@
 
 Requests (one event's depos each, in host memory) arrive at any time.  The scheduler keeps
 `n_slots` slots; each slot owns a simulator handle (its own scratch) and a CUDA stream, so
-slots run concurrently on the device.  Whenever a slot is free, the scheduler admits the
-oldest pending requests whose device memory (depo arrays + waveforms) fits the remaining HBM
-budget, up to `max_batch` per slot, copies their depos to the device and launches them as one
-batch (rasterize + scatter and the convolutions, wct_sim_run_batch) on that slot's stream.
-A request that arrives while others are on the GPU is admitted as soon as a slot and memory
-free up.  Latency is submit -> completion observed on the host.
+slots run concurrently on the device.  Whenever a slot is free, the scheduler admits pending
+requests whose device memory (depo arrays + waveforms) fits the remaining HBM budget, copies
+their depos to the device and launches them as one batch (rasterize + scatter and the
+convolutions, wct_sim_run_batch) on that slot's stream.  A request that arrives while others
+are on the GPU is admitted as soon as a slot and memory free up.  Latency is submit ->
+completion observed on the host.
+
+Admission is size aware, so that small events never wait behind a large one:
+  - a request of at least `heavy_depos` depos is heavy: it runs in a batch of its own, on one
+    of the last `heavy_slots` slots, whose streams have the lowest priority;
+  - light requests are batched in arrival order (skipping heavy ones) up to `max_batch`
+    requests and `max_batch_depos` depos per batch, on high-priority streams, so the device's
+    block scheduler runs their kernels ahead of a heavy event's whenever SMs free up;
+  - a heavy slot with no heavy request pending takes a light batch; heavy requests are admitted
+    in arrival order among themselves.
 
 The results of a request do not depend on what it was batched with: the fluctuation stream is
 keyed by (seed, event id, plane, depo index, bin), so each event is the same alone and in a mix
@@ -70,13 +79,14 @@ def pin_depos(d):
 class CudaBackend:
     """Device side of a slot: a simulator handle and a stream."""
 
-    def __init__(self, planes, responses, diffusion, keep_results: bool):
+    def __init__(self, planes, responses, diffusion, keep_results: bool, priority: int = 0):
         import torch
         from . import Simulator
         self.torch = torch
         self.planes = list(planes)
         self.sim = Simulator(planes, responses, diffusion)
-        self.stream = torch.cuda.Stream()
+        # lower numbers run first; the library's own batch streams follow this stream's priority
+        self.stream = torch.cuda.Stream(priority=priority)
         self.keep = keep_results
         self.dev, self.outs, self.host, self.event = [], [], [], None
 
@@ -112,18 +122,31 @@ class CudaBackend:
 
 
 class _Slot:
-    def __init__(self, backend):
+    def __init__(self, backend, heavy: bool):
         self.backend = backend
+        self.heavy = heavy               # runs heavy requests (alone, at low priority)
         self.batch: List[Request] = []
         self.bytes = 0
 
 
 class EventServer:
     def __init__(self, planes, responses, diffusion, n_slots: int = 4, max_batch: int = 8,
-                 hbm_budget_bytes: int = 16 << 30, keep_results: bool = False, backend_factory=None):
+                 hbm_budget_bytes: int = 16 << 30, keep_results: bool = False, backend_factory=None,
+                 heavy_depos: int = 500_000, max_batch_depos: int = 400_000, heavy_slots: Optional[int] = None):
         self.planes = list(planes)
-        make = backend_factory or (lambda: CudaBackend(planes, responses, diffusion, keep_results))
-        self.slots = [_Slot(make()) for _ in range(n_slots)]
+        if heavy_slots is None:
+            heavy_slots = 1 if n_slots > 1 else 0
+        heavy_slots = max(0, min(heavy_slots, n_slots))
+        n_light = n_slots - heavy_slots
+
+        def make(heavy: bool):
+            if backend_factory is not None:
+                return backend_factory()
+            return CudaBackend(planes, responses, diffusion, keep_results, priority=0 if heavy else -2)
+
+        self.slots = [_Slot(make(i >= n_light), i >= n_light) for i in range(n_slots)]
+        self.heavy_depos = int(heavy_depos)
+        self.max_batch_depos = int(max_batch_depos)
         self.max_batch = max_batch
         self.budget = int(hbm_budget_bytes)
         self.in_use = 0
@@ -171,6 +194,48 @@ class EventServer:
     def request_bytes(self, r: Request) -> int:
         return 20 * int(len(r.depos.t0)) + self.plane_bytes
 
+    def is_heavy(self, r: Request) -> bool:
+        return int(len(r.depos.t0)) >= self.heavy_depos
+
+    def _fits(self, need: int, need_total: int, batch) -> bool:
+        # within the budget; a request larger than the whole budget runs alone on an idle device
+        return self.in_use + need_total + need <= self.budget or not (batch or self.in_use > 0)
+
+    def _take(self, slot: "_Slot"):
+        """The batch a free slot launches next (removed from pending; caller holds the lock)."""
+        heavy_slots_exist = any(s.heavy for s in self.slots)
+        if slot.heavy:
+            for r in self.pending:                     # the oldest heavy request, alone
+                if self.is_heavy(r):
+                    need = self.request_bytes(r)
+                    if not self._fits(need, 0, []):
+                        return [], 0                   # wait for memory; light slots carry on
+                    self.pending.remove(r)
+                    return [r], need
+        batch: List[Request] = []
+        need_total = depos = 0
+        for r in list(self.pending):                   # light requests in arrival order
+            if len(batch) >= self.max_batch:
+                break
+            heavy = self.is_heavy(r)
+            if heavy and heavy_slots_exist:
+                continue                               # heavy requests wait for a heavy slot
+            n = int(len(r.depos.t0))
+            if heavy and batch:
+                continue                               # no heavy slots: it still runs alone
+            if batch and depos + n > self.max_batch_depos:
+                break
+            need = self.request_bytes(r)
+            if not self._fits(need, need_total, batch):
+                break                                  # wait for memory to free up
+            self.pending.remove(r)
+            batch.append(r)
+            need_total += need
+            depos += n
+            if heavy:
+                break
+        return batch, need_total
+
     # -- scheduler ---------------------------------------------------------------------------
     def step(self) -> int:
         """One scheduler pass: retire finished slots, admit pending requests into free slots.
@@ -186,17 +251,10 @@ class EventServer:
         for slot in self.slots:
             if slot.batch:
                 continue
-            batch: List[Request] = []
-            need_total = 0
             with self.lock:
-                while self.pending and len(batch) < self.max_batch:
-                    need = self.request_bytes(self.pending[0])
-                    if self.in_use + need_total + need > self.budget and (batch or self.in_use > 0):
-                        break                       # wait for memory to free up
-                    need_total += need
-                    batch.append(self.pending.popleft())
+                batch, need_total = self._take(slot) if self.pending else ([], 0)
             if not batch:
-                break
+                continue
             now = time.perf_counter()
             for r in batch:
                 r.t_admit = now

@@ -52,10 +52,23 @@ for sched in (-1, 6, 0, 1):
     desc, patches = sim.rasterize(0, dd)
     grid = sim.scatter(0, dd, patches=patches, patch_desc=desc)
     fused = sim.scatter(0, dd)
+    slot = sim.patch_slot_bins(0, float(d.x.max()))
+    desc_f, patches_f = sim.rasterize_fixed(0, dd, slot)
+    grid_f = sim.scatter(0, dd, patches=patches_f, patch_desc=desc_f)
     wf = sim.run_event(dd)[0]
     clean(sim)
     ref = oracle.scatter(oracle.rasterize(d, tiny.planes[0], synth.Diffusion(fluctuate=True, seed=4)), tiny.planes[0])
     assert max_rel_bin(to_np(grid), ref) <= BIN_TOL and max_rel_bin(to_np(fused), ref) <= BIN_TOL
+    assert max_rel_bin(to_np(grid_f), ref) <= BIN_TOL
+    # an undersized slot: the skipped depos are reported (WCT_EINVAL), no index goes out of range
+    desc_x, patches_x = sim.rasterize_fixed(0, dd, 24)
+    sim.scatter(0, dd, patches=patches_x, patch_desc=desc_x)
+    try:
+        sim.sync()
+        raise AssertionError("undersized slots were not reported")
+    except g.WctError as e:
+        assert e.code == 1
+    assert lib.wct_debug_bounds(sim._h, rec) == 0 and list(rec) == [0, 0, 0], list(rec)
     sim.close()
 # impact mode, both accumulation modes
 pl = tiny.planes[0]

@@ -239,9 +239,11 @@ def test_library_grids_return_to_zero(schedule):
         assert np.abs(b1[p] - b0[p]).max() <= 1e-5 * np.abs(b0[p]).max()
 
 
-def test_scan_free_fixed_slots_match_the_scanned_patches():
-    # the scan-free rasterize writes the same patches, each at its fixed slot i * slot_bins,
-    # and scattering them gives the same grid; an undersized slot skips and reports depos
+def test_scan_free_fixed_slots_match_the_oracle():
+    # the scan-free rasterize (the paper's OpenMP port drops the prefix sum for a fixed slot per
+    # depo): every depo's patch at i * slot_bins, element by element against the FP64 oracle with
+    # fluctuation on; the same bits as the scanned patches; the same grid when scattered; an
+    # undersized slot skips (and reports) exactly the depos whose oracle window exceeds it
     import paper_2304_01841_gb300 as g
     wl = synth.workload("uboone_plane")
     pl = wl.planes[0]
@@ -249,29 +251,65 @@ def test_scan_free_fixed_slots_match_the_scanned_patches():
     diff = synth.Diffusion(fluctuate=True, seed=21)
     sim = make_sim([pl], [synth.make_response(pl.response_kind)], diff)
     dd = _dev(d)
-    slot = g.patch_slot_bins(pl, diff, float(d.x.max()))
-    desc_s, patches_s = sim.rasterize(0, dd)
+    slot = sim.patch_slot_bins(0, float(d.x.max()))
     desc_f, patches_f = sim.rasterize_fixed(0, dd, slot)
+    desc_s, patches_s = sim.rasterize(0, dd)
     sim.sync()
-    ds, df = to_np(desc_s), to_np(desc_f)
-    assert np.array_equal(ds[:, 1:], df[:, 1:])
+    ref = oracle.rasterize(d, pl, diff)
+    df, ds = to_np(desc_f), to_np(desc_s)
+    assert np.array_equal(df[:, 1:], ref.desc[:, 1:])            # windows bit-exact
     assert np.array_equal(df[:, 0], np.arange(d.n) * slot)
-    ps, pf = to_np(patches_s), to_np(patches_f)
+    nb = ref.desc[:, 3] * ref.desc[:, 4]
+    assert nb.max() <= slot                                      # the slot holds every window
+    pf, ps = to_np(patches_f), to_np(patches_s)
+    got = np.concatenate([pf[i * slot: i * slot + nb[i]] for i in range(d.n)])
+    want = np.concatenate([ref.values[ref.desc[i, 0]: ref.desc[i, 0] + nb[i]] for i in range(d.n)])
+    assert got.size == ref.values.size
+    err = max_rel_bin(got, want)
+    assert err <= BIN_TOL, err
     for i in range(0, d.n, 997):
-        nb = int(ds[i, 3] * ds[i, 4])
-        assert np.array_equal(ps[ds[i, 0]: ds[i, 0] + nb], pf[df[i, 0]: df[i, 0] + nb])
-    g_s = to_np(sim.scatter(0, dd, patches_s, desc_s))
+        assert np.array_equal(ps[ds[i, 0]: ds[i, 0] + nb[i]], pf[i * slot: i * slot + nb[i]])
     g_f = to_np(sim.scatter(0, dd, patches_f, desc_f))
     sim.sync()
-    assert np.abs(g_s - g_f).max() <= 1e-5 * np.abs(g_s).max()
+    assert max_rel_bin(g_f, oracle.scatter(ref, pl)) <= BIN_TOL
     small = 40                                          # most windows hold more bins
-    desc_x, _ = sim.rasterize_fixed(0, dd, small)
+    desc_x, patches_x = sim.rasterize_fixed(0, dd, small)
     with pytest.raises(g.WctError) as ei:
         sim.sync()
     assert ei.value.code == 1
-    dx = to_np(desc_x)
-    over = ds[:, 3] * ds[:, 4] > small
-    assert over.any() and np.all(dx[over, 3] == 0) and np.array_equal(dx[~over, 3:], ds[~over, 3:])
+    dx, px = to_np(desc_x), to_np(patches_x)
+    over = nb > small
+    assert over.any() and (~over).any()
+    assert np.all(dx[over, 3:] == 0) and np.array_equal(dx[~over, 1:], ref.desc[~over, 1:])
+    keep = np.flatnonzero(~over)
+    got = np.concatenate([px[i * small: i * small + nb[i]] for i in keep])
+    want = np.concatenate([ref.values[ref.desc[i, 0]: ref.desc[i, 0] + nb[i]] for i in keep])
+    assert max_rel_bin(got, want) <= BIN_TOL
+
+
+def test_patch_slot_bins_is_the_largest_window():
+    # the slot from the library's window rule: never smaller than a window at the maximum drift,
+    # and reached there (depos at x_max swept across a bin in time and pitch)
+    wl = synth.workload("uboone_plane")
+    pl = wl.planes[0]
+    diff = synth.Diffusion(fluctuate=False, seed=3)
+    sim = make_sim([pl], [synth.make_response(pl.response_kind)], diff)
+    x_max = 3000.0
+    n = 4096
+    rng = np.random.default_rng(5)
+    u = rng.random(n)
+    d = synth.Depos(np.full(n, 0.0, np.float32) + (rng.random(n) * 0.5).astype(np.float32),
+                    np.full(n, x_max, np.float32), np.zeros(n, np.float32),
+                    (u * 0.3 - 0.15).astype(np.float32), np.full(n, 1000.0, np.float32))
+    ref = oracle.rasterize(d, pl, diff)
+    nt, np_ = ref.desc[:, 3].max(), ref.desc[:, 4].max()
+    assert sim.patch_slot_bins(0, x_max) == nt * np_
+    assert sim.patch_slot_bins(0, 0.0) == 1                          # point charges: one bin
+    assert sim.patch_slot_bins(0, 10.0) <= sim.patch_slot_bins(0, x_max)
+    import paper_2304_01841_gb300 as g
+    for bad in (-1.0, float("nan"), float("inf")):
+        with pytest.raises(g.WctError):
+            sim.patch_slot_bins(0, bad)
 
 
 def test_empty_event_gives_zero_waveforms():

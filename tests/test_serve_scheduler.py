@@ -134,3 +134,44 @@ def test_failed_batches_complete_with_their_error_and_the_server_carries_on():
         assert all("injected" in str(reqs[i].error) for i in failed)
         assert sorted(r.rid for r in srv.completed) == list(range(8))
         assert srv.in_use == 0
+
+
+def test_small_requests_never_wait_behind_a_heavy_one():
+    # a 1M-depo request at the head of the queue runs alone on the heavy slot; the small
+    # requests behind it are batched on the other slots without waiting for it
+    srv = _server(passes=6, n_slots=3, max_batch=8, hbm_budget_bytes=1 << 40)
+    big = srv.submit(_depos(1_000_000))
+    small = [srv.submit(_depos(2000)) for _ in range(5)]
+    srv.step()
+    launches = [b for kind, _, b in FakeBackend.log if kind == "launch"]
+    assert (big.rid,) in launches                                   # alone
+    assert any(set(b) == {r.rid for r in small} for b in launches)  # all small ones, same pass
+    assert all(r.t_admit > 0 for r in small)                        # admitted while the big one runs
+    srv.drain()
+    assert all(r.done.is_set() for r in [big] + small)
+
+
+def test_light_batches_are_capped_in_depos_and_heavy_ones_queue_in_order():
+    srv = _server(passes=2, n_slots=2, max_batch=8, hbm_budget_bytes=1 << 40, max_batch_depos=10_000,
+                  heavy_depos=500_000)
+    heavy = [srv.submit(_depos(600_000)) for _ in range(2)]
+    light = [srv.submit(_depos(4000)) for _ in range(5)]
+    srv.drain()
+    launches = [b for kind, _, b in FakeBackend.log if kind == "launch"]
+    light_ids = {r.rid for r in light}
+    for b in launches:
+        if set(b) & light_ids:
+            assert set(b) <= light_ids and 4000 * len(b) <= 10_000       # depo cap, never mixed
+    heavy_order = [b[0] for b in launches if b[0] in {r.rid for r in heavy}]
+    assert heavy_order == [r.rid for r in heavy] and all(len(b) == 1 for b in launches if b[0] in heavy_order)
+
+
+def test_single_slot_still_runs_heavy_requests_alone():
+    srv = _server(passes=2, n_slots=1, max_batch=8, hbm_budget_bytes=1 << 40)
+    a = srv.submit(_depos(10))
+    h = srv.submit(_depos(2_000_000))
+    b = srv.submit(_depos(10))
+    srv.drain()
+    launches = [b_ for kind, _, b_ in FakeBackend.log if kind == "launch"]
+    assert (h.rid,) in launches and all(len(x) == 1 or h.rid not in x for x in launches)
+    assert sorted(r.rid for r in srv.completed) == [a.rid, h.rid, b.rid]

@@ -1,11 +1,13 @@
-"""The allocation-free convolution entry point, wct_convolve_static, against wct_sim_convolve.
+"""The allocation-free convolution entry point, wct_convolve_static, against the FP64 oracle
+and against wct_sim_convolve.
 
 wct_convolve_static is for callers that may not allocate device memory when they call the
 library (a host framework that owns all device memory through its own pool, or a path that
 cannot afford cudaMalloc's implicit synchronisation).  It works from a fixed scratch array
 the library reserves when it is loaded, so this test checks that two calls in a row, which
-share and reuse that array, each give the result of the handle-based convolution, and that
-sizes beyond the reserved scratch are refused before any launch.
+share and reuse that array, each give the oracle's convolution (and the handle-based one's),
+that a timed-out device wait is reported through wct_convolve_static_status, and that sizes
+beyond the reserved scratch are refused before any launch.
 
 This file is collected last on purpose: it must pass after the other tests and on its own.
 """
@@ -14,6 +16,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 import synth
 from helpers import WAVE_RTOL, make_sim, rel_l2, to_np
 
@@ -48,7 +51,10 @@ def test_static_convolve_matches_handle_twice_in_a_row(lib):
         want = sim.convolve(0, g)
         got = torch.full_like(g, float("nan"))
         assert _static_convolve(lib, g, resp_dev, got) == 0
+        assert lib.wct_convolve_static_status(torch.cuda.current_stream().cuda_stream) == 0
         sim.sync()
+        ref = oracle.convolve_fft(to_np(g).astype(np.float64), resp)
+        assert rel_l2(to_np(got), ref) <= WAVE_RTOL, call
         assert rel_l2(to_np(got), to_np(want)) <= WAVE_RTOL, call
 
 
@@ -61,8 +67,29 @@ def test_static_convolve_narrow_response_in_place(lib):
     want = sim.convolve(0, g)
     buf = g.clone()
     assert _static_convolve(lib, buf, torch.from_numpy(resp).cuda(), buf) == 0
-    torch.cuda.synchronize()
+    assert lib.wct_convolve_static_status(torch.cuda.current_stream().cuda_stream) == 0
+    ref = oracle.convolve_fft(to_np(g).astype(np.float64), resp)
+    assert rel_l2(to_np(buf), ref) <= WAVE_RTOL
     assert rel_l2(to_np(buf), to_np(want)) <= WAVE_RTOL
+
+
+def test_static_convolve_reports_a_timed_out_wait(lib):
+    # a bounded wait that can never complete (nothing arrives on its barrier) gives up after a
+    # short limit and records WCT_ETIMEOUT in the fixed array's status word, as the convolution's
+    # copy-fed kernels do when a bulk copy never lands; the status call reports it once, the
+    # context stays usable and the next convolution is exact again
+    stream = torch.cuda.current_stream().cuda_stream
+    assert lib.wct_convolve_static_status(stream) == 0
+    assert lib.wct_convolve_static_selftest_wait(200_000, stream) == 0
+    assert lib.wct_convolve_static_status(stream) == 4           # WCT_ETIMEOUT
+    assert lib.wct_convolve_static_status(stream) == 0           # read and cleared
+    resp = synth.make_response("unipolar")
+    g = torch.from_numpy(np.random.default_rng(11).normal(size=(48, 700)).astype(np.float32)).cuda()
+    out = torch.empty_like(g)
+    assert _static_convolve(lib, g, torch.from_numpy(resp).cuda(), out) == 0
+    assert lib.wct_convolve_static_status(stream) == 0
+    assert rel_l2(to_np(out), oracle.convolve_fft(to_np(g).astype(np.float64), resp)) <= WAVE_RTOL
+    assert lib.wct_convolve_static_selftest_wait(-1, stream) == 1
 
 
 def test_static_convolve_rejects_sizes_beyond_its_scratch(lib):
