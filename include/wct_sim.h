@@ -21,7 +21,9 @@
  *    in a device status word and returned by wct_sim_sync() (or the next synchronising
  *    call).  The library never aborts, traps or exits; wct_sim_last_error() describes the
  *    most recent failure.
- *  - A handle is not thread-safe: use one handle per host thread or lock around it.
+ *  - A handle is not thread-safe: use one handle per host thread or lock around it.  Its
+ *    calls share the handle's device scratch, so enqueue them on one stream (or order the
+ *    streams); wct_sim_run_host orders itself after all earlier device work.
  */
 #ifndef WCT_SIM_H
 #define WCT_SIM_H
@@ -205,17 +207,24 @@ wct_status_t wct_sim_run_event(wct_sim_t *sim, const wct_depos_t *depos, float *
                                void *stream);
 
 /* Several events in one pass: events[e] for e < n_events; waveforms: HOST array of
- * n_events * n_planes DEVICE pointers, event-major.  Per event, its grids are cleared and
- * all its planes rasterized and scattered by one launch on a library stream, and each grid
- * is then convolved in place on a second library stream, so the rasterize of event e + 1
- * overlaps the convolution of event e; both streams are ordered after earlier work on
- * `stream`, and `stream` waits for both before later work.  The two library streams are
- * created at the first call: the rasterize stream with the priority of that call's `stream`,
- * the convolution stream one step higher (so a caller ranks one handle's batches above
- * another's by the priority of the stream it passes first).  When a call repeats an earlier call's pointers, depo counts
- * and event ids, the sequence is recorded as a CUDA graph, and later repeats replay it (up
- * to 8 graphs are kept per handle); the depo values themselves may change between replays.  Results equal
- * those of wct_sim_run_event for each event. */
+ * n_events * n_planes DEVICE pointers, event-major.  ONE persistent launch rasterizes and
+ * scatters every plane of every event (§2 steps 1-2), each event into a library grid set of
+ * its own: its warps take 8-depo chunks from a device counter, the largest events' chunks
+ * first, until none is left.  The grids are then convolved (§2 step 3) on two library streams
+ * taking the (event, plane) pairs alternately, each into the caller's waveform.  The grid sets
+ * (every plane's grid per event, kept all zero between uses) are library memory grown on the
+ * first call of a given size and counted against the HBM budget; if they do not all fit, the
+ * batch runs in chunks of events, one raster launch per chunk, the raster of chunk c + 1
+ * overlapping the convolutions of chunk c (schedule_id bits 4-7 ask for such chunks: value v
+ * > 0 means 2^(v-1) events per launch; bit 8 selects a single convolution stream, bit 9 three).  All library
+ * streams are ordered after earlier work on `stream`, and `stream` waits for them before
+ * later work.  They are created at the first call: the rasterize stream with the priority of
+ * that call's `stream`, the convolution streams one step higher (so a caller ranks one
+ * handle's batches above another's by the priority of the stream it passes first).  When a
+ * call repeats an earlier call's pointers, depo counts and event ids, the sequence is recorded
+ * as a CUDA graph, and later repeats replay it (up to 8 graphs are kept per handle); the depo
+ * values themselves may change between replays.  Results equal those of wct_sim_run_event for
+ * each event (up to the float32 summation order of the scatter-add). */
 wct_status_t wct_sim_run_batch(wct_sim_t *sim, const wct_depos_t *events, int n_events,
                                float *const *waveforms, void *stream);
 
@@ -263,7 +272,9 @@ typedef struct {
  * streams with double-buffered device staging owned by the library (2 x the waveforms of
  * every plane + 2 x the depos of the largest event, counted against the HBM budget): the
  * upload of event e + 1 and the download of event e - 1 overlap the kernels of event e.
- * Synchronous: returns when every waveform is in host memory, with the status of
+ * Synchronous: first waits for all work already enqueued on the device (earlier calls of this
+ * handle on any stream share its scratch), returns when every waveform is in host memory, with
+ * the status of
  * wct_sim_sync (WCT_EINVAL if invalid depos were skipped).  Results equal those of
  * wct_sim_run_event for each event.  WCT_EINVAL for a NULL or negative argument. */
 wct_status_t wct_sim_run_host(wct_sim_t *sim, const wct_host_depos_t *events, int n_events,
@@ -328,7 +339,11 @@ wct_status_t wct_sim_plane_info(const wct_sim_t *sim, int plane, int64_t *info);
  * one event set per plane.  wct_sim_stage_times waits for the recorded events and writes the
  * mean per run_event call (summed over planes), in microseconds:
  *   us[0] prep + binning, us[1] rasterize + scatter, us[2] forward row FFT,
- *   us[3] wire stage, us[4] inverse row FFT; us[5] (if n > 5) = number of calls timed. */
+ *   us[3] wire stage, us[4] inverse row FFT; us[5] (if n > 5) = number of calls timed.
+ * While timing, run_batch launches directly (no graph replay) and records, per persistent
+ * raster launch, its duration on the raster stream and the span of the convolutions that
+ * follow it (the longer of the two convolution streams); with n > 8, us[6] and us[7] receive
+ * their sums per run_batch call and us[8] the number of run_batch calls timed. */
 wct_status_t wct_sim_set_timing(wct_sim_t *sim, int enable);
 wct_status_t wct_sim_stage_times(wct_sim_t *sim, float *us, int n);
 

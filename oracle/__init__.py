@@ -19,6 +19,8 @@ Parity status of each function (what pins it; see tests/test_oracle_*.py):
                        direct quadruple loop, no circular wrap, linearity.
   digitise             pinned: noise-free codes against exact rounding of hand values,
                        clamping, the noise's normality and its keying.
+  all-core variants    rasterize_all_cores / scatter_all_cores (timing only) are checked
+                       bit-identical to the serial functions.
   drift attenuation    pinned: closed form q exp(-t_d / lifetime); fluctuated mean and
                        variance of the binomial; the same charge for every plane.
   impact-resolution    pinned: phase-independent responses reduce to the folded path,
@@ -58,8 +60,11 @@ def build(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-                               "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC]
+        try:   # OpenMP for the all-core timing variants; without it they run on one thread
+            subprocess.check_call(base + ["-fopenmp", "-lm"], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base + ["-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -90,6 +95,12 @@ def lib():
             L.or_scatter.restype = None
             L.or_convolve_direct.argtypes = [P, i64, i64, P, i64, i64, P]
             L.or_convolve_direct.restype = None
+            L.or_omp_threads.argtypes = [i32]
+            L.or_omp_threads.restype = i32
+            L.or_rasterize_omp.argtypes = [i64, P, P, P, P, P, P, P, P, i32, u64, i32, u64, P, i32]
+            L.or_rasterize_omp.restype = ctypes.c_int
+            L.or_scatter_omp.argtypes = [i64, P, P, i32, i64, i64, P, i32]
+            L.or_scatter_omp.restype = None
             _lib = L
     return _lib
 
@@ -189,6 +200,48 @@ def scatter(patches: Patches, plane) -> np.ndarray:
     lib().or_scatter(patches.desc.shape[0], _p(patches.desc), _p(vals), plane.n_impact_per_pitch,
                      plane.n_wires, plane.n_ticks, _p(grid))
     return grid
+
+
+def omp_threads(n_threads: int = 0) -> int:
+    """Threads the all-core variants use (1 if the oracle was built without OpenMP)."""
+    return int(lib().or_omp_threads(int(n_threads)))
+
+
+def rasterize_all_cores(depos, plane, diff, plane_index: int = 0, n_threads: int = 0) -> Patches:
+    """rasterize() with the depos spread over the host cores (each patch computed by one
+    thread at its own offset): the same patches, bit for bit.  For timing the oracle."""
+    desc, mus, total, bad = windows(depos, plane, diff)
+    vals = np.zeros(max(total, 1), dtype=np.float64)
+    pv, dv = _plane_vec(plane), _diff_vec(diff)
+    rc = lib().or_rasterize_omp(depos.n, _p(depos.t0), _p(depos.x), _p(depos.y), _p(depos.z),
+                                _p(depos.q), _p(pv), _p(dv), _p(desc), int(bool(diff.fluctuate)),
+                                int(diff.seed) & 0xFFFFFFFFFFFFFFFF, plane_index,
+                                int(depos.event_id), _p(vals), int(n_threads))
+    if rc != 0:
+        raise RuntimeError(f"oracle rasterize failed ({rc})")
+    return Patches(desc, vals[:total], mus, bad)
+
+
+def scatter_all_cores(patches: Patches, plane, n_threads: int = 0) -> np.ndarray:
+    """scatter() with each host thread owning a band of wires (every bin summed in the serial
+    depo order): the same grid, bit for bit.  For timing the oracle."""
+    grid = np.zeros((plane.n_wires, plane.n_ticks), dtype=np.float64)
+    vals = patches.values if patches.values.size else np.zeros(1)
+    lib().or_scatter_omp(patches.desc.shape[0], _p(patches.desc), _p(vals), plane.n_impact_per_pitch,
+                         plane.n_wires, plane.n_ticks, _p(grid), int(n_threads))
+    return grid
+
+
+def simulate_event_all_cores(depos, planes, diff, responses, n_threads: int = 0):
+    """The whole hot path of one event on every host core: per plane the all-core rasterize and
+    scatter, then scipy's FP64 FFT convolution with one worker per thread.  Returns the
+    waveforms (FP64)."""
+    workers = omp_threads(n_threads)
+    out = []
+    for p, (plane, resp) in enumerate(zip(planes, responses)):
+        pt = rasterize_all_cores(depos, plane, diff, p, n_threads)
+        out.append(convolve_fft(scatter_all_cores(pt, plane, n_threads), resp, workers=workers))
+    return out
 
 
 def convolve_direct(grid: np.ndarray, resp: np.ndarray) -> np.ndarray:

@@ -263,54 +263,67 @@ int64_t or_windows(int64_t n, const float *t0, const float *x, const float *y, c
  * unfluctuated patch is kept).  The depo index in the counter is the depo's position in
  * the event's arrays.
  */
+/* Depo i's patch (the body of or_rasterize's loop); 0, or < 0 on an error. */
+static int rasterize_one(int64_t i, const float *t0, const float *x, const float *y, const float *z,
+                         const float *q, const double *plane, const double *diff, const int64_t *desc,
+                         int32_t fluctuate, uint64_t seed, int32_t plane_index, uint64_t event_id,
+                         double *patches)
+{
+    const int32_t n_imp = (int32_t)plane[5];
+    const int64_t *d = desc + 5 * i;
+    const int64_t off = d[0], lo_t = d[1], lo_p = d[2], n_t = d[3], n_p = d[4];
+    if (n_t == 0 || n_p == 0)
+        return 0;
+    or_window w;
+    if (depo_window(t0[i], x[i], y[i], z[i], q[i], plane, diff, 1 << 30, 1 << 30, &w) != 0)
+        return -1;
+    double *wt = (double *)malloc(sizeof(double) * (size_t)n_t);
+    double *wp = (double *)malloc(sizeof(double) * (size_t)n_p);
+    if (!wt || !wp) { free(wt); free(wp); return -2; }
+    axis_weights(w.mu_t, w.s_t, lo_t, n_t, wt);
+    axis_weights(w.mu_p, w.s_p, lo_p, n_p, wp);
+    const double Q = (double)q[i];
+    double *P = patches + off;
+    for (int64_t a = 0; a < n_t; ++a)
+        for (int64_t b = 0; b < n_p; ++b)
+            P[a * n_p + b] = Q * wt[a] * wp[b];
+    if (fluctuate) {
+        double *F = (double *)malloc(sizeof(double) * (size_t)(n_t * n_p));
+        if (!F) { free(wt); free(wp); return -2; }
+        double sum = 0.0;
+        for (int64_t a = 0; a < n_t; ++a) {
+            for (int64_t b = 0; b < n_p; ++b) {
+                double wb = wt[a] * wp[b];
+                double mean = Q * wb;
+                double sd = sqrt(Q * wb * (1.0 - wb));
+                double zz = or_bin_normal(seed, (uint32_t)i, lo_t + a, lo_p + b, n_imp,
+                                          plane_index, event_id);
+                double v = mean + sd * zz;
+                F[a * n_p + b] = v > 0.0 ? v : 0.0;
+                sum += F[a * n_p + b];
+            }
+        }
+        if (sum > 0.0) {
+            for (int64_t k = 0; k < n_t * n_p; ++k)
+                P[k] = F[k] * (Q / sum);
+        }
+        free(F);
+    }
+    free(wt);
+    free(wp);
+    return 0;
+}
+
 int or_rasterize(int64_t n, const float *t0, const float *x, const float *y, const float *z,
                  const float *q, const double *plane, const double *diff, const int64_t *desc,
                  int32_t fluctuate, uint64_t seed, int32_t plane_index, uint64_t event_id,
                  double *patches)
 {
-    const int32_t n_imp = (int32_t)plane[5];
     for (int64_t i = 0; i < n; ++i) {
-        const int64_t *d = desc + 5 * i;
-        const int64_t off = d[0], lo_t = d[1], lo_p = d[2], n_t = d[3], n_p = d[4];
-        if (n_t == 0 || n_p == 0)
-            continue;
-        or_window w;
-        if (depo_window(t0[i], x[i], y[i], z[i], q[i], plane, diff, 1 << 30, 1 << 30, &w) != 0)
-            return -1;
-        double *wt = (double *)malloc(sizeof(double) * (size_t)n_t);
-        double *wp = (double *)malloc(sizeof(double) * (size_t)n_p);
-        if (!wt || !wp) { free(wt); free(wp); return -2; }
-        axis_weights(w.mu_t, w.s_t, lo_t, n_t, wt);
-        axis_weights(w.mu_p, w.s_p, lo_p, n_p, wp);
-        const double Q = (double)q[i];
-        double *P = patches + off;
-        for (int64_t a = 0; a < n_t; ++a)
-            for (int64_t b = 0; b < n_p; ++b)
-                P[a * n_p + b] = Q * wt[a] * wp[b];
-        if (fluctuate) {
-            double *F = (double *)malloc(sizeof(double) * (size_t)(n_t * n_p));
-            if (!F) { free(wt); free(wp); return -2; }
-            double sum = 0.0;
-            for (int64_t a = 0; a < n_t; ++a) {
-                for (int64_t b = 0; b < n_p; ++b) {
-                    double wb = wt[a] * wp[b];
-                    double mean = Q * wb;
-                    double sd = sqrt(Q * wb * (1.0 - wb));
-                    double zz = or_bin_normal(seed, (uint32_t)i, lo_t + a, lo_p + b, n_imp,
-                                              plane_index, event_id);
-                    double v = mean + sd * zz;
-                    F[a * n_p + b] = v > 0.0 ? v : 0.0;
-                    sum += F[a * n_p + b];
-                }
-            }
-            if (sum > 0.0) {
-                for (int64_t k = 0; k < n_t * n_p; ++k)
-                    P[k] = F[k] * (Q / sum);
-            }
-            free(F);
-        }
-        free(wt);
-        free(wp);
+        const int rc = rasterize_one(i, t0, x, y, z, q, plane, diff, desc, fluctuate, seed, plane_index, event_id,
+                                     patches);
+        if (rc != 0)
+            return rc;
     }
     return 0;
 }
@@ -335,6 +348,84 @@ void or_scatter(int64_t n, const int64_t *desc, const double *patches, int32_t n
                 if (wire < 0 || wire >= n_wires)
                     continue;
                 grid[wire * n_ticks + tick] += patches[off + a * n_p + b];
+            }
+        }
+    }
+}
+
+/* -------------------------------------------------------------------------------------
+ * All-core variants, for timing the oracle on every host core (built with OpenMP when the
+ * compiler has it; otherwise they run on one thread).  They compute exactly what the serial
+ * functions above compute:
+ *   or_rasterize_omp: depos spread over the threads (each patch is written by one thread,
+ *     at its own offset), so the patches are bit-identical to or_rasterize's;
+ *   or_scatter_omp: each thread owns a band of wires and adds, in depo order, the bins of
+ *     every patch that fold onto its band, so every bin's sum is taken in the serial order
+ *     and the grid is bit-identical to or_scatter's (no per-thread grid copies, no reduction).
+ * n_threads <= 0: the OpenMP default.  or_omp_threads reports the threads they will use.
+ * ------------------------------------------------------------------------------------- */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+int32_t or_omp_threads(int32_t n_threads)
+{
+#ifdef _OPENMP
+    return n_threads > 0 ? n_threads : (int32_t)omp_get_max_threads();
+#else
+    (void)n_threads;
+    return 1;
+#endif
+}
+
+int or_rasterize_omp(int64_t n, const float *t0, const float *x, const float *y, const float *z,
+                     const float *q, const double *plane, const double *diff, const int64_t *desc,
+                     int32_t fluctuate, uint64_t seed, int32_t plane_index, uint64_t event_id,
+                     double *patches, int32_t n_threads)
+{
+    int err = 0;
+    const int nt = or_omp_threads(n_threads);
+    (void)nt;
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nt) reduction(min : err)
+    for (int64_t i = 0; i < n; ++i) {
+        const int rc = rasterize_one(i, t0, x, y, z, q, plane, diff, desc, fluctuate, seed, plane_index, event_id,
+                                     patches);
+        if (rc < err)
+            err = rc;
+    }
+    return err;
+}
+
+void or_scatter_omp(int64_t n, const int64_t *desc, const double *patches, int32_t n_imp,
+                    int64_t n_wires, int64_t n_ticks, double *grid, int32_t n_threads)
+{
+    const int nt = or_omp_threads(n_threads);
+    (void)nt;
+#pragma omp parallel num_threads(nt)
+    {
+        int T = 1, me = 0;
+#ifdef _OPENMP
+        T = omp_get_num_threads();
+        me = omp_get_thread_num();
+#endif
+        const int64_t w_lo = n_wires * me / T, w_hi = n_wires * (me + 1) / T;   /* this thread's band */
+        for (int64_t i = 0; i < n; ++i) {
+            const int64_t *d = desc + 5 * i;
+            const int64_t off = d[0], lo_t = d[1], lo_p = d[2], n_t = d[3], n_p = d[4];
+            if (n_t == 0 || n_p == 0)
+                continue;
+            if (floor_div(lo_p + n_p - 1, n_imp) < w_lo || floor_div(lo_p, n_imp) >= w_hi)
+                continue;                                  /* no bin of this patch in the band */
+            for (int64_t a = 0; a < n_t; ++a) {
+                int64_t tick = lo_t + a;
+                if (tick < 0 || tick >= n_ticks)
+                    continue;
+                for (int64_t b = 0; b < n_p; ++b) {
+                    int64_t wire = floor_div(lo_p + b, n_imp);
+                    if (wire < w_lo || wire >= w_hi)
+                        continue;
+                    grid[wire * n_ticks + tick] += patches[off + a * n_p + b];
+                }
             }
         }
     }

@@ -297,11 +297,15 @@ class Simulator:
     STAGES = ("prep_binning", "raster_scatter", "row_r2c", "wire_stage", "row_c2r")
 
     def stage_times(self) -> dict:
-        """Mean microseconds per run_event of each stage since set_timing(True)."""
-        us = (ctypes.c_float * 6)()
-        self._check(self._lib.wct_sim_stage_times(self._h, us, 6))
+        """Mean microseconds per run_event of each stage since set_timing(True), and per
+        run_batch call its raster launches' and convolutions' durations."""
+        us = (ctypes.c_float * 9)()
+        self._check(self._lib.wct_sim_stage_times(self._h, us, 9))
         out = dict(zip(self.STAGES, (float(v) for v in us[:5])))
         out["events"] = int(us[5])
+        out["batch_raster"] = float(us[6])
+        out["batch_convolve"] = float(us[7])
+        out["batches"] = int(us[8])
         return out
 
     def counters(self) -> dict:

@@ -1029,7 +1029,7 @@ __global__ void __launch_bounds__(256) k_clear_tiles_fft(const ClearJob job) {
 // row once from shared memory.  full[g] completes when a group's copies
 // landed, empty[g] when every consumer finished reading the group.
 constexpr int kStageFB = 128;
-constexpr int kStageWiresMax = 128;      // output wires per CTA at most (runtime: 128, 64 or 32)
+constexpr int kStageWiresMax = 512;      // output wires per CTA at most (chosen at launch)
 constexpr int kGroupRows = 8;
 constexpr int kRingGroups = 4;
 

@@ -13,7 +13,9 @@
 // Unfused path: k_rasterize_patches (one warp per depo) writes every depo's full patch;
 // k_tile_scatter_patches sums caller-supplied patches per output tile in shared memory and
 // writes each tile once.
+#include <algorithm>
 #include <climits>
+#include <mutex>
 
 #include "wct_internal.cuh"
 #include "wct_device.cuh"
@@ -690,6 +692,37 @@ k_raster_batch_warps(const BatchTable tab, int32_t *status) {
                      c - it.chunk_begin, tab.plane[0].rk, it.flags);
 }
 
+// Batched, persistent: one launch for every (event, plane) pair of a batch.  Each warp keeps
+// taking the next warp-chunk from a device counter until the batch's chunks are exhausted, so
+// no warp waits for its CTA's siblings and the launch has no tail of idle CTA slots; the pairs
+// are ordered by the host (largest events first), so the most expensive chunks go out first.
+template <bool DET>
+__global__ void __launch_bounds__(kWarpsPerCta * 32)
+k_raster_batch_persistent(const BatchTable tab, int64_t total_chunks, unsigned long long *__restrict__ counter,
+                          int32_t *status) {
+    __shared__ WarpSmem<DET> S[kWarpsPerCta];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned long long c = 0;
+        if (lane == 0) c = atomicAdd(counter, 1ull);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        if (c >= (unsigned long long)total_chunks) break;
+        int lo = 0, hi = tab.n_items;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (tab.item[mid].chunk_begin <= (int64_t)c) lo = mid;
+            else hi = mid;
+        }
+        const BatchItem &it = tab.item[lo];
+        typename Acc<DET>::T *grid;
+        if constexpr (DET) grid = it.grid64;
+        else grid = it.grid;
+        raster_warp<DET>(S[warp], it.t0, it.x, it.y, it.z, it.q, it.n, tab.plane[it.plane], it.event_lo, grid, status,
+                         (int64_t)c - it.chunk_begin, tab.plane[0].rk, it.flags);
+        __syncwarp();
+    }
+}
+
 __global__ void __launch_bounds__(kChunkThreads)
 k_raster_chunks(const float *__restrict__ t0, const float *__restrict__ x, const float *__restrict__ y,
                 const float *__restrict__ z, const float *__restrict__ q, int64_t n, PlaneParams pp,
@@ -897,6 +930,49 @@ cudaError_t launch_raster_batch(const BatchTable &tab, int64_t total_chunks, int
     cudaError_t e = cudaFuncSetAttribute(k_raster_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_raster_batch<<<(unsigned)total_chunks, kChunkThreads, smem, s>>>(tab, status);
+    return cudaGetLastError();
+}
+
+namespace {
+// CTAs of the persistent batch rasterizer resident on the whole current device, per device
+// and accumulation mode, computed once under a lock.
+constexpr int kMaxDevicesRaster = 64;
+std::mutex g_raster_mu;
+int g_raster_resident[kMaxDevicesRaster][2] = {};
+
+int raster_resident(bool det) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevicesRaster ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+        cudaGetLastError();
+        return 152;
+    }
+    std::lock_guard<std::mutex> lock(g_raster_mu);
+    int &r = g_raster_resident[dev][det ? 1 : 0];
+    if (r == 0) {
+        int per_sm = 0;
+        const cudaError_t e =
+            det ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_batch_persistent<true>, kWarpsPerCta * 32, 0)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_batch_persistent<false>, kWarpsPerCta * 32, 0);
+        if (e != cudaSuccess || per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+        r = per_sm * sms;
+    }
+    return r;
+}
+}  // namespace
+
+cudaError_t launch_raster_batch_persistent(const BatchTable &tab, int64_t total_chunks, unsigned long long *counter,
+                                           int32_t *status, cudaStream_t s, bool det) {
+    if (total_chunks <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    const int64_t want = (total_chunks + kWarpsPerCta - 1) / kWarpsPerCta;
+    const int64_t grid = std::min<int64_t>(want, raster_resident(det));
+    if (det) k_raster_batch_persistent<true><<<(unsigned)grid, kWarpsPerCta * 32, 0, s>>>(tab, total_chunks, counter, status);
+    else k_raster_batch_persistent<false><<<(unsigned)grid, kWarpsPerCta * 32, 0, s>>>(tab, total_chunks, counter, status);
     return cudaGetLastError();
 }
 

@@ -99,6 +99,11 @@ cudaError_t launch_raster_chunks(const wct_depos_t &d, const PlaneParams &pp, ui
                                  unsigned long long *grid64 = nullptr);
 cudaError_t launch_raster_batch(const BatchTable &tab, int64_t total_chunks, int32_t *status, cudaStream_t s,
                                 bool det = false);
+// One persistent launch over every warp-chunk of the table's pairs (total_chunks warp-chunks of
+// 8 depos, chunk_begin in warp-chunks): the warps take chunks from *counter (reset on `s`
+// first) until none is left.
+cudaError_t launch_raster_batch_persistent(const BatchTable &tab, int64_t total_chunks, unsigned long long *counter,
+                                           int32_t *status, cudaStream_t s, bool det);
 // grid[r][c] += g64[r][c] / kFixScale and g64[r][c] = 0 over the tiles listed in flags (the
 // flag layout below, for an n_rows x n_cols grid with tile_w x tile_t tiles; flags only read)
 cudaError_t launch_fix_tiles(const uint32_t *flags, int n_rows, int n_cols, int tile_w, int tile_t,

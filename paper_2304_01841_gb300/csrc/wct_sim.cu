@@ -27,7 +27,6 @@ namespace {
 constexpr int kMaxPlanes = 8;
 constexpr int kStages = 5;        // prep + binning, raster-scatter, row r2c, wire stage, row c2r
 constexpr int kMaxSlots = 4096;
-constexpr int kBatchEvents = 16;  // fork / join and per-event dependency events of run_batch
 constexpr int kMaxM = 14336;   // largest complex FFT length: two M-point buffers in one CTA's shared memory
 
 struct PlaneState {
@@ -71,20 +70,28 @@ struct wct_sim {
     float2 *spec_imp = nullptr;     // impact mode: the spectra of every phase [phase][wire][Fs]
     size_t spec_imp_elems = 0;
 
-    // Accumulation grids of run_event / run_batch: two sets of every plane's grid, kept all
+    // Accumulation grids: set 0 serves run_event, sets 1.. run_batch (one per event of a raster
+    // launch, grown on demand).  A set holds every plane's grid and tile flags and is kept all
     // zero between uses: the rasterizer flags the tiles it touches, and once the forward
     // transform has read a grid those tiles are cleared again.
-    float *grids[2] = {};
+    std::vector<float *> grids;
     size_t grid_off[kMaxPlanes + 1] = {};
-    uint32_t *tile_flags[2] = {};
+    std::vector<uint32_t *> tile_flags;
     size_t flag_off[kMaxPlanes + 1] = {};
     // Deterministic mode: the rasterizers accumulate fixed-point integers into grids64 (same
     // offsets as grids, all zero between uses) and launch_fix_tiles moves the touched tiles into
     // the float grid; det_flags lists the touched tiles when the target is a caller's grid.
     bool det = false;
-    unsigned long long *grids64[2] = {};
+    std::vector<unsigned long long *> grids64;
     uint32_t *det_flags = nullptr;
-    cudaEvent_t gev[2] = {};   // run_batch: a grid set's clearing transforms are done
+    // run_batch: work counter of the persistent raster launch, the second convolution stream's
+    // spectrum scratch, and the events ordering the batch's streams
+    unsigned long long *work_counter = nullptr;
+    int batch_events_per_launch = 0;   // schedule: events per persistent raster launch (0 = all)
+    int conv_streams = 2;              // schedule: convolution streams (1, 2 or 3)
+    float2 *bspec[3][2] = {};          // convolution streams 1, 2: forward / wire-stage spectra
+    size_t bspec_elems[3] = {};
+    std::vector<cudaEvent_t> evpool;
     DepoDesc *desc = nullptr;
     int64_t *patch_size = nullptr, *patch_off = nullptr, *scan64 = nullptr;
     int64_t depo_cap = 0;
@@ -100,11 +107,15 @@ struct wct_sim {
     std::vector<std::array<cudaEvent_t, kStages + 1>> slots;
     int slots_used = 0;
     int events_timed = 0;
+    // run_batch timing, per raster launch: raster begin / end on the raster stream, then the
+    // convolutions' begin / end on each convolution stream
+    std::vector<std::array<cudaEvent_t, 6>> bslots;
+    int bslots_used = 0;
+    int batches_timed = 0;
     int64_t launches = 0;   // kernels launched by this handle
     // run_batch: CUDA graphs of whole batches, keyed by the batch's pointers and sizes
     cudaStream_t cap_stream = nullptr;
-    cudaStream_t rs_stream = nullptr, cv_stream = nullptr;   // run_batch raster / convolution streams
-    cudaEvent_t bev[kBatchEvents] = {};
+    cudaStream_t rs_stream = nullptr, cv_stream[3] = {};   // run_batch raster / convolution streams
     struct Graph {
         std::vector<uint64_t> key;
         cudaGraphExec_t exec;
@@ -441,11 +452,31 @@ void mark(wct_sim *s, int slot, int k, cudaStream_t st) {
     if (slot >= 0) cudaEventRecord(s->slots[slot][k], st);
 }
 
+// A fresh run_batch timing slot (one per raster launch), or -1 when not timing.
+int acquire_batch_slot(wct_sim *s) {
+    if (!s->timing || s->bslots_used >= kMaxSlots) return -1;
+    if (s->bslots_used == (int)s->bslots.size()) {
+        std::array<cudaEvent_t, 6> ev{};
+        for (auto &e : ev)
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                cudaGetLastError();
+                return -1;
+            }
+        s->bslots.push_back(ev);
+    }
+    return s->bslots_used++;
+}
+
+void bmark(wct_sim *s, int slot, int k, cudaStream_t st) {
+    if (slot >= 0) cudaEventRecord(s->bslots[slot][k], st);
+}
+
 // Restore the all-zero library grids after a failed call (synchronous; best effort).
 void clear_grids(wct_sim *s) {
-    for (int b = 0; b < 2; ++b) {
+    for (size_t b = 0; b < s->grids.size(); ++b) {
         if (s->grids[b]) cudaMemset(s->grids[b], 0, sizeof(float) * s->grid_off[s->n_planes]);
-        if (s->grids64[b]) cudaMemset(s->grids64[b], 0, sizeof(unsigned long long) * s->grid_off[s->n_planes]);
+        if (b < s->grids64.size() && s->grids64[b])
+            cudaMemset(s->grids64[b], 0, sizeof(unsigned long long) * s->grid_off[s->n_planes]);
         if (s->tile_flags[b]) cudaMemset(s->tile_flags[b], 0, sizeof(uint32_t) * s->flag_off[s->n_planes]);
     }
     for (int p = 0; p < s->n_planes; ++p) {
@@ -456,6 +487,34 @@ void clear_grids(wct_sim *s) {
     }
     if (s->det_flags) cudaMemset(s->det_flags, 0, sizeof(uint32_t) * s->flag_off[s->n_planes]);
     cudaDeviceSynchronize();
+}
+
+// One more accumulation grid set (every plane's grid, tile flags and, in the deterministic
+// mode, fixed-point grid), all zero; all or nothing.  Synchronous.
+wct_status_t add_grid_set(wct_sim *s) {
+    const size_t cells = s->grid_off[s->n_planes], words = s->flag_off[s->n_planes];
+    float *g = nullptr;
+    uint32_t *f = nullptr;
+    unsigned long long *g64 = nullptr;
+    wct_status_t st = s->det ? dev_alloc_all(s, {{(void **)&g, sizeof(float) * cells},
+                                                 {(void **)&f, sizeof(uint32_t) * words},
+                                                 {(void **)&g64, sizeof(unsigned long long) * cells}})
+                             : dev_alloc_all(s, {{(void **)&g, sizeof(float) * cells}, {(void **)&f, sizeof(uint32_t) * words}});
+    if (st) return st;
+    cudaError_t e = cudaMemset(g, 0, sizeof(float) * cells);
+    if (e == cudaSuccess) e = cudaMemset(f, 0, sizeof(uint32_t) * words);
+    if (e == cudaSuccess && g64) e = cudaMemset(g64, 0, sizeof(unsigned long long) * cells);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        dev_free(s, g);
+        dev_free(s, f);
+        dev_free(s, g64);
+        return cuda_fail(s, e, "grid init");
+    }
+    s->grids.push_back(g);
+    s->tile_flags.push_back(f);
+    s->grids64.push_back(g64);
+    return WCT_OK;
 }
 
 // Fused rasterize + scatter of one plane into `grid` (zeroed first unless it is known to be
@@ -491,18 +550,20 @@ wct_status_t raster_scatter(wct_sim *s, int plane, const wct_depos_t *d, float *
 // The convolution of one plane.  clear_grid (== grid, a library grid) with its tile flags:
 // the flagged tiles are zeroed once the forward transform has read the grid.
 wct_status_t convolve_plane(wct_sim *s, int plane, const float *grid, float *wf, cudaStream_t st, int slot,
-                            float *clear_grid = nullptr, uint32_t *flags = nullptr) {
+                            float *clear_grid = nullptr, uint32_t *flags = nullptr, float2 *S = nullptr,
+                            float2 *T = nullptr) {
     const PlaneState &ps = s->planes[plane];
     const int nw = ps.g.n_wires, nt = ps.g.n_ticks;
-    cudaError_t e = launch_row_r2c(ps.fft, grid, nt, nt, nw, s->spec, st, s->status);
+    if (!S) S = s->spec, T = s->spec2;
+    cudaError_t e = launch_row_r2c(ps.fft, grid, nt, nt, nw, S, st, s->status);
     if (e != cudaSuccess) return cuda_fail(s, e, "row r2c");
     mark(s, slot, 3, st);
     // the wire stage clears the grid tiles the rasterizer listed, as a side job
     const ClearJob job = clear_grid ? clear_job(clear_grid, flags, ps.pp) : ClearJob{};
-    e = launch_wire_stage(ps.fft, s->spec, ps.resp_spec, nw, s->spec2, st, s->status, clear_grid ? &job : nullptr);
+    e = launch_wire_stage(ps.fft, S, ps.resp_spec, nw, T, st, s->status, clear_grid ? &job : nullptr);
     if (e != cudaSuccess) return cuda_fail(s, e, "wire stage");
     mark(s, slot, 4, st);
-    e = launch_row_c2r(ps.fft, s->spec2, nw, wf, nt, nt, st, s->status);
+    e = launch_row_c2r(ps.fft, T, nw, wf, nt, nt, st, s->status);
     if (e != cudaSuccess) return cuda_fail(s, e, "row c2r");
     s->launches += 3;
     mark(s, slot, 5, st);
@@ -663,6 +724,11 @@ wct_status_t wct_sim_create(const wct_plane_t *planes, int n_planes, const wct_r
         const int id = s->opts.schedule_id;
         row_schedule = (id & 8) ? 3 : (id & 4) ? 2 : (id & 1);
         raster_schedule = (id >> 1) & 1;
+        // run_batch: bits 4-7 = v > 0 limit a persistent raster launch to 2^(v-1) events (chunks
+        // that pipeline with the previous chunk's convolutions); bit 8 = one convolution stream
+        const int v = (id >> 4) & 15;
+        s->batch_events_per_launch = v > 0 ? 1 << (v - 1) : 0;
+        s->conv_streams = ((id >> 8) & 1) ? 1 : ((id >> 9) & 1) ? 3 : 2;
     }
     s->det = s->opts.deterministic != 0;
     if (s->det) raster_schedule = 0;   // the fixed-point accumulation exists in the warp-level rasterizer
@@ -808,25 +874,12 @@ wct_status_t wct_sim_create(const wct_plane_t *planes, int n_planes, const wct_r
         s->flag_off[p + 1] = s->flag_off[p] + tile_flag_words(s->planes[p].pp);
     }
     if (st == WCT_OK && s->det) {
-        for (int b = 0; b < 2 && st == WCT_OK; ++b) {
-            st = dev_alloc(s, (void **)&s->grids64[b], sizeof(unsigned long long) * s->grid_off[n_planes]);
-            if (st == WCT_OK && cudaMemset(s->grids64[b], 0, sizeof(unsigned long long) * s->grid_off[n_planes]))
-                st = fail(s, WCT_ECUDA, "grid init");
-        }
-        if (st == WCT_OK) st = dev_alloc(s, (void **)&s->det_flags, sizeof(uint32_t) * s->flag_off[n_planes]);
+        st = dev_alloc(s, (void **)&s->det_flags, sizeof(uint32_t) * s->flag_off[n_planes]);
         if (st == WCT_OK && cudaMemset(s->det_flags, 0, sizeof(uint32_t) * s->flag_off[n_planes]))
             st = fail(s, WCT_ECUDA, "grid init");
     }
-    for (int b = 0; b < 2 && st == WCT_OK; ++b) {
-        st = dev_alloc(s, (void **)&s->grids[b], sizeof(float) * s->grid_off[n_planes]);
-        if (st == WCT_OK) st = dev_alloc(s, (void **)&s->tile_flags[b], sizeof(uint32_t) * s->flag_off[n_planes]);
-        if (st == WCT_OK) {
-            cudaError_t e = cudaMemset(s->grids[b], 0, sizeof(float) * s->grid_off[n_planes]);
-            if (e == cudaSuccess) e = cudaMemset(s->tile_flags[b], 0, sizeof(uint32_t) * s->flag_off[n_planes]);
-            if (e == cudaSuccess) e = cudaDeviceSynchronize();
-            if (e != cudaSuccess) st = cuda_fail(s, e, "grid init");
-        }
-    }
+    if (st == WCT_OK) st = dev_alloc(s, (void **)&s->work_counter, sizeof(unsigned long long));
+    if (st == WCT_OK) st = add_grid_set(s);   // set 0: run_event's
     if (st != WCT_OK) {
         for (auto &a : s->allocs)
             if (a.first) cudaFree(a.first);
@@ -844,13 +897,13 @@ wct_status_t wct_sim_destroy(wct_sim_t *s) {
         if (a.first) cudaFree(a.first);
     for (auto &slot : s->slots)
         for (auto &e : slot) cudaEventDestroy(e);
+    for (auto &slot : s->bslots)
+        for (auto &e : slot) cudaEventDestroy(e);
     for (auto &g : s->graphs) cudaGraphExecDestroy(g.exec);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
-    if (s->rs_stream) cudaStreamDestroy(s->rs_stream);
-    if (s->cv_stream) cudaStreamDestroy(s->cv_stream);
-    for (auto &e : s->bev)
-        if (e) cudaEventDestroy(e);
-    for (auto &e : s->gev)
+    for (cudaStream_t h : {s->rs_stream, s->cv_stream[0], s->cv_stream[1], s->cv_stream[2]})
+        if (h) cudaStreamDestroy(h);
+    for (auto &e : s->evpool)
         if (e) cudaEventDestroy(e);
     for (cudaStream_t h : {s->up_stream, s->comp_stream, s->down_stream})
         if (h) cudaStreamDestroy(h);
@@ -1001,14 +1054,17 @@ namespace {
 
 constexpr size_t kMaxGraphs = 8;
 
-// All (event, plane) pairs: grids cleared, one batched rasterize + scatter launch per group
-// of up to kBatchItems pairs, then the convolution of every grid (in place).
-// Library streams and events used to overlap the rasterize of one event with the
-// convolution of the previous one inside run_batch.
+// run_batch.  The whole batch (or, under a memory limit or a schedule asking for it, a chunk of
+// its events) is rasterized and scattered by ONE persistent launch over every (event, plane)
+// pair, each event into a grid set of its own, on a library raster stream; the convolutions of
+// the rasterized grids follow on library convolution streams (two by default, taking the
+// (event, plane) pairs alternately, so one plane's transform overlaps the tail of another's),
+// each with its own spectrum scratch.  With several chunks, the raster of chunk c + 1 overlaps
+// the convolutions of chunk c.  All streams fork from and join back into the caller's stream.
 wct_status_t batch_streams(wct_sim *s, cudaStream_t caller) {
     if (s->rs_stream) return WCT_OK;
     // the rasterize stream takes the priority of the stream of the first run_batch call and the
-    // convolution stream the next higher one, so the convolution's CTAs go first whenever SMs
+    // convolution streams the next higher one, so the convolution's CTAs go first whenever SMs
     // free up and the rasterize CTAs fill the remaining room, and a caller can rank one
     // handle's batches above another's (lower numbers run first)
     int lo = 0, hi = 0, own = 0;
@@ -1018,88 +1074,173 @@ wct_status_t batch_streams(wct_sim *s, cudaStream_t caller) {
         own = lo;
     }
     own = std::min(std::max(own, hi), lo);
+    const int conv = std::max(hi, own - 1);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->rs_stream, cudaStreamNonBlocking, own);
-    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->cv_stream, cudaStreamNonBlocking, std::max(hi, own - 1));
-    for (int i = 0; e == cudaSuccess && i < kBatchEvents; ++i)
-        e = cudaEventCreateWithFlags(&s->bev[i], cudaEventDisableTiming);
-    for (int b = 0; e == cudaSuccess && b < 2; ++b) e = cudaEventCreateWithFlags(&s->gev[b], cudaEventDisableTiming);
+    for (int j = 0; j < 3 && e == cudaSuccess; ++j)
+        e = cudaStreamCreateWithPriority(&s->cv_stream[j], cudaStreamNonBlocking, conv);
     if (e != cudaSuccess) return cuda_fail(s, e, "batch streams");
     return WCT_OK;
 }
 
-// All (event, plane) pairs, event by event: on the raster stream each event's grids are
-// cleared and rasterized by one batched launch; on the convolution stream each grid is then
-// convolved in place.  The raster of event e + 1 overlaps the convolution of event e (they
-// use different units: the raster is integer / SFU bound, the transforms shared-memory
-// bound).  Both streams fork from and join back into `st`.
+// The i-th event of the batch's event pool (created on first use; reused by later calls, whose
+// records and waits are stream-ordered after this call's).
+wct_status_t pool_event(wct_sim *s, size_t i, cudaEvent_t *out) {
+    while (s->evpool.size() <= i) {
+        cudaEvent_t e = nullptr;
+        const cudaError_t err = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+        if (err != cudaSuccess) return cuda_fail(s, err, "batch events");
+        s->evpool.push_back(e);
+    }
+    *out = s->evpool[i];
+    return WCT_OK;
+}
+
+// Batch grid sets 1..want (set 0 is run_event's); stops early when memory runs out, as long as
+// at least one batch set exists.  *have receives the number of batch sets.
+wct_status_t ensure_batch_sets(wct_sim *s, int want, int *have) {
+    while ((int)s->grids.size() < want + 1) {
+        const wct_status_t st = add_grid_set(s);
+        if (st == WCT_ENOMEM && s->grids.size() > 1) {
+            s->err.clear();
+            break;
+        }
+        if (st) return st;
+    }
+    *have = std::min(want, (int)s->grids.size() - 1);
+    return WCT_OK;
+}
+
+// The spectrum scratch of convolution streams 1 .. n - 1, as large as stream 0's (spec, spec2).
+wct_status_t ensure_conv_spectra(wct_sim *s, int n) {
+    for (int j = 1; j < n; ++j) {
+        if (s->bspec[j][0] && s->bspec_elems[j] >= s->spec_elems) continue;
+        dev_free(s, s->bspec[j][0]);
+        dev_free(s, s->bspec[j][1]);
+        s->bspec[j][0] = s->bspec[j][1] = nullptr;
+        s->bspec_elems[j] = 0;
+        const wct_status_t st = dev_alloc_all(s, {{(void **)&s->bspec[j][0], sizeof(float2) * s->spec_elems},
+                                                  {(void **)&s->bspec[j][1], sizeof(float2) * s->spec_elems}});
+        if (st) return st;
+        s->bspec_elems[j] = s->spec_elems;
+    }
+    return WCT_OK;
+}
+
 wct_status_t enqueue_batch(wct_sim *s, const wct_depos_t *events, int n_events, float *const *wfs, cudaStream_t st) {
     wct_status_t r = batch_streams(s, st);
     if (r) return r;
     const int npl = s->n_planes;
-    static thread_local BatchTable tab;   // ~21 KB: kept off the stack
+    // events per raster launch: the whole batch unless the schedule asks for smaller chunks; a
+    // launch's table holds at most kBatchItems (event, plane) pairs
+    int per = s->batch_events_per_launch > 0 ? s->batch_events_per_launch : n_events;
+    per = std::max(1, std::min({per, n_events, kBatchItems / npl}));
+    int n_chunks = (n_events + per - 1) / per;
+    // grid sets: one per event of a launch, twice that when chunks alternate (so the raster of
+    // chunk c + 1 never waits for the convolutions of chunk c)
+    int have = 0;
+    if ((r = ensure_batch_sets(s, n_chunks > 1 ? 2 * per : per, &have))) return r;
+    if (have < (n_chunks > 1 ? 2 * per : per)) {
+        per = std::max(1, have >= 2 ? have / 2 : 1);
+        n_chunks = (n_events + per - 1) / per;
+    }
+    const bool alternate = n_chunks > 1 && have >= 2 * per;
+    const int nc = std::max(1, std::min(3, s->conv_streams));
+    if ((r = ensure_conv_spectra(s, nc))) return r;
+    // largest events first: the persistent launch hands out their chunks before the small ones'
+    std::vector<int> order(n_events);
+    for (int e = 0; e < n_events; ++e) order[e] = e;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return events[a].n > events[b].n; });
+    static thread_local BatchTable tab;   // ~25 KB: kept off the stack
     for (int p = 0; p < npl; ++p) tab.plane[p] = s->planes[p].pp;
-    cudaStream_t rs = s->rs_stream, cv = s->cv_stream;
-    cudaError_t err = cudaEventRecord(s->bev[0], st);
-    if (err == cudaSuccess) err = cudaStreamWaitEvent(rs, s->bev[0], 0);
-    if (err == cudaSuccess) err = cudaStreamWaitEvent(cv, s->bev[0], 0);
+    cudaStream_t rs = s->rs_stream, *cv = s->cv_stream;
+    float2 *S[3] = {s->spec, s->bspec[1][0], s->bspec[2][0]}, *T[3] = {s->spec2, s->bspec[1][1], s->bspec[2][1]};
+    // events of the pool: 0 fork, then per chunk c: 1 + 4c raster done, 2 + 4c + j its
+    // convolutions done on convolution stream j
+    cudaEvent_t fork = nullptr;
+    if ((r = pool_event(s, 0, &fork))) return r;
+    cudaError_t err = cudaEventRecord(fork, st);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(rs, fork, 0);
+    for (int j = 0; j < nc && err == cudaSuccess; ++j) err = cudaStreamWaitEvent(cv[j], fork, 0);
     if (err != cudaSuccess) return cuda_fail(s, err, "batch fork");
-    for (int e = 0; e < n_events; ++e) {
-        const wct_depos_t &d = events[e];
+    int k_conv = 0;   // (event, plane) pairs convolved so far: they take the streams in turn
+    for (int c = 0; c < n_chunks; ++c) {
+        const int e0 = c * per, e1 = std::min(n_events, e0 + per);
+        const int base = 1 + (alternate ? (c & 1) * per : 0);   // first grid set of this chunk
+        cudaEvent_t rdone = nullptr, cdone[3] = {};
+        if ((r = pool_event(s, 1 + 4 * (size_t)c, &rdone))) return r;
+        for (int j = 0; j < nc; ++j)
+            if ((r = pool_event(s, 2 + 4 * (size_t)c + j, &cdone[j]))) return r;
+        // the sets were last used by chunk c - 2 (alternating) or c - 1: wait for their clearing
+        const int prev = alternate ? c - 2 : c - 1;
+        if (prev >= 0)
+            for (int j = 0; j < nc && err == cudaSuccess; ++j) err = cudaStreamWaitEvent(rs, s->evpool[2 + 4 * prev + j], 0);
+        if (err != cudaSuccess) return cuda_fail(s, err, "batch grid dependency");
         int64_t chunks = 0;
         tab.n_items = 0;
-        const int gb = e & 1;   // grid set of this event (all zero once its previous user is done)
-        if (e >= 2) {
-            err = cudaStreamWaitEvent(rs, s->gev[gb], 0);
-            if (err != cudaSuccess) return cuda_fail(s, err, "batch grid dependency");
-        }
-        for (int p = 0; p < npl; ++p) {
-            float *grid = s->grids[gb] + s->grid_off[p];
+        for (int i = e0; i < e1; ++i) {
+            const wct_depos_t &d = events[order[i]];
             if (d.n <= 0) continue;
-            BatchItem &b = tab.item[tab.n_items++];
-            b.t0 = d.t0_us;
-            b.x = d.x_mm;
-            b.y = d.y_mm;
-            b.z = d.z_mm;
-            b.q = d.q_e;
-            b.n = d.n;
-            b.grid = grid;
-            b.grid64 = s->det ? s->grids64[gb] + s->grid_off[p] : nullptr;
-            b.flags = s->tile_flags[gb] + s->flag_off[p];
-            b.chunk_begin = chunks;
-            b.event_lo = (uint32_t)d.event_id;
-            b.plane = p;
-            chunks += raster_chunk_count(d.n, tab.plane[0].raster_schedule);
-        }
-        if (chunks > 0) {
-            err = launch_raster_batch(tab, chunks, s->status, rs, s->det);
-            if (err != cudaSuccess) return cuda_fail(s, err, "batched raster-scatter");
-            s->launches += 1;
-            for (int i = 0; s->det && i < tab.n_items; ++i) {
-                const BatchItem &b = tab.item[i];
-                const PlaneParams &pp = tab.plane[b.plane];
-                err = launch_fix_tiles(b.flags, pp.n_wires, pp.n_ticks, pp.tile_w, pp.tile_t, b.grid64, b.grid, rs,
-                                       s->status);
-                if (err != cudaSuccess) return cuda_fail(s, err, "fixed-point grid");
-                s->launches += 1;
+            const int set = base + (i - e0);
+            for (int p = 0; p < npl; ++p) {
+                BatchItem &b = tab.item[tab.n_items++];
+                b.t0 = d.t0_us;
+                b.x = d.x_mm;
+                b.y = d.y_mm;
+                b.z = d.z_mm;
+                b.q = d.q_e;
+                b.n = d.n;
+                b.grid = s->grids[set] + s->grid_off[p];
+                b.grid64 = s->det ? s->grids64[set] + s->grid_off[p] : nullptr;
+                b.flags = s->tile_flags[set] + s->flag_off[p];
+                b.chunk_begin = chunks;
+                b.event_lo = (uint32_t)d.event_id;
+                b.plane = p;
+                chunks += raster_chunk_count(d.n, 0);
             }
         }
-        cudaEvent_t done = s->bev[1 + e % (kBatchEvents - 2)];
-        err = cudaEventRecord(done, rs);
-        if (err == cudaSuccess) err = cudaStreamWaitEvent(cv, done, 0);
-        if (err != cudaSuccess) return cuda_fail(s, err, "batch dependency");
-        for (int p = 0; p < npl; ++p) {
-            float *grid = s->grids[gb] + s->grid_off[p];
-            r = convolve_plane(s, p, grid, wfs[(size_t)e * npl + p], cv, -1, grid, s->tile_flags[gb] + s->flag_off[p]);
-            if (r) return r;
+        const int tslot = acquire_batch_slot(s);
+        bmark(s, tslot, 0, rs);
+        if (chunks > 0) {
+            err = launch_raster_batch_persistent(tab, chunks, s->work_counter, s->status, rs, s->det);
+            if (err != cudaSuccess) return cuda_fail(s, err, "batched raster-scatter");
+            s->launches += 1;
         }
-        err = cudaEventRecord(s->gev[gb], cv);
+        bmark(s, tslot, 1, rs);
+        err = cudaEventRecord(rdone, rs);
+        for (int j = 0; j < nc && err == cudaSuccess; ++j) err = cudaStreamWaitEvent(cv[j], rdone, 0);
+        if (err != cudaSuccess) return cuda_fail(s, err, "batch dependency");
+        bmark(s, tslot, 2, cv[0]);
+        bmark(s, tslot, 4, cv[nc - 1]);
+        for (int i = e0; i < e1; ++i) {
+            const int e = order[i], set = base + (i - e0);
+            for (int p = 0; p < npl; ++p, ++k_conv) {
+                const int j = k_conv % nc;
+                float *grid = s->grids[set] + s->grid_off[p];
+                if (s->det && events[e].n > 0) {
+                    // deterministic mode: the touched fixed-point tiles into the float grid, on
+                    // the stream that convolves it (overlapping the other stream's work)
+                    const PlaneParams &pp = s->planes[p].pp;
+                    err = launch_fix_tiles(s->tile_flags[set] + s->flag_off[p], pp.n_wires, pp.n_ticks, pp.tile_w,
+                                           pp.tile_t, s->grids64[set] + s->grid_off[p], grid, cv[j], s->status);
+                    if (err != cudaSuccess) return cuda_fail(s, err, "fixed-point grid");
+                    s->launches += 1;
+                }
+                r = convolve_plane(s, p, grid, wfs[(size_t)e * npl + p], cv[j], -1, grid,
+                                   s->tile_flags[set] + s->flag_off[p], S[j], T[j]);
+                if (r) return r;
+            }
+        }
+        bmark(s, tslot, 3, cv[0]);
+        bmark(s, tslot, 5, cv[nc - 1]);
+        for (int j = 0; j < nc && err == cudaSuccess; ++j) err = cudaEventRecord(cdone[j], cv[j]);
         if (err != cudaSuccess) return cuda_fail(s, err, "batch grid dependency");
     }
-    cudaEvent_t end = s->bev[kBatchEvents - 1];
-    err = cudaEventRecord(end, cv);
-    if (err == cudaSuccess) err = cudaStreamWaitEvent(st, end, 0);
-    if (err == cudaSuccess) err = cudaEventRecord(end, rs);
-    if (err == cudaSuccess) err = cudaStreamWaitEvent(st, end, 0);
+    if (s->timing) ++s->batches_timed;
+    // join: the caller's stream waits for the last chunk's convolutions and the raster stream
+    const int last = n_chunks - 1;
+    err = cudaSuccess;
+    for (int j = 0; j < nc && err == cudaSuccess; ++j) err = cudaStreamWaitEvent(st, s->evpool[2 + 4 * last + j], 0);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(st, s->evpool[1 + 4 * last], 0);
     if (err != cudaSuccess) return cuda_fail(s, err, "batch join");
     return WCT_OK;
 }
@@ -1129,6 +1270,7 @@ wct_status_t wct_sim_run_batch(wct_sim_t *s, const wct_depos_t *events, int n_ev
             }
             return WCT_OK;
         }
+    if (s->timing) return enqueue_batch(s, events, n_events, wfs, cs);   // timing events: no graph
     // graph key: everything the recorded launches depend on
     std::vector<uint64_t> key;
     key.reserve((size_t)n_events * (7 + s->n_planes) + 1);
@@ -1216,7 +1358,10 @@ wct_status_t wct_sim_run_host(wct_sim_t *s, const wct_host_depos_t *events, int 
             if (!wfs[(size_t)e * npl + p]) return fail(s, WCT_EINVAL, "a waveform pointer is NULL");
         max_n = std::max(max_n, h.n);
     }
-    cudaError_t err = cudaSuccess;
+    // the pipeline runs on the library's own streams: wait for work already enqueued on the
+    // device (this handle's earlier calls on any stream share its scratch)
+    cudaError_t err = cudaDeviceSynchronize();
+    if (err != cudaSuccess) return cuda_fail(s, err, "host pipeline: earlier work");
     if (!s->up_stream) {
         for (cudaStream_t *h : {&s->up_stream, &s->comp_stream, &s->down_stream})
             if (err == cudaSuccess) err = cudaStreamCreateWithFlags(h, cudaStreamNonBlocking);
@@ -1544,6 +1689,8 @@ wct_status_t wct_sim_set_timing(wct_sim_t *s, int enable) {
     s->timing = enable != 0;
     s->slots_used = 0;
     s->events_timed = 0;
+    s->bslots_used = 0;
+    s->batches_timed = 0;
     return WCT_OK;
 }
 
@@ -1563,6 +1710,30 @@ wct_status_t wct_sim_stage_times(wct_sim_t *s, float *us, int n) {
     const double div = s->events_timed > 0 ? (double)s->events_timed : 1.0;
     for (int j = 0; j < n && j < kStages; ++j) us[j] = (float)(acc[j] / div);
     if (n > kStages) us[kStages] = (float)s->events_timed;
+    if (n > kStages + 3) {
+        double raster = 0.0, conv = 0.0;
+        auto span = [](cudaEvent_t a, cudaEvent_t b) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+                cudaGetLastError();
+                return 0.0;
+            }
+            return 1000.0 * ms;
+        };
+        for (int k = 0; k < s->bslots_used; ++k) {
+            auto &ev = s->bslots[k];
+            for (int j : {1, 3, 5}) {
+                cudaError_t e = cudaEventSynchronize(ev[j]);
+                if (e != cudaSuccess) return cuda_fail(s, e, "batch stage events");
+            }
+            raster += span(ev[0], ev[1]);
+            conv += std::max(span(ev[2], ev[3]), span(ev[4], ev[5]));
+        }
+        const double bdiv = s->batches_timed > 0 ? (double)s->batches_timed : 1.0;
+        us[kStages + 1] = (float)(raster / bdiv);
+        us[kStages + 2] = (float)(conv / bdiv);
+        us[kStages + 3] = (float)s->batches_timed;
+    }
     return WCT_OK;
 }
 

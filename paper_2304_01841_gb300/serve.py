@@ -10,13 +10,15 @@ are on the GPU is admitted as soon as a slot and memory free up.  Latency is sub
 completion observed on the host.
 
 Admission is size aware, so that small events never wait behind a large one:
-  - a request of at least `heavy_depos` depos is heavy: it runs in a batch of its own, on one
-    of the last `heavy_slots` slots, whose streams have the lowest priority;
+  - a request of at least `heavy_depos` depos is heavy: it runs in a batch of its own on a
+    low-priority stream, on one of the last `heavy_slots` slots (or on an idle light slot, see
+    below);
   - light requests are batched in arrival order (skipping heavy ones) up to `max_batch`
     requests and `max_batch_depos` depos per batch, on high-priority streams, so the device's
     block scheduler runs their kernels ahead of a heavy event's whenever SMs free up;
-  - a heavy slot with no heavy request pending takes a light batch; heavy requests are admitted
-    in arrival order among themselves.
+  - a heavy slot with no heavy request pending takes a light batch; a light slot with no light
+    request pending takes a heavy request as long as another slot stays free for light
+    traffic; heavy requests are admitted in arrival order among themselves.
 
 The results of a request do not depend on what it was batched with: the fluctuation stream is
 keyed by (seed, event id, plane, depo index, bin), so each event is the same alone and in a mix
@@ -79,20 +81,26 @@ def pin_depos(d):
 class CudaBackend:
     """Device side of a slot: a simulator handle and a stream."""
 
-    def __init__(self, planes, responses, diffusion, keep_results: bool, priority: int = 0):
+    def __init__(self, planes, responses, diffusion, keep_results: bool, heavy_depos: int = 500_000):
         import torch
         from . import Simulator
         self.torch = torch
         self.planes = list(planes)
         self.sim = Simulator(planes, responses, diffusion)
-        # lower numbers run first; the library's own batch streams follow this stream's priority
-        self.stream = torch.cuda.Stream(priority=priority)
+        # lower numbers run first: light batches on a high-priority stream (the library's own
+        # batch streams follow its priority), heavy events on a low-priority one
+        self.stream_light = torch.cuda.Stream(priority=-2)
+        self.stream_heavy = torch.cuda.Stream(priority=0)
+        self.stream = self.stream_light
+        self.heavy_depos = int(heavy_depos)
         self.keep = keep_results
         self.dev, self.outs, self.host, self.event = [], [], [], None
 
     def launch(self, batch: List[Request]):
         from . import DeviceDepos
         torch = self.torch
+        heavy = len(batch) == 1 and int(len(batch[0].depos.t0)) >= self.heavy_depos
+        self.stream = self.stream_heavy if heavy else self.stream_light
         with torch.cuda.stream(self.stream):
             self.dev = []
             for r in batch:
@@ -101,7 +109,14 @@ class CudaBackend:
                 self.dev.append(DeviceDepos(*dev, event_id=int(d.event_id)))
             self.outs = [[torch.empty((p.n_wires, p.n_ticks), dtype=torch.float32, device="cuda")
                           for p in self.planes] for _ in batch]
-            self.sim.run_batch(self.dev, self.outs, stream=self.stream)
+            if len(batch) == 1:
+                # one event (e.g. a heavy one, alone on a low-priority slot): run_event, whose
+                # rasterizer is a plain grid of short CTAs, so higher-priority work from other
+                # slots takes over SMs as its CTAs finish (the batch's persistent raster launch
+                # would hold every SM until it is done)
+                self.sim.run_event(self.dev[0], self.outs[0], stream=self.stream)
+            else:
+                self.sim.run_batch(self.dev, self.outs, stream=self.stream)
             if self.keep:
                 self.host = [[o.to("cpu", non_blocking=True) for o in ev] for ev in self.outs]
             self.event = torch.cuda.Event()
@@ -139,12 +154,12 @@ class EventServer:
         heavy_slots = max(0, min(heavy_slots, n_slots))
         n_light = n_slots - heavy_slots
 
-        def make(heavy: bool):
+        def make():
             if backend_factory is not None:
                 return backend_factory()
-            return CudaBackend(planes, responses, diffusion, keep_results, priority=0 if heavy else -2)
+            return CudaBackend(planes, responses, diffusion, keep_results, heavy_depos=heavy_depos)
 
-        self.slots = [_Slot(make(i >= n_light), i >= n_light) for i in range(n_slots)]
+        self.slots = [_Slot(make(), i >= n_light) for i in range(n_slots)]
         self.heavy_depos = int(heavy_depos)
         self.max_batch_depos = int(max_batch_depos)
         self.max_batch = max_batch
@@ -204,7 +219,11 @@ class EventServer:
     def _take(self, slot: "_Slot"):
         """The batch a free slot launches next (removed from pending; caller holds the lock)."""
         heavy_slots_exist = any(s.heavy for s in self.slots)
-        if slot.heavy:
+        light_waiting = any(not self.is_heavy(r) for r in self.pending)
+        # a light slot helps with heavy requests only while no light request waits and another
+        # slot stays free for light traffic arriving meanwhile
+        spare = sum(1 for s in self.slots if not s.batch and s is not slot) >= 1
+        if slot.heavy or (heavy_slots_exist and not light_waiting and spare):
             for r in self.pending:                     # the oldest heavy request, alone
                 if self.is_heavy(r):
                     need = self.request_bytes(r)

@@ -409,3 +409,28 @@ def serving_depo_counts(n_events: int, seed: int = 20230409, small=(5_000, 50_00
     n_small = np.exp(rng.uniform(math.log(small[0]), math.log(small[1]), n_events))
     n_large = rng.uniform(large[0], large[1], n_events)
     return np.where(big, n_large, n_small).astype(np.int64)
+
+
+def slice_events(pool: Sequence[Depos], counts, rng: np.random.Generator, first_event_id: int) -> List[Depos]:
+    """Events of the given depo counts cut from a pool of large generated events: each a
+    contiguous slice of one pool event (whole track segments, plus the isolated depos the slice
+    covers), with consecutive event ids from first_event_id."""
+    out = []
+    for i, n in enumerate(counts):
+        base = pool[int(rng.integers(len(pool)))]
+        n = int(min(n, base.n))
+        s0 = int(rng.integers(0, base.n - n + 1))
+        d = base.subset(slice(s0, s0 + n))
+        out.append(Depos(d.t0, d.x, d.y, d.z, d.q, event_id=first_event_id + i))
+    return out
+
+
+def batch_events(n_events: int = 64, pool_seed: Optional[int] = None, first_event_id: int = 5000,
+                 slice_seed: int = 7) -> List[Depos]:
+    """The batched workload: n_events three-plane events (the "three_plane" geometry), depo
+    counts from batch_depo_counts, each cut from one of three generated 500k-depo events (200
+    tracks + 20% isolated low-charge depos, as the single three-plane event)."""
+    wl = workload("three_plane")
+    seed = wl.seed if pool_seed is None else pool_seed
+    pool = [wl.depos(n_depos=500_000, seed=seed + k) for k in range(3)]
+    return slice_events(pool, batch_depo_counts(n_events), np.random.default_rng(slice_seed), first_event_id)

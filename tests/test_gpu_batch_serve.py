@@ -76,6 +76,54 @@ def test_batch_multiplane_matches_single_and_graph_replay():
             assert _close(to_np(outs[e][p]), s, np.abs(s).max())
 
 
+def test_batch_schedules_and_memory_limit_match_single_events():
+    # one persistent raster launch for the whole batch (the default), chunks of 2 events that
+    # pipeline with the previous chunk's convolutions, a single convolution stream, and a budget
+    # that leaves room for only two batch grid sets (chunks of one event, alternating): every
+    # event equals run_event, and the default issues exactly one raster launch per batch
+    import paper_2304_01841_gb300 as g
+    planes, responses = _small_three_plane()
+    diff = synth.Diffusion(fluctuate=True, seed=78)
+    evs = _events(7, seed=5)
+    evs[3] = synth.Depos(*(np.zeros(0, np.float32) for _ in range(5)))
+    evs[3].event_id = 3
+    ref_sim = make_sim(planes, responses, diff)
+    dev = [g.DeviceDepos.from_host(e) for e in evs]
+    singles = [[to_np(w) for w in ref_sim.run_event(d)] for d in dev]
+    ref_sim.sync()
+    base = ref_sim.counters()["device_bytes"]
+    set_bytes = sum(4 * p.n_wires * p.n_ticks + 4 * (2 * ref_sim.plane_info(i)["n_tiles"] + 2)
+                    for i, p in enumerate(planes))
+    ref_sim.close()
+
+    def check(sim, label):
+        outs = [[torch.full((p.n_wires, p.n_ticks), float("nan"), device="cuda") for p in planes] for _ in evs]
+        for rep in range(2):
+            sim.run_batch(dev, outs)
+            sim.sync()
+            for e in range(len(evs)):
+                for p in range(len(planes)):
+                    assert _close(to_np(outs[e][p]), singles[e][p], np.abs(singles[e][p]).max()), (label, rep, e, p)
+
+    sim = make_sim(planes, responses, diff)
+    n0 = sim.counters()["kernel_launches"]
+    outs = [[torch.empty((p.n_wires, p.n_ticks), device="cuda") for p in planes] for _ in evs]
+    sim.run_batch(dev, outs)
+    sim.sync()
+    n_pairs = sum(1 for e in evs if e.n > 0) * len(planes)
+    assert sim.counters()["kernel_launches"] - n0 == 1 + 3 * len(evs) * len(planes), n_pairs
+    check(sim, "default")
+    sim.close()
+    for sched, label in ((8 | (2 << 4), "chunks of 2"), (8 | 256, "one convolution stream")):
+        sim = make_sim(planes, responses, diff, schedule_id=sched)
+        check(sim, label)
+        sim.close()
+    sim = make_sim(planes, responses, diff, schedule_id=8 | 256, hbm_budget_bytes=base + int(2.5 * set_bytes))
+    check(sim, "two grid sets")
+    assert sim.counters()["device_bytes"] <= base + int(2.5 * set_bytes)
+    sim.close()
+
+
 def test_server_results_same_alone_and_in_mix():
     import paper_2304_01841_gb300 as g
     from paper_2304_01841_gb300.serve import EventServer
@@ -158,9 +206,7 @@ def test_benchmarked_batch_of_64_three_plane_events_sampled():
     import oracle
     import paper_2304_01841_gb300 as g
     wl = synth.workload("three_plane")
-    counts = synth.batch_depo_counts(64)
-    pool = [wl.depos(n_depos=500_000, seed=wl.seed + k) for k in range(3)]
-    evs = bench._slice_pool(pool, counts, np.random.default_rng(7), 5000)
+    evs = bench.rank_events(0, 64)
     sim = make_sim(wl.planes, wl.responses(), wl.diffusion)
     dev = [g.DeviceDepos.from_host(e) for e in evs]
     outs = [[torch.empty((p.n_wires, p.n_ticks), dtype=torch.float32, device="cuda") for p in wl.planes]
@@ -178,13 +224,12 @@ def test_served_apa_mix_sampled():
     # the served configuration: APA-like planes (800/800/960 x 6000), a heavy-tailed mix of
     # small events and a 1M-depo one through the event server; the large event and a small one
     # against the oracle
-    import bench
     import oracle
     from paper_2304_01841_gb300.serve import EventServer, pin_depos
     wl = synth.workload("dune_apa")
     pool = [wl.depos(n_depos=1_000_000, seed=wl.seed + 1)]
     counts = [20_000, 1_000_000, 8_000, 45_000, 5_000, 30_000]
-    evs = bench._slice_pool(pool, counts, np.random.default_rng(11), 9000)
+    evs = synth.slice_events(pool, counts, np.random.default_rng(11), 9000)
     srv = EventServer(wl.planes, wl.responses(), wl.diffusion, n_slots=4, max_batch=8, hbm_budget_bytes=24 << 30,
                       keep_results=True)
     reqs = [srv.submit(pin_depos(e)) for e in evs]

@@ -148,3 +148,24 @@ def test_scatter_conserves_in_range_charge():
         m = np.outer((ticks >= 0) & (ticks < pl.n_ticks), (wires >= 0) & (wires < pl.n_wires))
         tot += P[m].sum()
     assert abs(g.sum() - tot) < 1e-9 * max(tot, 1.0)
+
+
+def test_all_core_variants_are_bit_identical_to_the_serial_oracle():
+    # the all-core timing variants (depos spread over threads; each thread owning a band of
+    # wires for the scatter) compute exactly the serial oracle's patches and grid
+    import oracle
+    import synth
+    wl = synth.workload("tiny")
+    d = wl.depos(n_depos=3000)
+    pl = wl.planes[0]
+    for fl in (False, True):
+        diff = synth.Diffusion(fluctuate=fl, seed=91)
+        ref = oracle.rasterize(d, pl, diff)
+        for threads in (1, 3, 0):
+            pt = oracle.rasterize_all_cores(d, pl, diff, n_threads=threads)
+            assert np.array_equal(pt.desc, ref.desc) and np.array_equal(pt.values, ref.values)
+            assert np.array_equal(oracle.scatter_all_cores(pt, pl, n_threads=threads), oracle.scatter(ref, pl))
+    assert oracle.omp_threads(3) in (1, 3)
+    wf = oracle.simulate_event_all_cores(d, [pl], synth.Diffusion(fluctuate=True, seed=91), [wl.responses()[0]])
+    _, _, w_ref = oracle.simulate_plane(d, pl, synth.Diffusion(fluctuate=True, seed=91), wl.responses()[0])
+    assert np.allclose(wf[0], w_ref, rtol=0, atol=1e-9 * np.abs(w_ref).max())
