@@ -1022,16 +1022,25 @@ __global__ void __launch_bounds__(256) k_clear_tiles_fft(const ClearJob job) {
 }
 
 // ---- wire stage fed by bulk copies -------------------------------------------------------
-// CTA = kStageFB consecutive frequencies x a run of wires_per_cta output wires.  A producer
-// warp streams the input rows' frequency slices (kStageFB complex = 1 KB each) into a ring of
-// kRingGroups groups of kGroupRows rows with bulk copies, one mbarrier pair per group; the
-// consumer threads (one per frequency) run the 21-tap stencil in pull form, reading each input
-// row once from shared memory.  full[g] completes when a group's copies
-// landed, empty[g] when every consumer finished reading the group.
+// CTA = kStageFB consecutive frequencies x a run of wires_per_cta output wires.  The input rows
+// s = w0 - KC + m (m = 0 .. n_out + 2 KC - 1) of the CTA's frequency slice (kStageFB complex =
+// 1 KB per row) stream through a ring of kRingGroups groups of kGroupRows rows in shared memory,
+// one mbarrier pair per group: full[g] completes when the group's copies landed, empty[g] when
+// every consumer has taken its rows.  Group k holds the rows m = 8k - 4 .. 8k + 3, so the 8 rows
+// that a block of 8 outputs adds to its window (rows 8q + 20 .. 8q + 27 for outputs 8q .. 8q + 7)
+// are exactly group q + 3: a consumer does one wait, eight constant-offset loads and one release
+// per block, with no per-row index arithmetic.  Rows outside the plane are copied from a zero
+// row, so the consumers never test them.  A producer thread issues the copies; the consumer
+// threads (one per frequency) keep a window of 28 input rows in registers and run the 21-tap
+// stencil in pull form, each input row read from shared memory once.
 constexpr int kStageFB = 128;
 constexpr int kStageWiresMax = 512;      // output wires per CTA at most (chosen at launch)
 constexpr int kGroupRows = 8;
 constexpr int kRingGroups = 4;
+constexpr int kGroupLead = 3;            // groups loaded before the first block's: rows -4 .. 19
+
+// A frequency slice of zeros: the copy source of the rows outside the plane.
+__device__ __align__(16) float2 g_zero_row[kStageFB] = {};
 
 __global__ void __launch_bounds__(kStageFB + 32, 3)
 k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, int Fs, int Fu, int n_wires,
@@ -1045,12 +1054,9 @@ k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, in
     const int nf = min(kStageFB, Fu - f0);             // even (Fu even, f0 multiple of 128)
     const uint32_t row_bytes = (uint32_t)nf * 8u;
     const int w0 = blockIdx.y * wires_per_cta;
-    const int w1 = min(w0 + wires_per_cta, n_wires);
-    const int n_in = (w1 - w0) + 2 * KC;               // input rows s = w0 - KC + m
-    const int m_lo = max(0, KC - w0);                  // rows inside the plane: [m_lo, m_hi)
-    const int m_hi = min(n_in, n_wires - w0 + KC);
-    const int n_rows = m_hi - m_lo;
-    const int n_groups = (n_rows + kGroupRows - 1) / kGroupRows;
+    const int n_out = min(wires_per_cta, n_wires - w0);
+    const int n_blocks = (n_out + kGroupRows - 1) / kGroupRows;
+    const int n_groups = n_blocks + kGroupLead;         // groups of one phase
     if (tid == 0) {
         for (int i = 0; i < kRingGroups; ++i) {
             mbar_init(&full[i], 1);
@@ -1066,20 +1072,21 @@ k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, in
         // (impact mode: the groups of every phase in turn, one ring sequence)
         if (tid == kStageFB) {
             for (int gg = 0; gg < n_phases * n_groups; ++gg) {
-                const int ph = gg / n_groups, g = gg - ph * n_groups;
+                const int ph = gg / n_groups, k = gg - ph * n_groups;
                 const int gs = gg % kRingGroups, use = gg / kRingGroups;
                 if (use > 0 && !mbar_wait(&empty[gs], (use - 1) & 1)) {
                     set_status(status, ST_ETIMEOUT);
                     break;
                 }
-                const int r0 = g * kGroupRows, r1 = min(r0 + kGroupRows, n_rows);
                 const float2 *Sp = S + (size_t)ph * s_phase_stride;
                 fence_proxy_async_smem();
-                mbar_arrive_expect_tx(&full[gs], row_bytes * (uint32_t)(r1 - r0));
-                for (int r = r0; r < r1; ++r)
-                    if (WCT_IDX_OK(status, w0 - KC + m_lo + r, n_wires))
-                        bulk_g2s(ring[gs * kGroupRows + (r - r0)], Sp + (size_t)(w0 - KC + m_lo + r) * Fs + f0,
-                                 row_bytes, &full[gs]);
+                mbar_arrive_expect_tx(&full[gs], row_bytes * (uint32_t)kGroupRows);
+#pragma unroll
+                for (int i = 0; i < kGroupRows; ++i) {
+                    const int src_row = w0 - KC + kGroupRows * k - 4 + i;
+                    const float2 *src = (src_row >= 0 && src_row < n_wires) ? Sp + (size_t)src_row * Fs + f0 : g_zero_row;
+                    bulk_g2s(ring[gs * kGroupRows + i], src, row_bytes, &full[gs]);
+                }
                 *(volatile int *)&s_issued = gg + 1;
             }
             __threadfence_block();
@@ -1093,78 +1100,90 @@ k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, in
         clear_listed_tiles(clear, blockIdx.y * gridDim.x + blockIdx.x, gridDim.x * gridDim.y, kStageFB);
     const int f = f0 + tid;
     const bool live = tid < nf;
-    // Pull form in blocks of kOutBlock outputs: the window holds input rows b .. b+kOutBlock+19,
-    // output b+j = sum_k win[j + 20 - k] * Rt[k]; each input row is read from the ring once.
-    constexpr int kOutBlock = 8;
-    constexpr int kWin = kOutBlock + 2 * KC;
+    constexpr int kOutBlock = kGroupRows;
+    constexpr int kWin = kOutBlock + 2 * KC;           // rows 8q .. 8q + 27 of block q
     float2 rr[KW], ri[KW];                             // (re, re) and (im, im) of each tap
     bool ok = true;
     int g_fail = 0;                                    // first group whose wait ran out (if !ok)
-    int gbase = 0;                                     // ring sequence number of the phase's group 0
-    auto load_row = [&](int m) -> float2 {
-        float2 x = make_float2(0.f, 0.f);
-        if (m >= m_lo && m < m_hi) {
-            const int idx = m - m_lo;
-            const int gl = idx / kGroupRows, in_g = idx - gl * kGroupRows;
-            const int g = gbase + gl, gs = g % kRingGroups;
-            if (in_g == 0 && ok && !mbar_wait(&full[gs], (g / kRingGroups) & 1)) {
-                set_status(status, ST_ETIMEOUT);
-                ok = false;
-                g_fail = g;
-            }
-            if (ok && live && WCT_IDX_OK(status, gs * kGroupRows + in_g, kRingGroups * kGroupRows))
-                x = ring[gs * kGroupRows + in_g][tid];
-            // after a timeout this thread releases no slot: a slot whose copy may still land is
-            // never handed to the producer again (it then gives up on its own bounded wait)
-            if (ok && (in_g == kGroupRows - 1 || idx == n_rows - 1))
-                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[gs])) : "memory");
+    // the 8 rows of ring group gg (sequence number) into x[0..7], then release the slot
+    auto take = [&](int gg, float2 (&x)[kGroupRows]) {
+        const int gs = gg % kRingGroups;
+        if (ok && !mbar_wait(&full[gs], (gg / kRingGroups) & 1)) {
+            set_status(status, ST_ETIMEOUT);
+            ok = false;
+            g_fail = gg;
         }
-        return x;
+#pragma unroll
+        for (int i = 0; i < kGroupRows; ++i)
+            x[i] = (ok && WCT_IDX_OK(status, gs * kGroupRows + i, kRingGroups * kGroupRows))
+                       ? ring[gs * kGroupRows + i][tid]
+                       : make_float2(0.f, 0.f);
+        // after a timeout this thread releases no slot: a slot whose copy may still land is
+        // never handed to the producer again (it then gives up on its own bounded wait)
+        if (ok) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[gs])) : "memory");
     };
-    const int n_out = w1 - w0;
-    for (int ph = 0; ph < n_phases; ++ph, gbase += n_groups) {
-    const float2 *Rp = Rt + (size_t)ph * r_phase_stride;
+    for (int ph = 0; ph < n_phases; ++ph) {
+        const int gbase = ph * n_groups;
+        const float2 *Rp = Rt + (size_t)ph * r_phase_stride;
 #pragma unroll
-    for (int k = 0; k < KW; ++k) {
-        const float2 v = live ? Rp[(size_t)k * Fs + f] : make_float2(0.f, 0.f);
-        rr[k] = make_float2(v.x, v.x);
-        ri[k] = make_float2(v.y, v.y);
-    }
-    const bool acc = accumulate || ph > 0;
-    float2 win[kWin];
+        for (int k = 0; k < KW; ++k) {
+            const float2 v = live ? Rp[(size_t)k * Fs + f] : make_float2(0.f, 0.f);
+            rr[k] = make_float2(v.x, v.x);
+            ri[k] = make_float2(v.y, v.y);
+        }
+        const bool acc = accumulate || ph > 0;
+        float2 win[kWin];
+        {
+            // rows -4 .. 19: the upper half of group 0, groups 1 and 2
+            float2 x[kGroupRows];
+            take(gbase, x);
 #pragma unroll
-    for (int t = 0; t < 2 * KC; ++t) win[t] = load_row(t);
-    for (int b = 0; b < n_out; b += kOutBlock) {
+            for (int i = 0; i < 4; ++i) win[i] = x[4 + i];
+            take(gbase + 1, x);
 #pragma unroll
-        for (int t = 0; t < kOutBlock; ++t) win[2 * KC + t] = load_row(b + 2 * KC + t);
+            for (int i = 0; i < kGroupRows; ++i) win[4 + i] = x[i];
+            take(gbase + 2, x);
 #pragma unroll
-        for (int j = 0; j < kOutBlock; ++j) {
-            // packed pairs: A = sum x * (r.re, r.re), B = sum x * (r.im, r.im), so that
-            // re = A.re - B.im and im = A.im + B.re (two FFMA2 per tap instead of four FFMA)
-            float2 A = make_float2(0.f, 0.f), B = A, A2 = A, B2 = A;
+            for (int i = 0; i < kGroupRows; ++i) win[12 + i] = x[i];
+        }
+        float2 *dst = T + (size_t)w0 * Fs + f;
+        for (int q = 0; q < n_blocks; ++q) {
+            {
+                float2 x[kGroupRows];
+                take(gbase + q + kGroupLead, x);
 #pragma unroll
-            for (int k = 0; k < KW; ++k) {
-                const float2 x = win[j + 2 * KC - k];
-                if (k & 1) {
-                    A2 = fma2(x, rr[k], A2);
-                    B2 = fma2(x, ri[k], B2);
-                } else {
-                    A = fma2(x, rr[k], A);
-                    B = fma2(x, ri[k], B);
+                for (int i = 0; i < kGroupRows; ++i) win[2 * KC + i] = x[i];
+            }
+            const int nj = min(kOutBlock, n_out - kOutBlock * q);
+#pragma unroll
+            for (int j = 0; j < kOutBlock; ++j) {
+                // packed pairs: A = sum x * (r.re, r.re), B = sum x * (r.im, r.im), so that
+                // re = A.re - B.im and im = A.im + B.re (two FFMA2 per tap instead of four FFMA)
+                float2 A = make_float2(0.f, 0.f), B = A, A2 = A, B2 = A;
+#pragma unroll
+                for (int k = 0; k < KW; ++k) {
+                    const float2 x = win[j + 2 * KC - k];
+                    if (k & 1) {
+                        A2 = fma2(x, rr[k], A2);
+                        B2 = fma2(x, ri[k], B2);
+                    } else {
+                        A = fma2(x, rr[k], A);
+                        B = fma2(x, ri[k], B);
+                    }
+                }
+                A = add2(A, A2);
+                B = add2(B, B2);
+                if (live && j < nj &&
+                    WCT_IDX_OK(status, (int64_t)(w0 + kOutBlock * q + j) * Fs + f, (int64_t)n_wires * Fs)) {
+                    float2 v = make_float2(A.x - B.y, A.y + B.x);
+                    if (acc) v = cadd(v, dst[(size_t)j * Fs]);
+                    dst[(size_t)j * Fs] = v;
                 }
             }
-            A = add2(A, A2);
-            B = add2(B, B2);
-            if (live && b + j < n_out && WCT_IDX_OK(status, (int64_t)(w0 + b + j) * Fs + f, (int64_t)n_wires * Fs)) {
-                float2 v = make_float2(A.x - B.y, A.y + B.x);
-                float2 *dst = &T[(size_t)(w0 + b + j) * Fs + f];
-                if (acc) v = cadd(v, *dst);
-                *dst = v;
-            }
-        }
+            dst += (size_t)kOutBlock * Fs;
 #pragma unroll
-        for (int t = 0; t < 2 * KC; ++t) win[t] = win[t + kOutBlock];
-    }
+            for (int t = 0; t < 2 * KC; ++t) win[t] = win[t + kOutBlock];
+        }
     }
     if (!ok && tid == 0) {
         // after a timeout: once the producer has stopped issuing (bounded), wait (bounded) for
