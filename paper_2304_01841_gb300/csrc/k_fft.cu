@@ -841,7 +841,7 @@ __device__ __forceinline__ void release_to_copy() {
 template <int T, int... Rs>
 __global__ void __launch_bounds__(T, 2)
 k_row_r2c_pair(FFTPlan p, const float *__restrict__ in, int n_rows, int n_cols, float2 *__restrict__ spec,
-               int32_t *status) {
+               int32_t *status, const uint8_t *__restrict__ act) {
     constexpr int M = (Rs * ...);
     constexpr bool kOdd = (sizeof...(Rs) & 1) != 0;     // result in B, A free after the last stage
     extern __shared__ float4 sm4[];
@@ -854,18 +854,24 @@ k_row_r2c_pair(FFTPlan p, const float *__restrict__ in, int n_rows, int n_cols, 
     const float2 c1 = p.rtw[1];
     pair_init<M>(p, L.TWH, bar);
     __syncthreads();
-    int row = blockIdx.x;
+    // rows known to be all zero (act[row] == 0) are skipped: their spectra are never read
+    auto next_row = [&](int r) {
+        if (act)
+            while (r < n_rows && !act[r]) r += gridDim.x;
+        return r;
+    };
+    int row = next_row(blockIdx.x);
     if (threadIdx.x == 0 && row < n_rows) {
         mbar_arrive_expect_tx(bar, bytes);
         bulk_g2s(A, in + (size_t)row * n_cols, bytes, bar);
     }
     uint32_t parity = 0;
-    for (; row < n_rows; row += gridDim.x) {
+    for (int next; row < n_rows; row = next) {
         for (int k = half + threadIdx.x; k < M; k += T) A[k] = make_float2(0.f, 0.f);   // zero pad
         if (!row_tma_wait(bar, parity, status)) return;
         parity ^= 1u;
         const float2 *Z = FftPair<M, T, false, 1, Rs...>::run(A, A, B, TWH);
-        const int next = row + gridDim.x;
+        next = next_row(row + gridDim.x);
         if constexpr (kOdd) {
             release_to_copy();
             if (threadIdx.x == 0 && next < n_rows) {
@@ -900,7 +906,7 @@ k_row_r2c_pair(FFTPlan p, const float *__restrict__ in, int n_rows, int n_cols, 
 template <int T, int... Rs>
 __global__ void __launch_bounds__(T, 2)
 k_row_c2r_pair(FFTPlan p, const float2 *__restrict__ spec, int n_rows, float *__restrict__ out, int n_cols,
-               int32_t *status) {
+               int32_t *status, const uint8_t *__restrict__ act) {
     constexpr int M = (Rs * ...);
     constexpr bool kOdd = (sizeof...(Rs) & 1) != 0;
     extern __shared__ float4 sm4[];
@@ -913,14 +919,25 @@ k_row_c2r_pair(FFTPlan p, const float2 *__restrict__ spec, int n_rows, float *__
     const float2 c1 = p.rtw[1];
     pair_init<M>(p, L.TWH, bar);
     __syncthreads();
-    int row = blockIdx.x;
+    const float2 zero = make_float2(0.f, 0.f);
+    // output rows known to be zero (act[row] == 0: no charge within the response's reach) are
+    // written as zeros, without a copy or a transform
+    auto next_row = [&](int r) {
+        if (act)
+            while (r < n_rows && !act[r]) {
+                float2 *dz = reinterpret_cast<float2 *>(out + (size_t)r * n_cols);
+                for (int n2 = threadIdx.x; 2 * n2 < n_cols; n2 += T) dz[n2] = zero;
+                r += gridDim.x;
+            }
+        return r;
+    };
+    int row = next_row(blockIdx.x);
     if (threadIdx.x == 0 && row < n_rows) {
         mbar_arrive_expect_tx(bar, bytes);
         bulk_g2s(A, spec + (size_t)row * p.Fs, bytes, bar);
     }
     uint32_t parity = 0;
-    const float2 zero = make_float2(0.f, 0.f);
-    for (; row < n_rows; row += gridDim.x) {
+    for (int next; row < n_rows; row = next) {
         if (!row_tma_wait(bar, parity, status)) return;
         parity ^= 1u;
         // Z[k] = E + i O, E = (X[k] + conj X[M-k]) / 2, O = exp(2 pi i k / P)(X[k] - conj X[M-k]) / 2,
@@ -946,7 +963,7 @@ k_row_c2r_pair(FFTPlan p, const float2 *__restrict__ spec, int n_rows, float *__
         }
         __syncthreads();
         const float2 *z = FftPair<M, T, true, 1, Rs...>::run(A, A, B, TWH);
-        const int next = row + gridDim.x;
+        next = next_row(row + gridDim.x);
         if constexpr (kOdd) {
             release_to_copy();
             if (threadIdx.x == 0 && next < n_rows) {
@@ -1029,8 +1046,9 @@ __global__ void __launch_bounds__(256) k_clear_tiles_fft(const ClearJob job) {
 // every consumer has taken its rows.  Group k holds the rows m = 8k - 4 .. 8k + 3, so the 8 rows
 // that a block of 8 outputs adds to its window (rows 8q + 20 .. 8q + 27 for outputs 8q .. 8q + 7)
 // are exactly group q + 3: a consumer does one wait, eight constant-offset loads and one release
-// per block, with no per-row index arithmetic.  Rows outside the plane are copied from a zero
-// row, so the consumers never test them.  A producer thread issues the copies; the consumer
+// per block, with no per-row index arithmetic.  Rows outside the plane, and rows the forward
+// transform skipped as all zero (act), are copied from a zero row, so the consumers never test
+// them.  A producer thread issues the copies; the consumer
 // threads (one per frequency) keep a window of 28 input rows in registers and run the 21-tap
 // stencil in pull form, each input row read from shared memory once.
 constexpr int kStageFB = 128;
@@ -1045,7 +1063,7 @@ __device__ __align__(16) float2 g_zero_row[kStageFB] = {};
 __global__ void __launch_bounds__(kStageFB + 32, 3)
 k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, int Fs, int Fu, int n_wires,
                  int wires_per_cta, float2 *__restrict__ T, int32_t *status, const ClearJob clear, int accumulate,
-                 int n_phases, int64_t s_phase_stride, int64_t r_phase_stride) {
+                 int n_phases, int64_t s_phase_stride, int64_t r_phase_stride, const uint8_t *__restrict__ act) {
     __shared__ __align__(16) float2 ring[kRingGroups * kGroupRows][kStageFB];
     __shared__ uint64_t full[kRingGroups], empty[kRingGroups];
     __shared__ int s_issued, s_prod_done;               // groups the producer issued; it has stopped
@@ -1081,10 +1099,16 @@ k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, in
                 const float2 *Sp = S + (size_t)ph * s_phase_stride;
                 fence_proxy_async_smem();
                 mbar_arrive_expect_tx(&full[gs], row_bytes * (uint32_t)kGroupRows);
+                bool live_row[kGroupRows];
 #pragma unroll
                 for (int i = 0; i < kGroupRows; ++i) {
                     const int src_row = w0 - KC + kGroupRows * k - 4 + i;
-                    const float2 *src = (src_row >= 0 && src_row < n_wires) ? Sp + (size_t)src_row * Fs + f0 : g_zero_row;
+                    live_row[i] = src_row >= 0 && src_row < n_wires && (!act || act[src_row]);
+                }
+#pragma unroll
+                for (int i = 0; i < kGroupRows; ++i) {
+                    const int src_row = w0 - KC + kGroupRows * k - 4 + i;
+                    const float2 *src = live_row[i] ? Sp + (size_t)src_row * Fs + f0 : g_zero_row;
                     bulk_g2s(ring[gs * kGroupRows + i], src, row_bytes, &full[gs]);
                 }
                 *(volatile int *)&s_issued = gg + 1;
@@ -1196,6 +1220,29 @@ k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, in
         const int issued = *(volatile int *)&s_issued;
         for (int g = g_fail; g < issued; ++g) mbar_wait(&full[g % kRingGroups], (g / kRingGroups) & 1);
     }
+}
+
+// Row activity of a library grid from the rasterizer's touched-tile flags (tiles of tile_w
+// wires x the flag layout's ticks, n_tiles_t per band of wires): act_s[w] = 1 when some tile of
+// wire w's band was touched (otherwise the row is all zero, and so is its spectrum), act_t[w] =
+// 1 when some wire within +-KC of w is (otherwise the convolution's output row is zero).
+__global__ void k_row_activity(const uint32_t *__restrict__ flags, int n_tiles_t, int tile_w, int n_wires,
+                               uint8_t *__restrict__ act_s, uint8_t *__restrict__ act_t) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= n_wires) return;
+    auto band = [&](int b) {
+        const uint32_t *f = flags + (size_t)b * n_tiles_t;
+        uint32_t any = 0;
+        for (int t = 0; t < n_tiles_t; ++t) any |= f[t];
+        return any != 0u;
+    };
+    const int b = w / tile_w;
+    const bool s_on = band(b);
+    const int b0 = max(w - KC, 0) / tile_w, b1 = min(w + KC, n_wires - 1) / tile_w;
+    bool t_on = s_on;
+    for (int bb = b0; bb <= b1 && !t_on; ++bb) t_on = band(bb);
+    act_s[w] = s_on ? 1 : 0;
+    act_t[w] = t_on ? 1 : 0;
 }
 
 // Twiddle tables on the device: tw[k] = exp(-2 pi i k / M) (k < M) and
@@ -1408,7 +1455,7 @@ bool launch_row_pair(const FFTPlan &p, bool composite, Launch &&launch, cudaErro
 }  // namespace
 
 cudaError_t launch_row_r2c(const FFTPlan &p, const float *in, int64_t in_stride, int n_in_cols, int n_rows,
-                           float2 *spec, cudaStream_t s, int32_t *status) {
+                           float2 *spec, cudaStream_t s, int32_t *status, const uint8_t *act) {
     if (n_rows <= 0) return cudaSuccess;
     if (row_kernel_choice(p) == 0 && (n_in_cols % 4 == 0) && in_stride == n_in_cols && aligned16(in) && aligned16(spec)) {
         cudaError_t err = cudaSuccess;
@@ -1421,7 +1468,7 @@ cudaError_t launch_row_r2c(const FFTPlan &p, const float *in, int64_t in_stride,
         cudaError_t err = cudaSuccess;
         const int grid = std::min(n_rows, 2 * device_sms());
         if (launch_row_pair<true>(p, row_kernel_choice(p) == 3, [&](auto kern, size_t smem, int threads) {
-                kern<<<grid, threads, smem, s>>>(p, in, n_rows, n_in_cols, spec, status);
+                kern<<<grid, threads, smem, s>>>(p, in, n_rows, n_in_cols, spec, status, act);
             }, err))
             return err;
     }
@@ -1441,7 +1488,7 @@ cudaError_t launch_row_r2c(const FFTPlan &p, const float *in, int64_t in_stride,
 }
 
 cudaError_t launch_row_c2r(const FFTPlan &p, const float2 *spec, int n_rows, float *out, int64_t out_stride,
-                           int n_out_cols, cudaStream_t s, int32_t *status) {
+                           int n_out_cols, cudaStream_t s, int32_t *status, const uint8_t *act) {
     if (n_rows <= 0) return cudaSuccess;
     if (row_kernel_choice(p) == 0 && (n_out_cols % 4 == 0) && out_stride == n_out_cols && aligned16(out) &&
         aligned16(spec)) {
@@ -1456,7 +1503,7 @@ cudaError_t launch_row_c2r(const FFTPlan &p, const float2 *spec, int n_rows, flo
         cudaError_t err = cudaSuccess;
         const int grid = std::min(n_rows, 2 * device_sms());
         if (launch_row_pair<false>(p, row_kernel_choice(p) == 3, [&](auto kern, size_t smem, int threads) {
-                kern<<<grid, threads, smem, s>>>(p, spec, n_rows, out, n_out_cols, status);
+                kern<<<grid, threads, smem, s>>>(p, spec, n_rows, out, n_out_cols, status, act);
             }, err))
             return err;
     }
@@ -1476,7 +1523,8 @@ cudaError_t launch_row_c2r(const FFTPlan &p, const float2 *spec, int n_rows, flo
 }
 
 cudaError_t launch_wire_stage(const FFTPlan &p, const float2 *spec, const float2 *resp_spec, int n_wires, float2 *out,
-                              cudaStream_t s, int32_t *status, const ClearJob *clear, bool accumulate, int n_phases) {
+                              cudaStream_t s, int32_t *status, const ClearJob *clear, bool accumulate, int n_phases,
+                              const uint8_t *act) {
     if (n_wires <= 0) return cudaSuccess;
     const ClearJob job = clear ? *clear : ClearJob{};
     if (aligned16(spec) && (p.Fs % 2) == 0 && (p.Fu % 2) == 0) {
@@ -1498,7 +1546,7 @@ cudaError_t launch_wire_stage(const FFTPlan &p, const float2 *spec, const float2
         dim3 grid(fb, (n_wires + wpc - 1) / wpc);
         k_wire_stage_tma<<<grid, kStageFB + 32, 0, s>>>(spec, resp_spec, p.Fs, p.Fu, n_wires, wpc, out, status, job,
                                                         accumulate ? 1 : 0, n_phases, (int64_t)n_wires * p.Fs,
-                                                        (int64_t)KW * p.Fs);
+                                                        (int64_t)KW * p.Fs, n_phases == 1 ? act : nullptr);
         return cudaGetLastError();
     }
     if (n_phases > 1) {
@@ -1519,6 +1567,13 @@ cudaError_t launch_wire_stage(const FFTPlan &p, const float2 *spec, const float2
         e = cudaGetLastError();
     }
     return e;
+}
+
+cudaError_t launch_row_activity(const uint32_t *flags, int n_tiles_t, int tile_w, int n_wires, uint8_t *act_s,
+                                uint8_t *act_t, cudaStream_t s) {
+    if (n_wires <= 0) return cudaSuccess;
+    k_row_activity<<<(n_wires + 255) / 256, 256, 0, s>>>(flags, n_tiles_t, tile_w, n_wires, act_s, act_t);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_make_twiddles(const FFTPlan &p, cudaStream_t s) {

@@ -176,12 +176,19 @@ cudaError_t launch_tile_scatter_patches(const int64_t *patch_desc, const float *
                                         const int32_t *tile_list, int64_t list_cap, const PlaneParams &pp, float *grid,
                                         cudaStream_t s, bool det = false, int32_t *status = nullptr);
 
+// act (optional, n_rows bytes): rows with act[row] == 0 are all zero; the paired kernels skip
+// them (their spectra rows are left unwritten and must be read as zero, as the wire stage does
+// when given the same act); other kernels transform every row
 cudaError_t launch_row_r2c(const FFTPlan &p, const float *in, int64_t in_stride, int n_in_cols, int n_rows,
-                           float2 *spec, cudaStream_t s, int32_t *status = nullptr);
+                           float2 *spec, cudaStream_t s, int32_t *status = nullptr, const uint8_t *act = nullptr);
 // accumulate: out += the stencil instead of out = (the per-phase sum of the impact mode)
+// act (optional, one phase only): spectrum rows with act[row] == 0 are read as zero
 cudaError_t launch_wire_stage(const FFTPlan &p, const float2 *spec, const float2 *resp_spec, int n_wires,
                               float2 *out, cudaStream_t s, int32_t *status = nullptr, const ClearJob *clear = nullptr,
-                              bool accumulate = false, int n_phases = 1);
+                              bool accumulate = false, int n_phases = 1, const uint8_t *act = nullptr);
+// act_s / act_t [n_wires] of a library grid from its touched-tile flags (see k_row_activity)
+cudaError_t launch_row_activity(const uint32_t *flags, int n_tiles_t, int tile_w, int n_wires, uint8_t *act_s,
+                                uint8_t *act_t, cudaStream_t s);
 // n_phases > 1 (impact mode): spec holds n_phases spectra [phase][wire][Fs] and resp_spec
 // n_phases response spectra [phase][21][Fs]; out = (out +) the sum over phases of their stencils
 // Noise + digitisation: code = clamp(floor(gain v + baseline + noise_rms z + 1/2), 0, max_code)
@@ -204,8 +211,10 @@ cudaError_t launch_raster_phases(int64_t n, const DepoDesc *desc, const PlanePar
                                  float *grids, uint32_t *flags, cudaStream_t s, unsigned long long *grids64 = nullptr,
                                  int32_t *status = nullptr);
 
+// act (optional): output rows with act[row] == 0 are zero; the paired kernels write them as zeros
+// without a transform (their spectrum rows need not exist), other kernels transform every row
 cudaError_t launch_row_c2r(const FFTPlan &p, const float2 *spec, int n_rows, float *out, int64_t out_stride,
-                           int n_out_cols, cudaStream_t s, int32_t *status = nullptr);
+                           int n_out_cols, cudaStream_t s, int32_t *status = nullptr, const uint8_t *act = nullptr);
 cudaError_t launch_scale_spectrum(float2 *spec, int64_t n, float scale, cudaStream_t s);
 cudaError_t launch_make_twiddles(const FFTPlan &p, cudaStream_t s);
 cudaError_t launch_wait_selftest(long long limit, int32_t *status, cudaStream_t s);

@@ -91,6 +91,10 @@ struct wct_sim {
     int conv_streams = 2;              // schedule: convolution streams (1, 2 or 3)
     float2 *bspec[3][2] = {};          // convolution streams 1, 2: forward / wire-stage spectra
     size_t bspec_elems[3] = {};
+    // per convolution scratch j (0: spec / spec2, j > 0: bspec[j]): the row activity of the grid
+    // being convolved, act[j][0] its rows, act[j][1] the output rows (wct::launch_row_activity)
+    uint8_t *act[3][2] = {};
+    int max_wires = 0;
     std::vector<cudaEvent_t> evpool;
     DepoDesc *desc = nullptr;
     int64_t *patch_size = nullptr, *patch_off = nullptr, *scan64 = nullptr;
@@ -549,21 +553,33 @@ wct_status_t raster_scatter(wct_sim *s, int plane, const wct_depos_t *d, float *
 
 // The convolution of one plane.  clear_grid (== grid, a library grid) with its tile flags:
 // the flagged tiles are zeroed once the forward transform has read the grid.
+// The convolution of one plane, with spectrum scratch js (0: spec / spec2, 1 or 2: bspec[js]).
+// clear_grid (== grid, a library grid) with its tile flags: rows of the grid that no depo
+// touched are all zero, so the transforms skip them (row activity from the flags), and the
+// flagged tiles are zeroed once the forward transform has read the grid.
 wct_status_t convolve_plane(wct_sim *s, int plane, const float *grid, float *wf, cudaStream_t st, int slot,
-                            float *clear_grid = nullptr, uint32_t *flags = nullptr, float2 *S = nullptr,
-                            float2 *T = nullptr) {
+                            float *clear_grid = nullptr, uint32_t *flags = nullptr, int js = 0) {
     const PlaneState &ps = s->planes[plane];
     const int nw = ps.g.n_wires, nt = ps.g.n_ticks;
-    if (!S) S = s->spec, T = s->spec2;
-    cudaError_t e = launch_row_r2c(ps.fft, grid, nt, nt, nw, S, st, s->status);
+    float2 *S = js == 0 ? s->spec : s->bspec[js][0], *T = js == 0 ? s->spec2 : s->bspec[js][1];
+    const uint8_t *act_s = nullptr, *act_t = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (clear_grid && s->act[js][0]) {
+        e = launch_row_activity(flags, ps.pp.n_tiles_t, ps.pp.tile_w, nw, s->act[js][0], s->act[js][1], st);
+        if (e != cudaSuccess) return cuda_fail(s, e, "row activity");
+        act_s = s->act[js][0];
+        act_t = s->act[js][1];
+        s->launches += 1;
+    }
+    e = launch_row_r2c(ps.fft, grid, nt, nt, nw, S, st, s->status, act_s);
     if (e != cudaSuccess) return cuda_fail(s, e, "row r2c");
     mark(s, slot, 3, st);
     // the wire stage clears the grid tiles the rasterizer listed, as a side job
     const ClearJob job = clear_grid ? clear_job(clear_grid, flags, ps.pp) : ClearJob{};
-    e = launch_wire_stage(ps.fft, S, ps.resp_spec, nw, T, st, s->status, clear_grid ? &job : nullptr);
+    e = launch_wire_stage(ps.fft, S, ps.resp_spec, nw, T, st, s->status, clear_grid ? &job : nullptr, false, 1, act_s);
     if (e != cudaSuccess) return cuda_fail(s, e, "wire stage");
     mark(s, slot, 4, st);
-    e = launch_row_c2r(ps.fft, T, nw, wf, nt, nt, st, s->status);
+    e = launch_row_c2r(ps.fft, T, nw, wf, nt, nt, st, s->status, act_t);
     if (e != cudaSuccess) return cuda_fail(s, e, "row c2r");
     s->launches += 3;
     mark(s, slot, 5, st);
@@ -869,6 +885,9 @@ wct_status_t wct_sim_create(const wct_plane_t *planes, int n_planes, const wct_r
     if (st == WCT_OK) st = dev_alloc(s, (void **)&s->spec, sizeof(float2) * spec_elems);
     if (st == WCT_OK) st = dev_alloc(s, (void **)&s->spec2, sizeof(float2) * spec_elems);
     s->spec_elems = spec_elems;
+    for (int p = 0; p < n_planes; ++p) s->max_wires = std::max(s->max_wires, s->planes[p].g.n_wires);
+    if (st == WCT_OK) st = dev_alloc(s, (void **)&s->act[0][0], 2 * (size_t)s->max_wires);
+    if (st == WCT_OK) s->act[0][1] = s->act[0][0] + s->max_wires;
     for (int p = 0; p < n_planes; ++p) {
         s->grid_off[p + 1] = s->grid_off[p] + (size_t)s->planes[p].g.n_wires * s->planes[p].g.n_ticks;
         s->flag_off[p + 1] = s->flag_off[p] + tile_flag_words(s->planes[p].pp);
@@ -1118,9 +1137,13 @@ wct_status_t ensure_conv_spectra(wct_sim *s, int n) {
         dev_free(s, s->bspec[j][1]);
         s->bspec[j][0] = s->bspec[j][1] = nullptr;
         s->bspec_elems[j] = 0;
+        dev_free(s, s->act[j][0]);
+        s->act[j][0] = s->act[j][1] = nullptr;
         const wct_status_t st = dev_alloc_all(s, {{(void **)&s->bspec[j][0], sizeof(float2) * s->spec_elems},
-                                                  {(void **)&s->bspec[j][1], sizeof(float2) * s->spec_elems}});
+                                                  {(void **)&s->bspec[j][1], sizeof(float2) * s->spec_elems},
+                                                  {(void **)&s->act[j][0], 2 * (size_t)s->max_wires}});
         if (st) return st;
+        s->act[j][1] = s->act[j][0] + s->max_wires;
         s->bspec_elems[j] = s->spec_elems;
     }
     return WCT_OK;
@@ -1153,7 +1176,6 @@ wct_status_t enqueue_batch(wct_sim *s, const wct_depos_t *events, int n_events, 
     static thread_local BatchTable tab;   // ~25 KB: kept off the stack
     for (int p = 0; p < npl; ++p) tab.plane[p] = s->planes[p].pp;
     cudaStream_t rs = s->rs_stream, *cv = s->cv_stream;
-    float2 *S[3] = {s->spec, s->bspec[1][0], s->bspec[2][0]}, *T[3] = {s->spec2, s->bspec[1][1], s->bspec[2][1]};
     // events of the pool: 0 fork, then per chunk c: 1 + 4c raster done, 2 + 4c + j its
     // convolutions done on convolution stream j
     cudaEvent_t fork = nullptr;
@@ -1226,7 +1248,7 @@ wct_status_t enqueue_batch(wct_sim *s, const wct_depos_t *events, int n_events, 
                     s->launches += 1;
                 }
                 r = convolve_plane(s, p, grid, wfs[(size_t)e * npl + p], cv[j], -1, grid,
-                                   s->tile_flags[set] + s->flag_off[p], S[j], T[j]);
+                                   s->tile_flags[set] + s->flag_off[p], j);
                 if (r) return r;
             }
         }

@@ -110,8 +110,9 @@ def test_batch_schedules_and_memory_limit_match_single_events():
     outs = [[torch.empty((p.n_wires, p.n_ticks), device="cuda") for p in planes] for _ in evs]
     sim.run_batch(dev, outs)
     sim.sync()
-    n_pairs = sum(1 for e in evs if e.n > 0) * len(planes)
-    assert sim.counters()["kernel_launches"] - n0 == 1 + 3 * len(evs) * len(planes), n_pairs
+    # one raster launch; per (event, plane) pair: row activity, forward transform, wire stage,
+    # inverse transform
+    assert sim.counters()["kernel_launches"] - n0 == 1 + 4 * len(evs) * len(planes)
     check(sim, "default")
     sim.close()
     for sched, label in ((8 | (2 << 4), "chunks of 2"), (8 | 256, "one convolution stream")):
