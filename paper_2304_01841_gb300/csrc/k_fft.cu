@@ -1056,6 +1056,7 @@ constexpr int kStageWiresMax = 512;      // output wires per CTA at most (chosen
 constexpr int kGroupRows = 8;
 constexpr int kRingGroups = 4;
 constexpr int kGroupLead = 3;            // groups loaded before the first block's: rows -4 .. 19
+constexpr int kImpactWires = 32;         // output wires per CTA with several phases (shared tile)
 
 // A frequency slice of zeros: the copy source of the rows outside the plane.
 __device__ __align__(16) float2 g_zero_row[kStageFB] = {};
@@ -1065,6 +1066,9 @@ k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, in
                  int wires_per_cta, float2 *__restrict__ T, int32_t *status, const ClearJob clear, int accumulate,
                  int n_phases, int64_t s_phase_stride, int64_t r_phase_stride, const uint8_t *__restrict__ act) {
     __shared__ __align__(16) float2 ring[kRingGroups * kGroupRows][kStageFB];
+    // impact mode (n_phases > 1): the CTA's outputs summed over the phases in shared memory
+    // ([output wire][frequency], dynamic, wires_per_cta rows) and written to T once
+    extern __shared__ float2 tile[];
     __shared__ uint64_t full[kRingGroups], empty[kRingGroups];
     __shared__ int s_issued, s_prod_done;               // groups the producer issued; it has stopped
     const int tid = threadIdx.x;
@@ -1103,7 +1107,7 @@ k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, in
 #pragma unroll
                 for (int i = 0; i < kGroupRows; ++i) {
                     const int src_row = w0 - KC + kGroupRows * k - 4 + i;
-                    live_row[i] = src_row >= 0 && src_row < n_wires && (!act || act[src_row]);
+                    live_row[i] = src_row >= 0 && src_row < n_wires && (!act || act[ph * n_wires + src_row]);
                 }
 #pragma unroll
                 for (int i = 0; i < kGroupRows; ++i) {
@@ -1200,8 +1204,20 @@ k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, in
                 if (live && j < nj &&
                     WCT_IDX_OK(status, (int64_t)(w0 + kOutBlock * q + j) * Fs + f, (int64_t)n_wires * Fs)) {
                     float2 v = make_float2(A.x - B.y, A.y + B.x);
-                    if (acc) v = cadd(v, dst[(size_t)j * Fs]);
-                    dst[(size_t)j * Fs] = v;
+                    if (n_phases > 1) {
+                        float2 &t = tile[(kOutBlock * q + j) * kStageFB + tid];
+                        const bool last = ph == n_phases - 1;
+                        if (ph > 0) v = cadd(v, t);
+                        if (!last) {
+                            t = v;
+                        } else {
+                            if (accumulate) v = cadd(v, dst[(size_t)j * Fs]);
+                            dst[(size_t)j * Fs] = v;
+                        }
+                    } else {
+                        if (acc) v = cadd(v, dst[(size_t)j * Fs]);
+                        dst[(size_t)j * Fs] = v;
+                    }
                 }
             }
             dst += (size_t)kOutBlock * Fs;
@@ -1226,23 +1242,28 @@ k_wire_stage_tma(const float2 *__restrict__ S, const float2 *__restrict__ Rt, in
 // wires x the flag layout's ticks, n_tiles_t per band of wires): act_s[w] = 1 when some tile of
 // wire w's band was touched (otherwise the row is all zero, and so is its spectrum), act_t[w] =
 // 1 when some wire within +-KC of w is (otherwise the convolution's output row is zero).
+// With n_phases > 1 (impact mode) the flags cover the phase grids stacked as one grid of
+// n_phases * n_wires rows: act_s then has a byte per phase row and act_t[w] is set when some
+// phase has a touched row within +-KC of w.
 __global__ void k_row_activity(const uint32_t *__restrict__ flags, int n_tiles_t, int tile_w, int n_wires,
-                               uint8_t *__restrict__ act_s, uint8_t *__restrict__ act_t) {
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= n_wires) return;
+                               int n_phases, uint8_t *__restrict__ act_s, uint8_t *__restrict__ act_t) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
     auto band = [&](int b) {
         const uint32_t *f = flags + (size_t)b * n_tiles_t;
         uint32_t any = 0;
         for (int t = 0; t < n_tiles_t; ++t) any |= f[t];
         return any != 0u;
     };
-    const int b = w / tile_w;
-    const bool s_on = band(b);
-    const int b0 = max(w - KC, 0) / tile_w, b1 = min(w + KC, n_wires - 1) / tile_w;
-    bool t_on = s_on;
-    for (int bb = b0; bb <= b1 && !t_on; ++bb) t_on = band(bb);
-    act_s[w] = s_on ? 1 : 0;
-    act_t[w] = t_on ? 1 : 0;
+    if (r < n_phases * n_wires) act_s[r] = band(r / tile_w) ? 1 : 0;
+    if (r < n_wires) {
+        bool t_on = false;
+        for (int ph = 0; ph < n_phases && !t_on; ++ph) {
+            const int base = ph * n_wires;
+            const int b0 = (base + max(r - KC, 0)) / tile_w, b1 = (base + min(r + KC, n_wires - 1)) / tile_w;
+            for (int bb = b0; bb <= b1 && !t_on; ++bb) t_on = band(bb);
+        }
+        act_t[r] = t_on ? 1 : 0;
+    }
 }
 
 // Twiddle tables on the device: tw[k] = exp(-2 pi i k / M) (k < M) and
@@ -1532,10 +1553,25 @@ cudaError_t launch_wire_stage(const FFTPlan &p, const float2 *spec, const float2
         // and the launch takes ceil(CTAs / resident CTAs) waves, so pick the wpc that
         // minimises waves x (wpc + 20): a last, nearly empty wave costs a full CTA time.
         const int fb = (p.Fu + kStageFB - 1) / kStageFB;
-        const int resident = wire_stage_resident();
-        int wpc = kStageWiresMax;
+        // impact mode: the phases' sum of a CTA's outputs lives in shared memory, so runs are
+        // short (at most kImpactWires output wires)
+        const int max_c = n_phases > 1 ? kImpactWires : kStageWiresMax;
+        const size_t dyn = n_phases > 1 ? sizeof(float2) * (size_t)kImpactWires * kStageFB : 0;
+        int resident = 0;
+        if (n_phases > 1) {
+            int per_sm = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wire_stage_tma, kStageFB + 32, dyn) != cudaSuccess ||
+                per_sm < 1) {
+                cudaGetLastError();
+                per_sm = 1;
+            }
+            resident = per_sm * std::max(device_sms(), 1);
+        } else {
+            resident = wire_stage_resident();
+        }
+        int wpc = max_c;
         int64_t best = INT64_MAX;
-        for (int c = 16; c <= kStageWiresMax; ++c) {
+        for (int c = 16; c <= max_c; ++c) {
             const int64_t ctas = (int64_t)fb * ((n_wires + c - 1) / c);
             const int64_t cost = (ctas + resident - 1) / resident * (c + 2 * KC);
             if (cost < best) {
@@ -1544,9 +1580,13 @@ cudaError_t launch_wire_stage(const FFTPlan &p, const float2 *spec, const float2
             }
         }
         dim3 grid(fb, (n_wires + wpc - 1) / wpc);
-        k_wire_stage_tma<<<grid, kStageFB + 32, 0, s>>>(spec, resp_spec, p.Fs, p.Fu, n_wires, wpc, out, status, job,
+        if (dyn) {
+            const cudaError_t e = cudaFuncSetAttribute(k_wire_stage_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+            if (e != cudaSuccess) return e;
+        }
+        k_wire_stage_tma<<<grid, kStageFB + 32, dyn, s>>>(spec, resp_spec, p.Fs, p.Fu, n_wires, wpc, out, status, job,
                                                         accumulate ? 1 : 0, n_phases, (int64_t)n_wires * p.Fs,
-                                                        (int64_t)KW * p.Fs, n_phases == 1 ? act : nullptr);
+                                                        (int64_t)KW * p.Fs, act);
         return cudaGetLastError();
     }
     if (n_phases > 1) {
@@ -1570,9 +1610,10 @@ cudaError_t launch_wire_stage(const FFTPlan &p, const float2 *spec, const float2
 }
 
 cudaError_t launch_row_activity(const uint32_t *flags, int n_tiles_t, int tile_w, int n_wires, uint8_t *act_s,
-                                uint8_t *act_t, cudaStream_t s) {
-    if (n_wires <= 0) return cudaSuccess;
-    k_row_activity<<<(n_wires + 255) / 256, 256, 0, s>>>(flags, n_tiles_t, tile_w, n_wires, act_s, act_t);
+                                uint8_t *act_t, cudaStream_t s, int n_phases) {
+    const int rows = n_phases * n_wires;
+    if (rows <= 0) return cudaSuccess;
+    k_row_activity<<<(rows + 255) / 256, 256, 0, s>>>(flags, n_tiles_t, tile_w, n_wires, n_phases, act_s, act_t);
     return cudaGetLastError();
 }
 

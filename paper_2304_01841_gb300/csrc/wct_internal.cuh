@@ -182,13 +182,14 @@ cudaError_t launch_tile_scatter_patches(const int64_t *patch_desc, const float *
 cudaError_t launch_row_r2c(const FFTPlan &p, const float *in, int64_t in_stride, int n_in_cols, int n_rows,
                            float2 *spec, cudaStream_t s, int32_t *status = nullptr, const uint8_t *act = nullptr);
 // accumulate: out += the stencil instead of out = (the per-phase sum of the impact mode)
-// act (optional, one phase only): spectrum rows with act[row] == 0 are read as zero
+// act (optional, [n_phases][n_wires]): spectrum rows with act == 0 are read as zero
 cudaError_t launch_wire_stage(const FFTPlan &p, const float2 *spec, const float2 *resp_spec, int n_wires,
                               float2 *out, cudaStream_t s, int32_t *status = nullptr, const ClearJob *clear = nullptr,
                               bool accumulate = false, int n_phases = 1, const uint8_t *act = nullptr);
-// act_s / act_t [n_wires] of a library grid from its touched-tile flags (see k_row_activity)
+// act_s [n_phases][n_wires] / act_t [n_wires] of a library grid (the phase grids stacked, in the
+// impact mode) from its touched-tile flags (see k_row_activity)
 cudaError_t launch_row_activity(const uint32_t *flags, int n_tiles_t, int tile_w, int n_wires, uint8_t *act_s,
-                                uint8_t *act_t, cudaStream_t s);
+                                uint8_t *act_t, cudaStream_t s, int n_phases = 1);
 // n_phases > 1 (impact mode): spec holds n_phases spectra [phase][wire][Fs] and resp_spec
 // n_phases response spectra [phase][21][Fs]; out = (out +) the sum over phases of their stencils
 // Noise + digitisation: code = clamp(floor(gain v + baseline + noise_rms z + 1/2), 0, max_code)

@@ -46,6 +46,7 @@ struct PlaneState {
     size_t phase_grid_bytes = 0;
     uint32_t *phase_flags = nullptr;   // touched-tile flags + list of the phase grids (one grid)
     size_t phase_flag_bytes = 0;
+    uint8_t *phase_act = nullptr;      // row activity of the phase grids [n_phases][n_wires] + [n_wires]
     unsigned long long *phase_grids64 = nullptr;   // deterministic mode: fixed-point phase grids
     size_t phase_grid64_bytes = 0;
     int phase_tiles = 0;
@@ -631,6 +632,8 @@ void drop_impact(wct_sim *s, PlaneState &ps) {
     dev_free(s, ps.phase_grids, ps.phase_grid_bytes);
     dev_free(s, ps.phase_flags, ps.phase_flag_bytes);
     dev_free(s, ps.phase_grids64, ps.phase_grid64_bytes);
+    dev_free(s, ps.phase_act);
+    ps.phase_act = nullptr;
     ps.phase_grids64 = nullptr;
     ps.phase_grid64_bytes = 0;
     ps.resp_imp = nullptr;
@@ -678,17 +681,25 @@ wct_status_t run_plane_impact(wct_sim *s, int p, const wct_depos_t *d, float *wf
     if (e != cudaSuccess) return cuda_fail(s, e, "phase raster");
     s->launches += (n > 0 ? 2 : 0) + (ps.phase_grids64 ? 1 : 0);
     mark(s, slot, 2, cs);
-    // every phase grid's rows in one forward launch, one wire stage over all phases
-    e = launch_row_r2c(ps.fft_imp, ps.phase_grids, nt, nt, ps.n_phases * nw, s->spec_imp, cs, s->status);
+    // every phase grid's rows in one forward launch (rows no depo touched skipped), one wire
+    // stage over all phases, one inverse transform
+    const uint8_t *act_s = ps.phase_act, *act_t = ps.phase_act ? ps.phase_act + (size_t)ps.n_phases * nw : nullptr;
+    if (act_s) {
+        e = launch_row_activity(ps.phase_flags, ps.pp.n_tiles_t, ps.pp.tile_w, nw, ps.phase_act,
+                                ps.phase_act + (size_t)ps.n_phases * nw, cs, ps.n_phases);
+        if (e != cudaSuccess) return cuda_fail(s, e, "phase row activity");
+        s->launches += 1;
+    }
+    e = launch_row_r2c(ps.fft_imp, ps.phase_grids, nt, nt, ps.n_phases * nw, s->spec_imp, cs, s->status, act_s);
     if (e != cudaSuccess) return cuda_fail(s, e, "phase transforms");
     mark(s, slot, 3, cs);
     const ClearJob job = phase_clear_job(ps);
     e = launch_wire_stage(ps.fft_imp, s->spec_imp, ps.resp_imp, nw, s->spec2, cs, s->status, &job, false,
-                          ps.n_phases);
+                          ps.n_phases, act_s);
     if (e != cudaSuccess) return cuda_fail(s, e, "phase stencils");
     s->launches += 2;
     mark(s, slot, 4, cs);
-    e = launch_row_c2r(ps.fft_imp, s->spec2, nw, wf, nt, nt, cs, s->status);
+    e = launch_row_c2r(ps.fft_imp, s->spec2, nw, wf, nt, nt, cs, s->status, act_t);
     if (e != cudaSuccess) return cuda_fail(s, e, "row c2r");
     s->launches += 1;
     mark(s, slot, 5, cs);
@@ -1525,6 +1536,7 @@ wct_status_t wct_sim_set_impact_responses(wct_sim_t *s, int plane, const wct_res
         ps.phase_grid_bytes = sizeof(float) * (size_t)n_phases * ps.g.n_wires * ps.g.n_ticks;
         st = dev_alloc(s, (void **)&ps.phase_grids, ps.phase_grid_bytes);
     }
+    if (st == WCT_OK) st = dev_alloc(s, (void **)&ps.phase_act, (size_t)(n_phases + 1) * ps.g.n_wires);
     if (st == WCT_OK) {
         const int tiles_w = (n_phases * ps.g.n_wires + ps.pp.tile_w - 1) / ps.pp.tile_w;
         ps.phase_tiles = tiles_w * ps.pp.n_tiles_t;
