@@ -329,6 +329,11 @@ def measure_uboone(n_events=16, reps=10):
         sim.run_event(e, o)
     sim.sync()
     st = sim.stage_times()
+    # the batch's convolutions (two streams), timed on their streams
+    sim.set_timing(True)
+    sim.run_batch(evs, outs)
+    sim.sync()
+    conv_batch_us = sim.stage_times()["batch_convolve"] / n_events
     sim.set_timing(False)
     peak, _, kind = measured_peaks()
     sb = stage_bytes(pl, wl.n_depos, sim.plane_info(0)["spectrum_bins_used"])
@@ -344,6 +349,8 @@ def measure_uboone(n_events=16, reps=10):
             "raster_scatter_us": round(st["raster_scatter"], 1), "kernels": kern,
             "convolve_us": round(conv_us, 1),
             "convolve_frac_unpruned": round(unp / (conv_us * 1e-6) / 1e9 / peak, 4),
+            "convolve_batched_us_per_event": round(conv_batch_us, 1),
+            "convolve_batched_frac_unpruned": round(unp / (conv_batch_us * 1e-6) / 1e9 / peak, 4),
             "convolve_frac_supported_bins": round(sb["convolve"] / (conv_us * 1e-6) / 1e9 / peak, 4),
             "convolve_unpruned_bytes": unp, "classical_3pass_bytes": classical,
             "peak_source": f"{kind} (burst copy)"}
@@ -728,6 +735,8 @@ def main():
     stages = {
         "batch_raster_launch": raster_report,
         "batch_convolutions_us": round(conv_us_b, 1),
+        "batch_convolutions_frac_unpruned": round(E * unpruned / (conv_us_b * 1e-6) / 1e9 / peak_gbs, 4)
+        if conv_us_b > 0 else None,
         "per_batch_kernel_us": {k: round(v, 1) for k, v in per_batch.items()},
         "convolve_kernels_run_event": kernels,
         "convolve_total_run_event": {

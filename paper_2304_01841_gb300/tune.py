@@ -1,10 +1,12 @@
 """Schedule autotuning with a persistent cache.
 
 The library has several kernel schedules per handle (wct_opts_t::schedule_id: the row
-transforms' form and the rasterizer's granularity).  `autotune` times one event through
-`run_event` under each candidate schedule on the current device and keeps the fastest; the
-choice is cached in a JSON file keyed by the device name and the planes' geometry, so later
-processes reuse it without timing again (`Simulator(..., schedule_id=best)`).
+transforms' form and the rasterizer's granularity; for run_batch, the events per persistent
+raster launch and the number of convolution streams).  `autotune` times one event through
+`run_event` under each candidate schedule on the current device and keeps the fastest;
+`autotune_batch` does the same for a batch through `run_batch`.  The choice is cached in a JSON
+file keyed by the device name and the planes' geometry (and the batch size), so later processes
+reuse it without timing again (`Simulator(..., schedule_id=best)`).
 
 The timing and handle creation go through callables so the selection and the cache can be
 tested without a GPU.
@@ -20,6 +22,13 @@ from typing import Callable, Dict, Optional, Sequence
 # -1: paired row transforms with composite radices (the default); 4: paired, radices <= 8;
 # 1: one persistent row CTA per SM; 0: register-staged rows; +2: CTA-level rasterizer
 CANDIDATES = (-1, 4, 1, 0, 6)
+
+
+# run_batch candidates (bit 3: paired composite row transforms, the default's): -1 the default
+# (one raster launch for the whole batch, two convolution streams); +256 one convolution
+# stream; +512 three; (v << 4): 2^(v-1) events per raster launch, pipelined with the previous
+# launch's convolutions
+BATCH_CANDIDATES = (-1, 8 | 256, 8 | 512, 8 | (5 << 4), 8 | (4 << 4))
 
 
 def default_cache_path() -> str:
@@ -111,5 +120,58 @@ def autotune(planes, responses, diffusion, depos, candidates: Sequence[int] = CA
             if close:
                 close()
     best = min(ms, key=lambda c: (ms[c], cands.index(c)))
+    cache.put(key, best, ms)
+    return best
+
+
+def _cuda_batch_timer(sim, events, reps: int) -> float:
+    """Median device time (ms) of run_batch on `events` after two warm-up calls (the second
+    records the batch's graph, later calls replay it)."""
+    import torch
+    st = torch.cuda.current_stream()
+    outs = sim.run_batch(events)
+    sim.run_batch(events, outs)
+    sim.sync()
+    times = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        sim.run_batch(events, outs)
+        b.record(st)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    sim.sync()
+    return statistics.median(times)
+
+
+def autotune_batch(planes, responses, diffusion, events, candidates: Sequence[int] = BATCH_CANDIDATES, reps: int = 3,
+                   deterministic: bool = False, cache: Optional[TuneCache] = None, device: Optional[str] = None,
+                   make_sim: Optional[Callable] = None, timer: Optional[Callable] = None) -> int:
+    """The fastest run_batch schedule_id among `candidates` for a batch of len(events) events
+    (DeviceDepos) on these planes (from the cache when present, else measured and stored)."""
+    if device is None:
+        import torch
+        device = torch.cuda.get_device_name()
+    cache = cache if cache is not None else TuneCache()
+    key = "batch|" + tune_key(device, planes, deterministic) + f"|events={len(events)}"
+    hit = cache.get(key)
+    if hit is not None:
+        return hit
+    if make_sim is None:
+        from . import Simulator
+
+        def make_sim(sched):
+            return Simulator(planes, responses, diffusion, schedule_id=sched, deterministic=deterministic)
+    timer = timer or _cuda_batch_timer
+    ms: Dict[int, float] = {}
+    for c in candidates:
+        sim = make_sim(c)
+        try:
+            ms[c] = float(timer(sim, events, reps))
+        finally:
+            close = getattr(sim, "close", None)
+            if close:
+                close()
+    best = min(ms, key=lambda c: (ms[c], list(candidates).index(c)))
     cache.put(key, best, ms)
     return best

@@ -37,3 +37,21 @@ def test_autotune_measures_caches_and_stays_exact(tmp_path):
     sim.sync()
     _, _, ref = oracle.simulate_plane(d, wl.planes[0], wl.diffusion, wl.responses()[0])
     assert rel_l2(wf, ref) <= WAVE_RTOL
+
+
+def test_batch_autotune_measures_and_stays_exact(tmp_path):
+    import numpy as np
+    import paper_2304_01841_gb300 as g
+    from paper_2304_01841_gb300 import tune
+    wl = synth.workload("three_plane")
+    evs = [wl.depos(n_depos=n, seed=40 + i, event_id=60 + i) for i, n in enumerate((6000, 15000, 3000, 9000))]
+    dev = [g.DeviceDepos.from_host(e) for e in evs]
+    cache = tune.TuneCache(str(tmp_path / "tune.json"))
+    best = tune.autotune_batch(wl.planes, wl.responses(), wl.diffusion, dev, reps=2, cache=cache)
+    assert best in tune.BATCH_CANDIDATES
+    sim = make_sim(wl.planes, wl.responses(), wl.diffusion, schedule_id=best)
+    out = sim.run_batch(dev)
+    sim.sync()
+    for p in range(3):
+        _, _, ref = oracle.simulate_plane(evs[1], wl.planes[p], wl.diffusion, wl.responses()[p], plane_index=p)
+        assert rel_l2(to_np(out[1][p]), ref) <= WAVE_RTOL

@@ -53,3 +53,30 @@ def test_ties_keep_the_earlier_candidate_and_bad_cache_is_ignored(tmp_path):
     (tmp_path / "tune.json").write_text("not json")
     best, made = _run(tmp_path, {-1: 0.5, 4: 0.5, 1: 0.5, 0: 0.5, 6: 0.5})
     assert best == -1 and len(made) == 5
+
+
+def test_batch_autotune_picks_the_fastest_and_caches_it(tmp_path):
+    from paper_2304_01841_gb300 import tune
+    planes = [synth.Plane(64, 500)]
+    times = {-1: 5.0, 8 | 256: 6.0, 8 | 512: 4.5, 8 | (5 << 4): 4.5, 8 | (4 << 4): 7.0}
+    made = []
+
+    class FakeSim:
+        def __init__(self, sched):
+            self.sched = sched
+            made.append(sched)
+
+        def close(self):
+            pass
+
+    cache = tune.TuneCache(str(tmp_path / "t.json"))
+    best = tune.autotune_batch(planes, None, None, [object()] * 4, cache=cache, device="dev",
+                               make_sim=FakeSim, timer=lambda sim, ev, reps: times[sim.sched])
+    assert best == 8 | 512 and made == list(tune.BATCH_CANDIDATES)        # ties: the earlier candidate
+    made.clear()
+    again = tune.autotune_batch(planes, None, None, [object()] * 4, cache=tune.TuneCache(cache.path), device="dev",
+                                make_sim=FakeSim, timer=lambda sim, ev, reps: 0.0)
+    assert again == best and made == []                                   # from the cache, no timing
+    other = tune.autotune_batch(planes, None, None, [object()] * 8, cache=cache, device="dev",
+                                make_sim=FakeSim, timer=lambda sim, ev, reps: times[sim.sched])
+    assert other == best and len(made) == len(tune.BATCH_CANDIDATES)      # another batch size: measured
