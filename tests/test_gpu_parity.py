@@ -526,3 +526,47 @@ def test_full_size_batch_as_benchmarked():
         sim.sync()
         scale = float(single.abs().max())
         assert float((outs[e][0] - single).abs().max()) <= 1e-5 * scale, e
+
+
+def test_sparse_event_zero_rows_skipped_exactly():
+    # one short track and a few isolated depos on the full uboone plane: most wire rows carry no
+    # charge, so the transforms skip them (row activity from the touched tiles); the waveform
+    # matches the oracle, rows beyond the response's reach of any charge are exactly zero, and
+    # the batch and the impact mode agree
+    import paper_2304_01841_gb300 as g
+    wl = synth.workload("uboone_plane")
+    pl = wl.planes[0]
+    rng = np.random.default_rng(31)
+    n = 3000
+    t = rng.random(n)
+    x = (1200.0 + 400.0 * t).astype(np.float32)
+    z = (-300.0 + 60.0 * t).astype(np.float32)              # ~20 wires of track
+    q = np.full(n, 5000.0, np.float32)
+    iso = 20
+    x = np.concatenate([x, rng.uniform(100, 3000, iso).astype(np.float32)])
+    z = np.concatenate([z, rng.uniform(-5000, 5000, iso).astype(np.float32)])
+    q = np.concatenate([q, np.full(iso, 800.0, np.float32)])
+    m = n + iso
+    d = synth.Depos(np.zeros(m, np.float32), x, np.zeros(m, np.float32), z, q, event_id=71)
+    diff = synth.Diffusion(fluctuate=True, seed=5)
+    resp = synth.make_response(pl.response_kind)
+    sim = make_sim([pl], [resp], diff)
+    dd = _dev(d)
+    wf = to_np(sim.run_event(dd)[0])
+    wb = to_np(sim.run_batch([dd, _dev(wl.depos(n_depos=2000, seed=8, event_id=72))])[0][0])
+    sim.sync()
+    _, grid, ref = oracle.simulate_plane(d, pl, diff, resp)
+    assert rel_l2(wf, ref) <= WAVE_RTOL and rel_l2(wb, ref) <= WAVE_RTOL
+    charged = np.flatnonzero(np.abs(grid).sum(axis=1) > 0)
+    near = np.zeros(pl.n_wires, bool)
+    for w in charged:
+        near[max(w - 10, 0): w + 11] = True
+    assert near.mean() < 0.5                                 # mostly empty rows
+    assert np.all(wf[~near] == 0.0) and np.all(wb[~near] == 0.0)
+    r_imp = synth.make_response_impact(pl.response_kind, n_impact=pl.n_impact_per_pitch)
+    sim.set_impact_responses(0, r_imp)
+    wi = to_np(sim.run_event(dd)[0])
+    sim.sync()
+    _, _, ref_i = oracle.simulate_plane_impact(d, pl, diff, r_imp)
+    assert rel_l2(wi, ref_i) <= WAVE_RTOL
+    assert np.all(wi[~near] == 0.0)
