@@ -1127,17 +1127,45 @@ cudaError_t launch_raster_phases(int64_t n, const DepoDesc *desc, const PlanePar
 // Deterministic mode: the fixed-point tiles listed in `flags` (layout of flag_tiles; the list
 // is only read) are added to the float grid, each value rounded once to float and scaled by
 // 1 / kFixScale (exact), and zeroed again.  One CTA per listed tile, grid-stride; a thread per
-// tick column of the tile.
+// four adjacent bins (16-byte loads, several in flight) when the row length, the tile width and
+// both grids allow it, else a thread per tick column.
 __global__ void __launch_bounds__(256)
 k_fix_tiles(const uint32_t *__restrict__ flags, int n_tiles, int n_tiles_t, int tile_w, int tile_t, int n_rows,
             int n_cols, unsigned long long *__restrict__ g64, float *__restrict__ grid, int32_t *status) {
     const uint32_t count = flags[n_tiles];
+    // four bins per thread and several rows in flight where the rows allow 16-byte accesses
+    const bool vec = (n_cols & 3) == 0 && (tile_t & 3) == 0 && (reinterpret_cast<uintptr_t>(grid) & 15) == 0 &&
+                     (reinterpret_cast<uintptr_t>(g64) & 15) == 0;
     for (uint32_t i = blockIdx.x; i < count; i += gridDim.x) {
         const int t = (int)flags[n_tiles + 2 + i];
         if (!WCT_IDX_OK(status, t, n_tiles)) continue;
         const int tw = t / n_tiles_t, tt = t - tw * n_tiles_t;
         const int r0 = tw * tile_w, c0 = tt * tile_t;
         const int r1 = min(r0 + tile_w, n_rows), c1 = min(c0 + tile_t, n_cols);
+        if (vec) {
+            const int q_per_row = (c1 - c0) >> 2;              // 4-bin quads per row of the tile
+            const int n_q = (r1 - r0) * q_per_row;
+#pragma unroll 4
+            for (int k = threadIdx.x; k < n_q; k += blockDim.x) {
+                const int r = r0 + k / q_per_row, c = c0 + 4 * (k - (k / q_per_row) * q_per_row);
+                const size_t idx = (size_t)r * n_cols + c;
+                ulonglong2 *g2 = reinterpret_cast<ulonglong2 *>(g64 + idx);
+                const ulonglong2 a = g2[0], b = g2[1];
+                if ((a.x | a.y | b.x | b.y) != 0ull) {
+                    float4 *gf = reinterpret_cast<float4 *>(grid + idx);
+                    float4 v = *gf;
+                    const float sc = 1.f / kFixScale;
+                    v.x += __ll2float_rn((long long)a.x) * sc;
+                    v.y += __ll2float_rn((long long)a.y) * sc;
+                    v.z += __ll2float_rn((long long)b.x) * sc;
+                    v.w += __ll2float_rn((long long)b.y) * sc;
+                    *gf = v;
+                    g2[0] = make_ulonglong2(0ull, 0ull);
+                    g2[1] = make_ulonglong2(0ull, 0ull);
+                }
+            }
+            continue;
+        }
         for (int r = r0; r < r1; ++r)
             for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
                 const size_t idx = (size_t)r * n_cols + c;
