@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 
 import synth
-from helpers import make_sim, rel_l2, to_np
+from helpers import WAVE_RTOL, make_sim, rel_l2, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -76,6 +76,45 @@ def test_batch_multiplane_matches_single_and_graph_replay():
             assert _close(to_np(outs[e][p]), s, np.abs(s).max())
 
 
+def test_batch_with_empty_off_plane_and_single_depo_events():
+    # degenerate members of a batch: an empty event, events whose depos all fall outside the
+    # planes (beyond the wires, beyond the ticks), a one-depo event and one event passed twice,
+    # mixed with ordinary ones; every waveform is written (outputs start at 7), the degenerate
+    # ones are exactly zero, and every event matches the FP64 oracle
+    import oracle
+    import paper_2304_01841_gb300 as g
+    planes, responses = _small_three_plane()
+    diff = synth.Diffusion(fluctuate=True, seed=91)
+    sim = make_sim(planes, responses, diff)
+    base = _events(3, seed=5, lo=300, hi=900, id0=40)
+    empty = base[0].subset(slice(0, 0))
+    empty.event_id = 50
+    beyond_wires = base[1].subset(slice(None))
+    beyond_wires.z = beyond_wires.z + np.float32(5000.0)     # pitch far beyond every plane's wires
+    beyond_wires.y = beyond_wires.y + np.float32(5000.0)
+    beyond_wires.event_id = 51
+    beyond_ticks = base[2].subset(slice(None))
+    beyond_ticks.t0 = beyond_ticks.t0 + np.float32(1e4)      # arrivals after the last tick
+    beyond_ticks.event_id = 52
+    one = base[0].subset(slice(3, 4))
+    one.event_id = 53
+    evs = [base[0], empty, beyond_wires, one, base[1], beyond_ticks, base[2]]
+    dev = [g.DeviceDepos.from_host(e) for e in evs]
+    evs.append(base[0])                                       # the same device arrays twice
+    dev.append(dev[0])
+    outs = [[torch.full((p.n_wires, p.n_ticks), 7.0, device="cuda") for p in planes] for _ in evs]
+    sim.run_batch(dev, outs)
+    sim.sync()
+    for e, d in enumerate(evs):
+        for p in range(len(planes)):
+            got = to_np(outs[e][p])
+            if e in (1, 2, 5):
+                assert float(np.abs(got).max()) == 0.0, (e, p)
+                continue
+            _, _, ref = oracle.simulate_plane(d, planes[p], diff, responses[p], plane_index=p)
+            assert rel_l2(got, ref) <= WAVE_RTOL, (e, p)
+
+
 def test_batch_schedules_and_memory_limit_match_single_events():
     # one persistent raster launch for the whole batch (the default), chunks of 2 events that
     # pipeline with the previous chunk's convolutions, a single convolution stream, and a budget
@@ -131,6 +170,7 @@ def test_server_results_same_alone_and_in_mix():
     planes, responses = _small_three_plane()
     diff = synth.Diffusion(fluctuate=True, seed=5)
     evs = _events(24, seed=3, lo=10, hi=6000, id0=300)
+    evs[7] = evs[7].subset(slice(0, 0))        # an empty request among the others
     srv = EventServer(planes, responses, diff, n_slots=3, max_batch=4, hbm_budget_bytes=64 << 20,
                       keep_results=True)
     reqs = [srv.submit(e) for e in evs[:10]]
