@@ -27,7 +27,7 @@ def test_shard_plan_gives_disjoint_events_per_rank():
 
 
 def test_unpruned_and_classical_bytes_of_the_three_planes():
-    # the survey's byte model: grid read + waveform write + one spectrum round trip at every bin
+    # the unpruned byte model: grid read + waveform write + one spectrum round trip at every bin
     # of the unpadded half spectrum (1286 MB for the three-plane event); the classical
     # three-pass 2D-FFT schedule moves three more spectra
     planes = synth.workload("three_plane").planes
