@@ -569,6 +569,8 @@ def measure_serving(n_events=120, loads=(0.5, 0.8, 0.95)):
 # --------------------------------------------------------------------------------------------
 def main():
     args = parse()
+    if args.steps < 1 or args.warmup < 0 or args.batch < 1:
+        raise SystemExit("bench.py: --steps and --batch must be >= 1, --warmup >= 0")
     if args.impl == "reference":
         run_reference(args)
         return
@@ -625,9 +627,11 @@ def main():
     t0 = time.perf_counter()
     start = torch.cuda.Event(enable_timing=True)
     stop = torch.cuda.Event(enable_timing=True)
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     start.record(stream)
     for k in range(K):
         sim.run_batch(dev_events, outs)
+        marks[k].record(stream)
     stop.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -635,6 +639,7 @@ def main():
     clk = clocks.stop()
     sim.sync()
     elapsed_ms = start.elapsed_time(stop)
+    step_ms = sorted([start.elapsed_time(marks[0])] + [marks[k - 1].elapsed_time(marks[k]) for k in range(1, K)])
     launches = sim.counters()["kernel_launches"] - launches0
     elapsed_ms = max_over_ranks(elapsed_ms, world, "cuda")
     value = world * K * depos_per_batch / (elapsed_ms / 1000.0)
@@ -831,6 +836,10 @@ def main():
                        "l2": "every event has its own 317 MB of grids and 317 MB of waveforms (> 126 MB L2) and a "
                              "step cycles through 64 events: no flush needed"},
             "events_per_s": events_per_s,
+            "step_ms": {"median": step_ms[len(step_ms) // 2],
+                        "p99": step_ms[min(len(step_ms) - 1, int(math.ceil(0.99 * len(step_ms))) - 1)],
+                        "min": step_ms[0], "max": step_ms[-1],
+                        "what": "device time of each timed step on this rank (CUDA events on the launching stream)"},
             "one_at_a_time": {"events_per_s": E / t_one, "depos_per_s": depos_per_batch / t_one,
                               "batched_over_one_at_a_time": events_per_s / world / (E / t_one)},
             "latency_ms": {"p50": p50, "p99": p99,
