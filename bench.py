@@ -159,7 +159,7 @@ def unpruned_convolve_bytes(plane, resp_ticks=200):
 
 def kernel_counters():
     """ncu counters per launch of the main kernels (profiles/kernel_counters.json), valid only
-    while the CUDA sources are unchanged (csrc digest)."""
+    while the device-code sources are unchanged (csrc_digest)."""
     p = os.path.join(ROOT, "profiles", "kernel_counters.json")
     try:
         with open(p) as f:
@@ -169,10 +169,14 @@ def kernel_counters():
 
 
 def csrc_digest():
+    """Digest of the sources that hold device code (the kernels k_*.cu and the headers they
+    include); the host-only orchestration (wct_sim.cu, wct_response.cu) does not enter it."""
     import hashlib
     h = hashlib.sha256()
     cdir = os.path.join(ROOT, "paper_2304_01841_gb300", "csrc")
     for name in sorted(os.listdir(cdir)):
+        if not (name.startswith("k_") and name.endswith(".cu")) and not name.endswith(".cuh"):
+            continue
         with open(os.path.join(cdir, name), "rb") as f:
             h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
@@ -649,20 +653,49 @@ def main():
     t_one = cuda_timed(lambda: [sim.run_event(d, o) for d, o in zip(dev_events, outs)], 1, warm=1)
     sim.sync()
 
-    # ---- per-event latency and per-kernel times: run_event, CUDA events on the launching
-    # stream around each event and (library timing) around each kernel ---------------------
+    # ---- per-event latency: run_event as a caller runs it, CUDA events on the launching
+    # stream around each event -----------------------------------------------------------
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(E + 1)]
-    sim.set_timing(True)
     ev[0].record(stream)
     for i in range(E):
         sim.run_event(dev_events[i], outs[i])
         ev[i + 1].record(stream)
     torch.cuda.synchronize()
     sim.sync()
-    st_ev = sim.stage_times()
     lat = sorted(ev[j].elapsed_time(ev[j + 1]) for j in range(E))
     p50 = lat[len(lat) // 2]
     p99 = lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
+    # ---- the same through a stream of the highest priority: run_event then convolves each
+    # plane on one of two library streams of that priority while the next plane is rasterized
+    try:
+        top = torch.cuda.Stream.priority_range()[1]
+    except Exception:
+        top = -1
+    hp = torch.cuda.Stream(priority=top)
+    hp.wait_stream(stream)
+    evh = [torch.cuda.Event(enable_timing=True) for _ in range(E + 1)]
+    for i in range(2):
+        sim.run_event(dev_events[i], outs[i], stream=hp)
+    evh[0].record(hp)
+    for i in range(E):
+        sim.run_event(dev_events[i], outs[i], stream=hp)
+        evh[i + 1].record(hp)
+    hp.synchronize()
+    sim.sync(stream=hp)
+    stream.wait_stream(hp)
+    lat_hp = sorted(evh[j].elapsed_time(evh[j + 1]) for j in range(E))
+    latency_hp = {"p50": lat_hp[len(lat_hp) // 2],
+                  "p99": lat_hp[min(len(lat_hp) - 1, int(math.ceil(0.99 * len(lat_hp))) - 1)],
+                  "events_per_s": E * 1e3 / sum(lat_hp), "stream_priority": top,
+                  "what": "as latency_ms, on a stream of the highest priority (convolutions on two streams)"}
+    # ---- per-kernel times: the same events with the library's stage timing on (the planes
+    # then run one after the other on the stream, so each kernel's time is its own) --------
+    sim.set_timing(True)
+    for i in range(E):
+        sim.run_event(dev_events[i], outs[i])
+    torch.cuda.synchronize()
+    sim.sync()
+    st_ev = sim.stage_times()
     # ---- the batch's persistent raster launch and its convolutions, timed on their streams
     sim.set_timing(True)
     sim.run_batch(dev_events, outs)
@@ -844,6 +877,7 @@ def main():
                               "batched_over_one_at_a_time": events_per_s / world / (E / t_one)},
             "latency_ms": {"p50": p50, "p99": p99,
                            "what": "device time of one event of the batch through run_event, events back to back"},
+            "latency_ms_priority_stream": latency_hp,
             "roofline": roofline,
             "stages": stages,
             "cpu_baseline": cpu,

@@ -202,7 +202,16 @@ wct_status_t wct_sim_scatter(wct_sim_t *sim, int plane, const wct_depos_t *depos
 wct_status_t wct_sim_convolve(wct_sim_t *sim, int plane, const float *grid, float *waveform, void *stream);
 
 /* The whole DepoTransform (§2, all three steps) for every plane of one event.
- * waveforms: HOST array of n_planes DEVICE pointers, each float32 [n_wires][n_ticks]. */
+ * waveforms: HOST array of n_planes DEVICE pointers, each float32 [n_wires][n_ticks].
+ * The planes are rasterized one after the other on `stream`.  When `stream` has a priority
+ * above the device's lowest (the default priority, 0, is the lowest), the event has two or
+ * more planes, none in the impact mode, and stage timing is off, plane p's convolution runs
+ * on a library stream of `stream`'s priority (two per priority, p mod 2) once that plane's
+ * raster is done, while `stream` goes on with the next plane; `stream` waits for both before
+ * later work.  Otherwise every step runs on `stream`: work on the lowest-priority stream is
+ * treated as background work that should not occupy more of the GPU at once.  The second
+ * stream's spectrum scratch is allocated at the first such call and counted against the HBM
+ * budget; if it cannot be had, or with timing on, the planes run entirely on `stream`. */
 wct_status_t wct_sim_run_event(wct_sim_t *sim, const wct_depos_t *depos, float *const *waveforms,
                                void *stream);
 

@@ -129,6 +129,16 @@ struct wct_sim {
     std::vector<Graph> graphs;
     std::vector<std::vector<uint64_t>> seen;   // recent batch keys not (yet) recorded
     int64_t graph_launches = 0;
+    // run_event: the planes' convolutions forked onto two streams of the caller's priority
+    // (one pair per priority seen), ordered by ev_plane (a plane's grid is complete) and
+    // ev_join (a fork stream's work is done); ev_overlap_off after scratch could not be had
+    struct EventStreams {
+        int priority;
+        cudaStream_t st[2];
+    };
+    std::vector<EventStreams> ev_streams;
+    cudaEvent_t ev_plane[kMaxPlanes] = {}, ev_join[2] = {};
+    bool ev_overlap_off = false;
     // run_host: upload / compute / download streams, double-buffered device staging
     cudaStream_t up_stream = nullptr, comp_stream = nullptr, down_stream = nullptr;
     cudaEvent_t ev_up[2] = {}, ev_comp[2] = {}, ev_down[2] = {};
@@ -706,6 +716,99 @@ wct_status_t run_plane_impact(wct_sim *s, int p, const wct_depos_t *d, float *wf
     return WCT_OK;
 }
 
+wct_status_t ensure_conv_spectra(wct_sim *s, int n);
+
+// The two fork streams of run_event for the caller's stream priority (created on first use).
+cudaError_t event_streams(wct_sim *s, cudaStream_t caller, cudaStream_t (&fs)[2]) {
+    int prio = 0;
+    cudaError_t e = cudaStreamGetPriority(caller, &prio);
+    if (e != cudaSuccess) return e;
+    for (const auto &es : s->ev_streams)
+        if (es.priority == prio) {
+            fs[0] = es.st[0];
+            fs[1] = es.st[1];
+            return cudaSuccess;
+        }
+    wct_sim::EventStreams es{prio, {nullptr, nullptr}};
+    for (int j = 0; j < 2 && e == cudaSuccess; ++j)
+        e = cudaStreamCreateWithPriority(&es.st[j], cudaStreamNonBlocking, prio);
+    for (int p = 0; p < s->n_planes && e == cudaSuccess; ++p)
+        if (!s->ev_plane[p]) e = cudaEventCreateWithFlags(&s->ev_plane[p], cudaEventDisableTiming);
+    for (int j = 0; j < 2 && e == cudaSuccess; ++j)
+        if (!s->ev_join[j]) e = cudaEventCreateWithFlags(&s->ev_join[j], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        for (cudaStream_t h : es.st)
+            if (h) cudaStreamDestroy(h);
+        return e;
+    }
+    s->ev_streams.push_back(es);
+    fs[0] = es.st[0];
+    fs[1] = es.st[1];
+    return cudaSuccess;
+}
+
+// run_event of a folded handle with several planes, stage timing off, on a stream above the
+// device's lowest priority: each plane is rasterized on the caller's stream as before, and its
+// convolution then runs on fork stream p mod 2 (each with its own spectrum scratch, at the
+// caller's priority) while the caller's stream goes on with the next plane's raster; the
+// caller's stream finally waits for both fork streams.  One plane's transforms thus overlap
+// another's and the next raster, as in run_batch.  Work on the lowest-priority stream is
+// background work and keeps the single-stream form: spread over three streams it holds more
+// of the GPU at once, and higher-priority streams' work then waits longer for SMs (measured
+// on a served mix: light-event p50 latency 0.85 -> 2-8 ms at 0.8-0.95 load when heavy
+// low-priority events forked).  *taken = false (and nothing enqueued) when this form does
+// not apply or its scratch cannot be had; the caller then runs the planes one after the other
+// on its stream.
+wct_status_t run_event_forked(wct_sim *s, const wct_depos_t *d, float *const *wfs, cudaStream_t cs, bool *taken) {
+    *taken = false;
+    if (s->timing || s->n_planes < 2 || s->ev_overlap_off) return WCT_OK;
+    for (int p = 0; p < s->n_planes; ++p)
+        if (s->planes[p].n_phases > 0) return WCT_OK;
+    int prio = 0, lowest = 0, highest = 0;
+    if (cudaStreamGetPriority(cs, &prio) != cudaSuccess ||
+        cudaDeviceGetStreamPriorityRange(&lowest, &highest) != cudaSuccess) {
+        cudaGetLastError();
+        return WCT_OK;
+    }
+    if (prio >= lowest) return WCT_OK;                 // background work: one stream
+    if (!s->bspec[1][0] || s->bspec_elems[1] < s->spec_elems) {
+        // the second stream's spectra; without them (memory or budget) run_event stays serial
+        const std::string keep = s->err;
+        if (ensure_conv_spectra(s, 2) != WCT_OK) {
+            s->err = keep;
+            s->ev_overlap_off = true;
+            return WCT_OK;
+        }
+    }
+    cudaStream_t fs[2] = {};
+    if (event_streams(s, cs, fs) != cudaSuccess) {
+        cudaGetLastError();
+        s->ev_overlap_off = true;
+        return WCT_OK;
+    }
+    *taken = true;
+    wct_status_t st = WCT_OK;
+    cudaError_t e = cudaSuccess;
+    for (int p = 0; p < s->n_planes && st == WCT_OK && e == cudaSuccess; ++p) {
+        float *grid = s->grids[0] + s->grid_off[p];
+        uint32_t *flags = s->tile_flags[0] + s->flag_off[p];
+        const int j = p & 1;
+        if ((st = raster_scatter(s, p, d, grid, cs, -1, false, flags))) break;
+        e = cudaEventRecord(s->ev_plane[p], cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(fs[j], s->ev_plane[p], 0);
+        if (e == cudaSuccess) st = convolve_plane(s, p, grid, wfs[p], fs[j], -1, grid, flags, j);
+    }
+    // join, also after a failure, so that no forked work outlives the call unordered
+    for (int j = 0; j < 2; ++j) {
+        cudaError_t e2 = cudaEventRecord(s->ev_join[j], fs[j]);
+        if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(cs, s->ev_join[j], 0);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (st == WCT_OK && e != cudaSuccess) st = cuda_fail(s, e, "run_event streams");
+    if (st) clear_grids(s);
+    return st;
+}
+
 }  // namespace
 
 extern "C" {
@@ -940,6 +1043,13 @@ wct_status_t wct_sim_destroy(wct_sim_t *s) {
     for (int b = 0; b < 2; ++b)
         for (cudaEvent_t h : {s->ev_up[b], s->ev_comp[b], s->ev_down[b]})
             if (h) cudaEventDestroy(h);
+    for (auto &es : s->ev_streams)
+        for (cudaStream_t h : es.st)
+            if (h) cudaStreamDestroy(h);
+    for (cudaEvent_t h : s->ev_plane)
+        if (h) cudaEventDestroy(h);
+    for (cudaEvent_t h : s->ev_join)
+        if (h) cudaEventDestroy(h);
     delete s;
     return WCT_OK;
 }
@@ -1054,6 +1164,9 @@ wct_status_t wct_sim_run_event(wct_sim_t *s, const wct_depos_t *d, float *const 
         if (!wfs[p]) return fail(s, WCT_EINVAL, "a waveform pointer is NULL");
     if ((st = ensure_depo_capacity(s, d->n))) return st;
     cudaStream_t cs = (cudaStream_t)stream;
+    bool taken = false;
+    st = run_event_forked(s, d, wfs, cs, &taken);
+    if (taken) return st;
     for (int p = 0; p < s->n_planes; ++p) {
         // accumulate into the library grid (all zero), which the forward transform clears
         // again as it reads it; the inverse transform writes the caller's waveform

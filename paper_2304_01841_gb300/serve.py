@@ -113,7 +113,8 @@ class CudaBackend:
                 # one event (e.g. a heavy one, alone on a low-priority slot): run_event, whose
                 # rasterizer is a plain grid of short CTAs, so higher-priority work from other
                 # slots takes over SMs as its CTAs finish (the batch's persistent raster launch
-                # would hold every SM until it is done)
+                # would hold every SM until it is done); on the high-priority stream it also
+                # convolves the planes on two streams, on the low-priority one it keeps to one
                 self.sim.run_event(self.dev[0], self.outs[0], stream=self.stream)
             else:
                 self.sim.run_batch(self.dev, self.outs, stream=self.stream)

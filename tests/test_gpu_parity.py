@@ -212,6 +212,40 @@ def test_event_three_plane_full_waveforms():
     _event_parity(wl, wl.depos(), check_grid=False)
 
 
+def test_event_three_plane_on_a_high_priority_stream():
+    # on a stream above the device's lowest priority, run_event convolves each plane on one of
+    # two library streams of that priority while the next plane is rasterized: two events back
+    # to back on that stream (the second reuses the grids the first one's convolutions
+    # cleared), each against the oracle; the same event on the default stream (every step on
+    # one stream) agrees, and in the deterministic mode bit for bit
+    wl = synth.workload("three_plane")
+    da = wl.depos(n_depos=100_000)
+    db = wl.depos(n_depos=60_000, seed=wl.seed + 77)
+    db.event_id = da.event_id + 1
+    hp = torch.cuda.Stream(priority=-2)
+    for det in (False, True):
+        sim = make_sim(wl.planes, wl.responses(), wl.diffusion, deterministic=det)
+        ea, eb = _dev(da), _dev(db)
+        hp.wait_stream(torch.cuda.current_stream())
+        wa = sim.run_event(ea, stream=hp)
+        wb = sim.run_event(eb, stream=hp)
+        hp.synchronize()
+        sim.sync(stream=hp)
+        serial = [to_np(w) for w in sim.run_event(ea)]
+        sim.sync()
+        for p, pl in enumerate(wl.planes):
+            got_a, got_b = to_np(wa[p]), to_np(wb[p])
+            if det:
+                assert np.array_equal(got_a, serial[p]), p
+            else:
+                assert np.abs(got_a - serial[p]).max() <= 1e-5 * np.abs(serial[p]).max(), p
+                _, _, ref_a = oracle.simulate_plane(da, pl, wl.diffusion, wl.responses()[p], plane_index=p)
+                _, _, ref_b = oracle.simulate_plane(db, pl, wl.diffusion, wl.responses()[p], plane_index=p)
+                assert rel_l2(got_a, ref_a) <= WAVE_RTOL, p
+                assert rel_l2(got_b, ref_b) <= WAVE_RTOL, p
+        sim.close()
+
+
 # ------------------------------------------------------------------------------------------
 # Edge cases
 # ------------------------------------------------------------------------------------------
