@@ -805,7 +805,10 @@ wct_status_t run_event_forked(wct_sim *s, const wct_depos_t *d, float *const *wf
         if (e == cudaSuccess) e = e2;
     }
     if (st == WCT_OK && e != cudaSuccess) st = cuda_fail(s, e, "run_event streams");
-    if (st) clear_grids(s);
+    if (st) {
+        cudaDeviceSynchronize();                       // forked work done before the grids are reset
+        clear_grids(s);
+    }
     return st;
 }
 
