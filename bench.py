@@ -674,7 +674,7 @@ def main():
     hp = torch.cuda.Stream(priority=top)
     hp.wait_stream(stream)
     evh = [torch.cuda.Event(enable_timing=True) for _ in range(E + 1)]
-    for i in range(2):
+    for i in range(min(2, E)):
         sim.run_event(dev_events[i], outs[i], stream=hp)
     evh[0].record(hp)
     for i in range(E):

@@ -104,7 +104,8 @@ __device__ __forceinline__ float fold_plain(const Item &f, const float *wt, cons
 }
 
 // Fluctuated, not yet rescaled, folded charge of one item: the sum over the wire's sub-bins
-// in the window of max(0, q w + sqrt(q w (1 - w)) z), w = w_t * w_p.  z comes from the
+// in the window of max(0, q w + sqrt(q w (1 - w)) z), w = w_t * w_p (the variance m - m w
+// with m = q w as one fused multiply-add: one rounding, never negative).  z comes from the
 // counter-based pool: Philox4x32-10 of (depo, tick, wire * G + group, c3) under the key;
 // a call serves a group of four sub-bins, lanes 0/1 from the Box-Muller pair of words 0/1
 // and lanes 2/3 from words 2/3.
@@ -134,7 +135,7 @@ __device__ __forceinline__ float fold_fluct(const Item &f, const float *wt, cons
             if (l >= l0 && l < l1) {
                 const float w = wa * wp[f.j_base + sb + l];
                 const float m = q * w;
-                const float v = fmaf(sfu_sqrt(m * (1.f - w)), z[l], m);
+                const float v = fmaf(sfu_sqrt(fmaf(-m, w, m)), z[l], m);
                 acc += fmaxf(v, 0.f);
             }
         }
@@ -795,7 +796,7 @@ k_rasterize_patches(int64_t n, const DepoDesc *__restrict__ desc, const int64_t 
                 const float w = wt[a] * wp[j];
                 const float m = q * w;
                 const float z = bin_normal(pp, (uint32_t)di, d.lo_t + a, d.lo_p + j, c3);
-                const float v = fmaxf(fmaf(sfu_sqrt(m * (1.f - w)), z, m), 0.f);
+                const float v = fmaxf(fmaf(sfu_sqrt(fmaf(-m, w, m)), z, m), 0.f);
                 out[b] = v;
                 part += v;
             }
@@ -1082,7 +1083,7 @@ k_raster_phases(int64_t n, const DepoDesc *__restrict__ desc, PlaneParams pp, ui
                 for (int l = 0; l < 4; ++l)
                     if (l >= l0 && l < l1) {
                         const float w = wt[a] * wp[jb + l], m = q * w;
-                        part += fmaxf(fmaf(sfu_sqrt(m * (1.f - w)), z[l], m), 0.f);
+                        part += fmaxf(fmaf(sfu_sqrt(fmaf(-m, w, m)), z[l], m), 0.f);
                     }
             }
             const float sum = warp_sum(part);
@@ -1100,7 +1101,7 @@ k_raster_phases(int64_t n, const DepoDesc *__restrict__ desc, PlaneParams pp, ui
             for (int l = 0; l < 4; ++l)
                 if (l >= l0 && l < l1) {
                     const float w = wt[a] * wp[jb + l], m = q * w;
-                    const float v = (pp.fluctuate && scale > 0.f) ? fmaxf(fmaf(sfu_sqrt(m * (1.f - w)), z[l], m), 0.f) * scale
+                    const float v = (pp.fluctuate && scale > 0.f) ? fmaxf(fmaf(sfu_sqrt(fmaf(-m, w, m)), z[l], m), 0.f) * scale
                                                                  : m;
                     const int phase = (g << 2) + l;
                     const int64_t t = ((int64_t)phase * pp.n_wires + wire) * pp.n_ticks + tick;
